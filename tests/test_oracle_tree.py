@@ -1,0 +1,210 @@
+"""Pins of the precision-tree emulator (oracle/tree.py).
+
+The emulator walks Alg. 1-3 recursively.  It is pinned by
+  * the all-FP64 tree, which must reproduce the plain Cholesky (Sec. 3.2: the
+    recursion only reorders the arithmetic);
+  * an independent, non-recursive formulation written here: a left-looking
+    block Cholesky in which every update term l_ik * l_jk is rounded in the
+    precision of the shallower of the two tree nodes that separate (i, j) and
+    (j, k).  Following Alg. 1-3 by hand, an update to an entry of a node's A21
+    is made by that node's TRSM and an update to its A22 by that node's SYRK,
+    so this is the precision the tree assigns to the term.  With every leaf in
+    FP64 the two computations differ only in float64 rounding order;
+  * flop shares of a level, which follow from Alg. 1-3 in closed form;
+  * the accuracy ladder of Sec. 4.2 (ordering only).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dense, lowprec, tree
+from synth import dominant_spd, paper_spd, seed_for
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_parse_and_split():
+    t = tree.parse("[F16,F16,F16,F16,F32|F64@128]")
+    assert t.levels == ["F16"] * 4 + ["F32"] and t.inner == "F64" and t.inner_size == 128
+    t = tree.parse("[F8,F16,F16,F32|F64@128]")
+    assert t.levels[0] == "F8"
+    for bad in ["F16,F32", "[F12]", "[]", "[F16|F16@12]"]:
+        with pytest.raises(ValueError):
+            tree.parse(bad)
+    assert tree.split(8192) == 4096 and tree.split(1000) == 512 and tree.split(7) == 3
+    for n in range(2, 3000):
+        n1 = tree.split(n)
+        assert 0 < n1 < n
+        if n >= 512:
+            assert n1 % 128 == 0
+        elif n >= 32:
+            assert n1 % 16 == 0
+
+
+def test_precision_assignment_by_depth_and_inner():
+    t = tree.parse("[F16,F16,F32|F64@128]")
+    assert tree.node_prec(t, 0, 4096) == "F16"
+    assert tree.node_prec(t, 1, 2048) == "F16"
+    assert tree.node_prec(t, 2, 1024) == "F32"
+    assert tree.node_prec(t, 5, 256) == "F32"
+    assert tree.node_prec(t, 6, 128) == "F64"
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 64), (64, 64), (65, 64), (300, 64), (1000, 128), (777, 96)])
+def test_all_f64_tree_equals_plain_cholesky(n, leaf):
+    A = dominant_spd(n, 1.0, seed_for(0, n), shift=1.0)
+    L0, info0 = dense.cholesky(A)
+    L1, info1, _ = tree.emulate_potrf(A, tree.parse("[F64]", leaf=leaf))
+    assert info0 == info1 == 0
+    assert dense.factor_error(L1, L0) <= 1e-14
+    assert dense.backward_error(A, L1) <= 1e-13
+
+
+def test_level_flop_shares_closed_form():
+    # level l of a power-of-two tree carries 0.75 * 4^-l of n^3/3 (m^3/4 per node of order m)
+    t = tree.parse("[F16,F16,F16,F16,F32|F64@128]")
+    s = tree.level_flop_split(8192, t)
+    assert abs(s["F16"] - (1 - 4.0 ** -4)) < 1e-12
+    assert abs(s["F64"] - 4.0 ** -6) < 1e-12
+    t = tree.parse("[F8,F16,F16,F32|F64@128]")
+    s = tree.level_flop_split(32768, t)
+    assert abs(s["F8"] - 0.75) < 1e-12 and abs(s["F16"] - (0.25 - 4.0 ** -3)) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# independent left-looking formulation with per-term precision
+# ---------------------------------------------------------------------------------------
+def _leaves_and_nodes(n, t):
+    """Leaf ranges, and for each internal node its (depth, order, split index)."""
+    leaves, nodes = [], []
+
+    def walk(off, m, depth):
+        if m <= t.leaf:
+            leaves.append((off, m))
+            return
+        m1 = tree.split(m)
+        nodes.append((off, m, depth, off + m1))
+        walk(off, m1, depth + 1)
+        walk(off + m1, m - m1, depth + 1)
+
+    walk(0, n, 0)
+    return leaves, nodes
+
+
+def _separating_node(nodes, a, b):
+    """Deepest node containing indices a < b with a left of its split and b right of it."""
+    best = None
+    for off, m, depth, s in nodes:
+        if off <= a < s <= b < off + m:
+            if best is None or depth > best[0]:
+                best = (depth, m)
+    return best
+
+
+def _round(p, X, M=None, r0=0, c0=0, sb=128):
+    if p == "F64":
+        return X
+    if p == "F32":
+        return lowprec.round_f32(X)
+    if p == "F16":
+        q, a = lowprec.quantize_f16(X)
+        assert a == 1.0
+        return q
+    q, s = lowprec.quantize_e4m3_tiles(M, r0, c0, X.shape[0], X.shape[1], sb)
+    return q * s
+
+
+def left_looking_reference(A, t):
+    n = A.shape[0]
+    leaves, nodes = _leaves_and_nodes(n, t)
+    L = np.zeros((n, n))
+    for J, (j0, nj) in enumerate(leaves):
+        for I in range(J, len(leaves)):
+            i0, ni = leaves[I]
+            S = np.array(np.tril(A)[i0:i0 + ni, j0:j0 + nj]) if I == J else np.array(A[i0:i0 + ni, j0:j0 + nj])
+            for K in range(J):
+                k0, nk = leaves[K]
+                njk = _separating_node(nodes, k0, j0)
+                if I == J:
+                    node = njk
+                else:
+                    nij = _separating_node(nodes, j0, i0)
+                    node = nij if nij[0] < njk[0] else njk
+                p = tree.node_prec(t, node[0], node[1])
+                Xi = _round(p, L[i0:i0 + ni, k0:k0 + nk], L, i0, k0)
+                Xj = _round(p, L[j0:j0 + nj, k0:k0 + nk], L, j0, k0)
+                S -= Xi @ Xj.T
+            if I == J:
+                Lj, info = dense.cholesky(S)
+                assert info == 0
+                L[j0:j0 + nj, j0:j0 + nj] = Lj
+            else:
+                L[i0:i0 + ni, j0:j0 + nj] = dense.trsm_rlt(S, L[j0:j0 + nj, j0:j0 + nj])
+    return L
+
+
+@pytest.mark.parametrize("spec,n,leaf", [
+    ("[F16,F32]", 384, 64),
+    ("[F16,F16,F32|F64@64]", 640, 64),
+    ("[F32,F16,F64]", 520, 64),
+    ("[F16,F16,F16,F32|F64@128]", 1024, 128),
+    ("[F8,F16,F32|F64@128]", 1024, 128),
+])
+def test_emulator_matches_left_looking_term_precision(spec, n, leaf):
+    t = tree.parse(spec, leaf=leaf)
+    A = dominant_spd(n, 1.05, seed_for(1, n))
+    L_emu, info, _ = tree.emulate_potrf(A, t, leaf_compute="F64")
+    assert info == 0
+    L_ref = left_looking_reference(A, t)
+    err = np.max(np.abs(L_emu - L_ref)) / np.max(np.abs(L_ref))
+    assert err <= 1e-13, err
+    # and the reduced precision did something: far from the FP64 factor
+    L64, _ = dense.cholesky(A)
+    assert dense.factor_error(L_emu, L64) > 1e-9
+
+
+def test_a_misplaced_precision_is_detected():
+    """Rounding the TRSM terms by the (deeper) L-node level instead of the destination
+    level is a plausible mistake; the left-looking reference must tell them apart."""
+    t = tree.parse("[F16,F32]", leaf=64)
+    A = dominant_spd(384, 1.05, seed_for(1, 384))
+    L_ref = left_looking_reference(A, t)
+
+    class Wrong(tree.Emulator):
+        def trsm(self, r0, m, c0, nc, p):
+            super().trsm(r0, m, c0, nc, "F32" if p == "F16" else p)
+
+    em = Wrong(A, t, leaf_compute="F64")
+    em.potrf(0, em.n, 0)
+    err = np.max(np.abs(np.tril(em.M) - L_ref)) / np.max(np.abs(L_ref))
+    assert err > 1e-8
+
+
+def test_accuracy_ladder_of_the_paper_in_shape():
+    with open(os.path.join(GOLD, "paper_numbers.json")) as f:
+        ladder = json.load(f)["accuracy_digits_ladder"]
+    n = 1024
+    A = paper_spd(n, seed_for(9, 0))
+    errs = []
+    for spec in ladder["order_best_to_worst"]:
+        L, info, _ = tree.emulate_potrf(A, tree.parse(spec, leaf=128))
+        assert info == 0
+        errs.append(dense.backward_error(A, L))
+    assert -np.log10(errs[0]) >= ladder["F64_min_digits"]
+    assert -np.log10(errs[-1]) <= ladder["F16_max_digits"]
+    # mixed configurations sit between pure FP32-level and pure FP16
+    assert errs[0] < errs[1] < errs[2]
+    assert errs[3] < errs[-1] and errs[4] < errs[-1]
+
+
+def test_fp8_level_uses_tile_scales():
+    t = tree.parse("[F8,F32|F64@128]", leaf=128)
+    A = dominant_spd(512, 2.0, seed_for(2, 512))
+    L, info, em = tree.emulate_potrf(A, t)
+    assert info == 0
+    be = dense.backward_error(A, L)
+    # E4M3 keeps 3 mantissa bits: the error is far above FP16's but bounded
+    assert 1e-5 < be < 5e-2
+    assert any(c[0] == "F8" for c in em.gemm_calls)
