@@ -1,0 +1,168 @@
+/*
+ * hrp.h — C ABI of the hierarchical recursive precision (HRP) Cholesky library
+ * for GB300 (sm_103a).
+ *
+ * The library factors a dense symmetric positive-definite matrix A = L L^T with the
+ * nested recursive Cholesky of Carrica et al., "Hierarchical Recursive Precision for
+ * Accelerating Symmetric Linear Solves on MXUs" (arXiv 2601.08082):
+ *   - Alg. 1 Tree-POTRF_L, Alg. 2 Tree-TRSM_{R,L,T}, Alg. 3 Tree-SYRK_L (Sec. 3.2):
+ *     POTRF, TRSM and SYRK are all split recursively down to GEMMs;
+ *   - the tree-structured precision hierarchy of Sec. 3.3: low precision on large
+ *     off-diagonal blocks, FP32/FP64 on the recursively refined diagonal;
+ *   - the per-block quantization of Sec. 3.4 around every low-precision GEMM;
+ * and solves A X = B with the factor (the "linear solve" of the title and abstract),
+ * optionally refined in FP64 (mixed-precision iterative refinement, Sec. 1-2).
+ *
+ * Conventions (all entry points)
+ *   - Matrices are column-major with a leading dimension (LAPACK style):
+ *     entry (i, j) of A is A[i + j * lda], 0-based, lda >= max(1, n).
+ *   - Pointers named d* are DEVICE pointers on the handle's device; other pointers are
+ *     host pointers.  The caller owns every buffer it passes; the handle owns its
+ *     workspace.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on it in order.  Functions documented as synchronous wait for the
+ *     stream before returning (only to read back a status); *_async variants never wait.
+ *   - Return value: hrp_status.  On HRP_ERR_INVALID_ARG, hrp_last_arg() returns the
+ *     1-based position of the offending argument, negated (LAPACK's -i convention).
+ *   - There is no CPU fallback: every step runs in this library's CUDA kernels.
+ *   - The first call that needs a larger workspace allocates it (cudaMalloc); make one
+ *     call of each size before capturing calls into a CUDA graph.
+ */
+#ifndef HRP_H_
+#define HRP_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HRP_OK = 0,
+  HRP_ERR_INVALID_ARG = 1,     /* bad argument, see hrp_last_arg() */
+  HRP_ERR_NOT_SPD = 2,         /* *info = 1-based global column of the first pivot that is not
+                                  positive and finite (LAPACK POTRF's convention) */
+  HRP_ERR_NO_CONVERGENCE = 3,  /* refinement did not reach tol within max_iter */
+  HRP_ERR_ALLOC = 4,           /* device or host allocation failed */
+  HRP_ERR_CUDA = 5,            /* a CUDA call failed; hrp_last_error() has the text */
+  HRP_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired (no trap, context usable) */
+  HRP_ERR_UNSUPPORTED = 7,     /* valid request this build does not implement */
+  HRP_ERR_RANGE = 8            /* input outside the range an FP16 tree handles without alpha > 1 */
+} hrp_status;
+
+/* Precisions of the tree (Sec. 3.3). HRP_F8E4M3 is OCP E4M3FN with per-tile scales. */
+typedef enum { HRP_F64 = 0, HRP_F32 = 1, HRP_F16 = 2, HRP_F8E4M3 = 3 } hrp_prec;
+
+#define HRP_MAX_DEPTH 16
+
+/*
+ * Precision tree (Sec. 3.3; notation of Sec. 4.2: a list from the outermost
+ * off-diagonal level to the innermost diagonal).
+ *   level[t], t < depth: precision of the off-diagonal TRSM/SYRK work of a node at
+ *     recursion depth t; nodes deeper than depth-1 use level[depth-1].
+ *   inner, inner_size: when inner_size > 0, every node of order <= inner_size runs
+ *     entirely in `inner` (F64 or F32), e.g. "[F16,F16,F16,F16,F32|F64@128]".
+ *   leaf: Alg. 1 base case size b (a diagonal block of order <= leaf is factored by the
+ *     leaf POTRF kernel); 1 <= leaf <= 128.
+ *   trsm_leaf, syrk_leaf: Alg. 2 / Alg. 3 base-case sizes (0 = leaf); trsm_leaf <= leaf.
+ *   scale_block: tile edge of the FP8 power-of-two scales (128).
+ * Split point of a node of order n (reading of "e.g. n1 = floor(n/2)"): n/2 rounded to
+ * the nearest multiple of 128 for n >= 512, of 16 for 32 <= n < 512, floor(n/2) below.
+ */
+typedef struct {
+  int depth;
+  int level[HRP_MAX_DEPTH];
+  int leaf;
+  int inner;
+  int inner_size;
+  int trsm_leaf;
+  int syrk_leaf;
+  int scale_block;
+} hrp_tree;
+
+typedef struct hrp_handle_s hrp_handle;
+
+/* Create a handle bound to CUDA device `device`; *out receives it. */
+hrp_status hrp_create(hrp_handle** out, int device);
+/* Free the handle and all workspace it owns (synchronizes the device). */
+hrp_status hrp_destroy(hrp_handle* h);
+
+/* 1-based index (negated) of the last invalid argument, 0 if none. */
+int hrp_last_arg(const hrp_handle* h);
+/* Text of the last error on this handle (static storage owned by the handle). */
+const char* hrp_last_error(const hrp_handle* h);
+const char* hrp_status_string(hrp_status s);
+
+/*
+ * Parse a tree string "[P0,P1,...,Pd-1]" or "[P0,...,Pd-1|F64@S]" with P in
+ * {F64,F32,F16,F8}; leaf as described above; trsm_leaf = syrk_leaf = 0, scale_block = 128.
+ */
+hrp_status hrp_tree_parse(const char* spec, int leaf, hrp_tree* out);
+/* Print a tree in the same notation into buf (always NUL-terminated). Returns length. */
+int hrp_tree_format(const hrp_tree* t, char* buf, size_t len);
+
+/*
+ * Factor A = L L^T (Alg. 1-3 with the tree's precisions).
+ *   n >= 0; dA device, column-major, lda >= max(1,n). The lower triangle is read and
+ *   overwritten with L (the computed values, held in FP64); the strict upper triangle
+ *   is not touched.
+ *   info: host int* (may be NULL). The call synchronizes `stream` once at the end to read
+ *   it: 0, or the 1-based column of the first failing pivot (then HRP_ERR_NOT_SPD).
+ */
+hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda,
+                     int* info, void* stream);
+/*
+ * As hrp_potrf, but never synchronizes: d_info is a DEVICE int that receives 0 or the
+ * failing column when the enqueued work completes. Capturable in a CUDA graph once the
+ * workspace for n exists.
+ */
+hrp_status hrp_potrf_async(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda,
+                           int* d_info, void* stream);
+
+/*
+ * Solve A X = B given the factor from hrp_potrf (L in the lower triangle of dL):
+ * forward substitution L Y = B, then backward L^T X = Y, both in FP64.
+ * dB (n x nrhs, ldb >= max(1,n)) is overwritten with X. Asynchronous.
+ */
+hrp_status hrp_potrs(hrp_handle* h, int n, int nrhs, const double* dL, int ldl,
+                     double* dB, int ldb, void* stream);
+
+/*
+ * Factor + solve + FP64 iterative refinement.
+ *   dA is NOT modified (the factor lives in the handle's workspace).
+ *   X_0 = POTRS(B); repeat R = B - A X (FP64, A's lower triangle read as symmetric),
+ *   D = POTRS(R), X += D, until max_j ||r_j||_2/||b_j||_2 <= tol or max_iter corrections.
+ *   If the tree's factorization fails (info > 0) the call refactors with the fallback
+ *   tree "[F32|F64@128]" and reports it in *used_fallback.
+ *   iters, resid, info, used_fallback: host pointers (may be NULL). Synchronous (one
+ *   device->host read of the residual per iteration).
+ */
+hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
+                    const double* dA, int lda, const double* dB, int ldb,
+                    double* dX, int ldx, int max_iter, double tol,
+                    int* iters, double* resid, int* info, int* used_fallback, void* stream);
+
+/*
+ * Relative backward error ||A - L L^T||_F / ||A||_F computed on the device in FP64
+ * (A symmetric from its lower triangle in dA; L from the lower triangle of dL).
+ * *out is a host double. Synchronous.
+ */
+hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda,
+                              const double* dL, int ldl, double* out, void* stream);
+
+/*
+ * Per-phase device times of the last hrp_potrf on this handle when timing is enabled
+ * (hrp_set_timing(h, 1)): ms[0]=leaf POTRF, [1]=TRSM (leaves+GEMMs), [2]=SYRK GEMMs,
+ * [3]=other. Returns the number of values written (<= n).
+ */
+hrp_status hrp_set_timing(hrp_handle* h, int enable);
+int hrp_get_timing(hrp_handle* h, double* ms, int n);
+
+/* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
+long long hrp_last_launch_count(const hrp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRP_H_ */

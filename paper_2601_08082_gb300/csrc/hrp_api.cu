@@ -1,0 +1,592 @@
+// C ABI of the HRP library and the host-side recursion scheduler.
+//
+// The scheduler walks Alg. 1 (Tree-POTRF_L), Alg. 2 (Tree-TRSM_{R,L,T}) and Alg. 3
+// (Tree-SYRK_L) on the host and enqueues one kernel per base case or GEMM on the caller's
+// stream, choosing each kernel by the precision the tree assigns to the node (Sec. 3.3):
+//   - leaf POTRF: FP64 or FP32 in shared memory (k_leaf.cu);
+//   - leaf TRSM: FP64 substitution, or FP32 through the inverse of the diagonal leaf;
+//   - GEMM at an F16 level: tcgen05 FP16 GEMM from the FP16 shadow (k_gemm_tc.cu),
+//     at F32/F64 levels a SIMT GEMM on the FP64 master (k_gemm_simt.cu).
+// Tree-SYRK is enqueued as ONE lower-triangle GEMM: every entry of C is produced by
+// exactly one GEMM (or leaf SYRK) of the recursion with the full inner dimension and the
+// node's precision, so the flattened launch performs the same arithmetic per entry.
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hrp_internal.cuh"
+
+struct hrp_handle_s {
+  int device = 0;
+  int last_arg = 0;
+  char last_err[512] = {0};
+  int* d_info = nullptr;       // internal info word
+  unsigned* d_err = nullptr;   // device error flags
+  int* d_ticket = nullptr;
+  int* d_flags = nullptr;
+  size_t flags_cap = 0;
+  int epoch = 1;
+  __half* shadow = nullptr;
+  size_t shadow_cap = 0;       // elements
+  float* w32 = nullptr;
+  size_t w32_cap = 0;          // elements
+  double* fact = nullptr;      // posv factor copy
+  size_t fact_cap = 0;
+  double* work = nullptr;      // posv residual/correction
+  size_t work_cap = 0;
+  double* d_norms = nullptr;   // 2 * 64 doubles
+  double* h_norms = nullptr;   // pinned host mirror
+  long long launches = 0;
+  bool timing = false;
+  double phase_ms[4] = {0, 0, 0, 0};
+};
+
+namespace hrp {
+namespace {
+
+hrp_status set_err(hrp_handle* h, hrp_status st, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->last_err, sizeof(h->last_err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+hrp_status bad_arg(hrp_handle* h, int pos, const char* what) {
+  if (h) h->last_arg = -pos;
+  return set_err(h, HRP_ERR_INVALID_ARG, "argument %d: %s", pos, what);
+}
+
+template <typename T>
+hrp_status ensure(hrp_handle* h, T** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return HRP_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (need == 0) return HRP_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), need * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_err(h, HRP_ERR_ALLOC, "cudaMalloc(%zu bytes) failed: %s", need * sizeof(T), cudaGetErrorString(e));
+  }
+  *cap = need;
+  return HRP_OK;
+}
+
+int split(int n) {
+  int q;
+  if (n >= 512) q = 128;
+  else if (n >= 32) q = 16;
+  else return n / 2;
+  int n1 = q * ((n + q) / (2 * q));
+  if (n1 <= 0 || n1 >= n) return n / 2;
+  return n1;
+}
+
+int node_prec(const hrp_tree* t, int depth, int n) {
+  if (t->inner_size > 0 && n <= t->inner_size) return t->inner;
+  int d = depth < t->depth ? depth : t->depth - 1;
+  return t->level[d];
+}
+
+hrp_status validate_tree(hrp_handle* h, const hrp_tree* t, int pos) {
+  if (!t) return bad_arg(h, pos, "tree is NULL");
+  if (t->depth < 1 || t->depth > HRP_MAX_DEPTH) return bad_arg(h, pos, "tree depth out of range");
+  for (int i = 0; i < t->depth; ++i)
+    if (t->level[i] < HRP_F64 || t->level[i] > HRP_F8E4M3) return bad_arg(h, pos, "bad precision in tree");
+  if (t->leaf < 1 || t->leaf > 128) return bad_arg(h, pos, "leaf must be in [1, 128]");
+  if (t->inner_size < 0) return bad_arg(h, pos, "inner_size < 0");
+  if (t->inner_size > 0 && t->inner != HRP_F64 && t->inner != HRP_F32) return bad_arg(h, pos, "inner must be F64 or F32");
+  int tl = t->trsm_leaf ? t->trsm_leaf : t->leaf;
+  if (tl < 1 || tl > t->leaf) return bad_arg(h, pos, "trsm_leaf must be in [1, leaf]");
+  int sl = t->syrk_leaf ? t->syrk_leaf : t->leaf;
+  if (sl < 1) return bad_arg(h, pos, "syrk_leaf < 0");
+  return HRP_OK;
+}
+
+bool tree_has(const hrp_tree* t, int prec) {
+  for (int i = 0; i < t->depth; ++i)
+    if (t->level[i] == prec) return true;
+  return t->inner_size > 0 && t->inner == prec;
+}
+
+// ------------------------------------------------------------------------------------
+// One factorization: the recursion of Alg. 1-3 turned into stream-ordered launches.
+// ------------------------------------------------------------------------------------
+struct Fact {
+  hrp_handle* h;
+  const hrp_tree* t;
+  double* A;
+  int lda;
+  int n;
+  int* info;
+  cudaStream_t s;
+  __half* shadow;       // null if no F16 level
+  int lds;
+  float* w32;           // null if every level is F64
+  bool tc;
+  std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
+  cudaError_t err = cudaSuccess;
+  long long launches = 0;
+
+  void chk(cudaError_t e) {
+    ++launches;
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  int tleaf() const { return t->trsm_leaf ? t->trsm_leaf : t->leaf; }
+
+  void leaf_potrf(int off, int nb, int p) {
+    float* W = nullptr;
+    if (w32) {
+      W = w32 + (size_t)off * 128;
+      leaves[off] = nb;
+    }
+    chk(launch_potrf_leaf(A + (size_t)off * lda + off, lda, nb, off, p == HRP_F64, p == HRP_F16, W, 128, info, s));
+  }
+
+  void leaf_trsm(int r0, int m, int c0, int nc, int p) {
+    double* Ab = A;
+    __half* sh = shadow;
+    if (p == HRP_F64) {
+      chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
+      return;
+    }
+    auto it = leaves.find(c0);
+    if (w32 && it != leaves.end() && it->second == nc) {
+      chk(launch_trsm_leaf32(Ab, lda, r0, m, c0, nc, w32 + (size_t)c0 * 128, 128, sh, lds, info, s));
+    } else {
+      chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
+    }
+  }
+
+  // C = A[r0:r0+m, c0:c0+nd] -= X Y^T, X = A[r0:r0+m, k0:k0+k], Y = A[c0:c0+nd, k0:k0+k]
+  void gemm(int p, int r0, int m, int c0, int nd, int k0, int k, bool lower) {
+    if (m <= 0 || nd <= 0 || k <= 0) return;
+    double* C = A + (size_t)c0 * lda + r0;
+    const double* X = A + (size_t)k0 * lda + r0;
+    const double* Y = A + (size_t)k0 * lda + c0;
+    switch (p) {
+      case HRP_F64: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F64, lower, s)); break;
+      case HRP_F32: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F32, lower, s)); break;
+      case HRP_F16:
+        if (tc && shadow && (k0 % 8) == 0 && k >= 16)
+          chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s));
+        else
+          chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F16, lower, s));
+        break;
+      default:
+        if (err == cudaSuccess) err = cudaErrorNotSupported;
+    }
+  }
+
+  // Alg. 2: B = A[r0:r0+m, c0:c0+nc] <- B L^{-T}, L = A[c0:c0+nc, c0:c0+nc]
+  void trsm(int r0, int m, int c0, int nc, int p) {
+    if (std::min(m, nc) <= tleaf()) {
+      leaf_trsm(r0, m, c0, nc, p);
+      return;
+    }
+    int n1 = split(nc);
+    trsm(r0, m, c0, n1, p);
+    gemm(p, r0, m, c0 + n1, nc - n1, c0, n1, false);   // B2 -= B1 L21^T
+    trsm(r0, m, c0 + n1, nc - n1, p);
+  }
+
+  // Alg. 3 flattened: C = A[c0:c0+nc, c0:c0+nc] (lower) -= X X^T, X = A[c0:c0+nc, a0:a0+k]
+  void syrk(int c0, int nc, int a0, int k, int p) { gemm(p, c0, nc, c0, nc, a0, k, true); }
+
+  // Alg. 1
+  void potrf(int off, int nb, int depth) {
+    if (nb <= 0) return;
+    int p = node_prec(t, depth, nb);
+    if (nb <= t->leaf) {
+      leaf_potrf(off, nb, p);
+      return;
+    }
+    int n1 = split(nb), n2 = nb - n1;
+    potrf(off, n1, depth + 1);
+    trsm(off + n1, n2, off, n1, p);
+    syrk(off + n1, n2, off, n1, p);
+    potrf(off + n1, n2, depth + 1);
+  }
+};
+
+hrp_status cuda_status(hrp_handle* h, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return HRP_OK;
+  if (e == cudaErrorNotSupported) return set_err(h, HRP_ERR_UNSUPPORTED, "%s: precision not supported by this build", where);
+  return set_err(h, HRP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s) {
+  hrp_status st;
+  if (tree_has(t, HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "FP8 levels are not built in this version");
+  Fact f{};
+  f.h = h;
+  f.t = t;
+  f.A = dA;
+  f.lda = lda;
+  f.n = n;
+  f.info = d_info;
+  f.s = s;
+  f.tc = tc_gemm_supported();
+  f.shadow = nullptr;
+  f.lds = 0;
+  f.w32 = nullptr;
+  if (tree_has(t, HRP_F16)) {
+    f.lds = (n + 63) / 64 * 64;
+    if ((st = ensure(h, &h->shadow, &h->shadow_cap, (size_t)n * f.lds)) != HRP_OK) return st;
+    f.shadow = h->shadow;
+  }
+  if (tree_has(t, HRP_F32) || tree_has(t, HRP_F16)) {
+    if ((st = ensure(h, &h->w32, &h->w32_cap, (size_t)n * 128 + 128 * 128)) != HRP_OK) return st;
+    f.w32 = h->w32;
+  }
+  f.chk(launch_fill_int(d_info, INT_MAX, 1, s));
+  f.potrf(0, n, 0);
+  f.chk(launch_finalize_info(d_info, s));
+  h->launches = f.launches;
+  return cuda_status(h, f.err, "hrp_potrf");
+}
+
+hrp_status check_dev_err(hrp_handle* h, cudaStream_t s) {
+  unsigned e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_status(h, ce, "device status");
+  if (e & DEV_ERR_TIMEOUT) {
+    cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s);
+    return set_err(h, HRP_ERR_TIMEOUT, "a bounded device wait expired");
+  }
+  return HRP_OK;
+}
+
+}  // namespace
+}  // namespace hrp
+
+using namespace hrp;
+
+extern "C" {
+
+const char* hrp_status_string(hrp_status s) {
+  switch (s) {
+    case HRP_OK: return "HRP_OK";
+    case HRP_ERR_INVALID_ARG: return "HRP_ERR_INVALID_ARG";
+    case HRP_ERR_NOT_SPD: return "HRP_ERR_NOT_SPD";
+    case HRP_ERR_NO_CONVERGENCE: return "HRP_ERR_NO_CONVERGENCE";
+    case HRP_ERR_ALLOC: return "HRP_ERR_ALLOC";
+    case HRP_ERR_CUDA: return "HRP_ERR_CUDA";
+    case HRP_ERR_TIMEOUT: return "HRP_ERR_TIMEOUT";
+    case HRP_ERR_UNSUPPORTED: return "HRP_ERR_UNSUPPORTED";
+    case HRP_ERR_RANGE: return "HRP_ERR_RANGE";
+  }
+  return "HRP_ERR_UNKNOWN";
+}
+
+hrp_status hrp_create(hrp_handle** out, int device) {
+  if (!out) return HRP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return HRP_ERR_CUDA;
+  if (device < 0 || device >= count) return HRP_ERR_INVALID_ARG;
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return HRP_ERR_CUDA;
+  hrp_handle* h = new (std::nothrow) hrp_handle_s();
+  if (!h) return HRP_ERR_ALLOC;
+  h->device = device;
+  bool ok = cudaMalloc(&h->d_info, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_err, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&h->d_ticket, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_norms, sizeof(double) * 128) == cudaSuccess &&
+            cudaMallocHost(&h->h_norms, sizeof(double) * 128) == cudaSuccess;
+  if (!ok || cudaMemset(h->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+    hrp_destroy(h);
+    return HRP_ERR_ALLOC;
+  }
+  *out = h;
+  return HRP_OK;
+}
+
+hrp_status hrp_destroy(hrp_handle* h) {
+  if (!h) return HRP_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  cudaFree(h->d_info);
+  cudaFree(h->d_err);
+  cudaFree(h->d_ticket);
+  cudaFree(h->d_flags);
+  cudaFree(h->shadow);
+  cudaFree(h->w32);
+  cudaFree(h->fact);
+  cudaFree(h->work);
+  cudaFree(h->d_norms);
+  if (h->h_norms) cudaFreeHost(h->h_norms);
+  delete h;
+  return HRP_OK;
+}
+
+int hrp_last_arg(const hrp_handle* h) { return h ? h->last_arg : 0; }
+const char* hrp_last_error(const hrp_handle* h) { return h ? h->last_err : ""; }
+
+hrp_status hrp_tree_parse(const char* spec, int leaf, hrp_tree* out) {
+  if (!spec || !out) return HRP_ERR_INVALID_ARG;
+  hrp_tree t;
+  memset(&t, 0, sizeof(t));
+  t.leaf = leaf;
+  t.scale_block = 128;
+  const char* p = spec;
+  while (*p == ' ') ++p;
+  if (*p != '[') return HRP_ERR_INVALID_ARG;
+  ++p;
+  bool inner_part = false;
+  while (true) {
+    while (*p == ' ' || *p == ',') ++p;
+    if (*p == ']') { ++p; break; }
+    if (*p == '|') { inner_part = true; ++p; continue; }
+    int prec;
+    if (!strncmp(p, "F64", 3)) { prec = HRP_F64; p += 3; }
+    else if (!strncmp(p, "F32", 3)) { prec = HRP_F32; p += 3; }
+    else if (!strncmp(p, "F16", 3)) { prec = HRP_F16; p += 3; }
+    else if (!strncmp(p, "F8E4M3", 6)) { prec = HRP_F8E4M3; p += 6; }
+    else if (!strncmp(p, "E4M3", 4)) { prec = HRP_F8E4M3; p += 4; }
+    else if (!strncmp(p, "F8", 2)) { prec = HRP_F8E4M3; p += 2; }
+    else return HRP_ERR_INVALID_ARG;
+    if (inner_part) {
+      while (*p == ' ') ++p;
+      if (*p != '@' || (prec != HRP_F64 && prec != HRP_F32)) return HRP_ERR_INVALID_ARG;
+      ++p;
+      char* endp = nullptr;
+      long v = strtol(p, &endp, 10);
+      if (endp == p || v <= 0) return HRP_ERR_INVALID_ARG;
+      p = endp;
+      t.inner = prec;
+      t.inner_size = (int)v;
+      while (*p == ' ') ++p;
+      if (*p != ']') return HRP_ERR_INVALID_ARG;
+      continue;
+    }
+    if (t.depth >= HRP_MAX_DEPTH) return HRP_ERR_INVALID_ARG;
+    t.level[t.depth++] = prec;
+  }
+  while (*p == ' ') ++p;
+  if (*p != '\0' || t.depth == 0) return HRP_ERR_INVALID_ARG;
+  *out = t;
+  return HRP_OK;
+}
+
+int hrp_tree_format(const hrp_tree* t, char* buf, size_t len) {
+  static const char* names[] = {"F64", "F32", "F16", "F8"};
+  std::string s = "[";
+  for (int i = 0; t && i < t->depth; ++i) {
+    if (i) s += ",";
+    int l = t->level[i];
+    s += (l >= 0 && l <= 3) ? names[l] : "?";
+  }
+  if (t && t->inner_size > 0) {
+    s += "|";
+    s += (t->inner >= 0 && t->inner <= 3) ? names[t->inner] : "?";
+    s += "@" + std::to_string(t->inner_size);
+  }
+  s += "]";
+  if (buf && len) {
+    strncpy(buf, s.c_str(), len - 1);
+    buf[len - 1] = '\0';
+  }
+  return (int)s.size();
+}
+
+hrp_status hrp_potrf_async(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda, int* d_info, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (n < 0) return bad_arg(h, 3, "n < 0");
+  if (n > 0 && !dA) return bad_arg(h, 4, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 5, "lda < max(1, n)");
+  if (!d_info) return bad_arg(h, 6, "d_info is NULL");
+  cudaSetDevice(h->device);
+  return potrf_enqueue(h, tree, n, dA, lda, d_info, static_cast<cudaStream_t>(stream));
+}
+
+hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda, int* info, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (n < 0) return bad_arg(h, 3, "n < 0");
+  if (n > 0 && !dA) return bad_arg(h, 4, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 5, "lda < max(1, n)");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = potrf_enqueue(h, tree, n, dA, lda, h->d_info, s);
+  if (st != HRP_OK) return st;
+  int hinfo = 0;
+  cudaError_t e = cudaMemcpyAsync(&hinfo, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_potrf");
+  if ((st = check_dev_err(h, s)) != HRP_OK) return st;
+  if (info) *info = hinfo;
+  if (hinfo) return set_err(h, HRP_ERR_NOT_SPD, "leading minor of order %d is not positive definite", hinfo);
+  return HRP_OK;
+}
+
+static hrp_status potrs_impl(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
+                             bool fp32, cudaStream_t s) {
+  hrp_status st;
+  size_t nb = (size_t)(n + 63) / 64;
+  int* old_flags = h->d_flags;
+  size_t old_cap = h->flags_cap;
+  if ((st = ensure(h, &h->d_flags, &h->flags_cap, nb)) != HRP_OK) return st;
+  if (h->d_flags != old_flags || h->flags_cap != old_cap) {
+    // fresh flags must not hold a value equal to a future epoch
+    cudaError_t me = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->flags_cap, s);
+    if (me != cudaSuccess) return cuda_status(h, me, "hrp_potrs");
+    h->epoch = 1;
+  }
+  int ne = potrs_epochs(nrhs);
+  if (h->epoch > INT_MAX - 1024) {
+    cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->flags_cap, s);
+    h->epoch = 1;
+  }
+  int ep = h->epoch;
+  h->epoch += ne;
+  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->d_ticket, h->d_flags, ep, h->d_err, s);
+  h->launches += 2 * ne;
+  return cuda_status(h, e, "hrp_potrs");
+}
+
+hrp_status hrp_potrs(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, double* dB, int ldb, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (n < 0) return bad_arg(h, 2, "n < 0");
+  if (nrhs < 0) return bad_arg(h, 3, "nrhs < 0");
+  if (n > 0 && !dL) return bad_arg(h, 4, "dL is NULL");
+  if (ldl < (n > 1 ? n : 1)) return bad_arg(h, 5, "ldl < max(1, n)");
+  if (n > 0 && nrhs > 0 && !dB) return bad_arg(h, 6, "dB is NULL");
+  if (ldb < (n > 1 ? n : 1)) return bad_arg(h, 7, "ldb < max(1, n)");
+  cudaSetDevice(h->device);
+  h->launches = 0;
+  return potrs_impl(h, n, nrhs, dL, ldl, dB, ldb, false, static_cast<cudaStream_t>(stream));
+}
+
+hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const double* dA, int lda, const double* dB,
+                    int ldb, double* dX, int ldx, int max_iter, double tol, int* iters, double* resid, int* info,
+                    int* used_fallback, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (n < 0) return bad_arg(h, 3, "n < 0");
+  if (nrhs < 0 || nrhs > 64) return bad_arg(h, 4, "nrhs must be in [0, 64]");
+  if (n > 0 && !dA) return bad_arg(h, 5, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 6, "lda < max(1, n)");
+  if (n > 0 && nrhs > 0 && !dB) return bad_arg(h, 7, "dB is NULL");
+  if (ldb < (n > 1 ? n : 1)) return bad_arg(h, 8, "ldb < max(1, n)");
+  if (n > 0 && nrhs > 0 && !dX) return bad_arg(h, 9, "dX is NULL");
+  if (ldx < (n > 1 ? n : 1)) return bad_arg(h, 10, "ldx < max(1, n)");
+  if (max_iter < 0) return bad_arg(h, 11, "max_iter < 0");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (iters) *iters = 0;
+  if (resid) *resid = 0.0;
+  if (info) *info = 0;
+  if (used_fallback) *used_fallback = 0;
+  if (n == 0 || nrhs == 0) return HRP_OK;
+  if ((st = ensure(h, &h->fact, &h->fact_cap, (size_t)n * n)) != HRP_OK) return st;
+  if ((st = ensure(h, &h->work, &h->work_cap, (size_t)n * nrhs)) != HRP_OK) return st;
+  long long total_launches = 0;
+  cudaError_t e;
+  // factor a copy of A (A itself is kept for the residual)
+  hrp_tree fallback;
+  hrp_tree_parse("[F32|F64@128]", 128, &fallback);
+  const hrp_tree* use = tree;
+  int hinfo = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if ((e = launch_copy_lower(h->fact, n, dA, lda, n, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    if ((st = potrf_enqueue(h, use, n, h->fact, n, h->d_info, s)) != HRP_OK) return st;
+    total_launches += h->launches + 1;
+    e = cudaMemcpyAsync(&hinfo, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    if (hinfo == 0) break;
+    if (attempt == 0) {
+      use = &fallback;
+      if (used_fallback) *used_fallback = 1;
+    }
+  }
+  if (info) *info = hinfo;
+  if (hinfo) return set_err(h, HRP_ERR_NOT_SPD, "factorization failed at column %d (fallback tree too)", hinfo);
+  // X0 = POTRS(B) in FP32
+  if ((e = launch_copy_matrix(dX, ldx, dB, ldb, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+  if ((st = potrs_impl(h, n, nrhs, h->fact, n, dX, ldx, true, s)) != HRP_OK) return st;
+  int it = 0;
+  double worst = 0.0;
+  while (true) {
+    if ((e = launch_residual(dA, lda, dX, ldx, dB, ldb, h->work, n, n, nrhs, s)) != cudaSuccess)
+      return cuda_status(h, e, "hrp_posv residual");
+    if ((e = launch_col_norms2(h->work, n, dB, ldb, n, nrhs, h->d_norms, s)) != cudaSuccess)
+      return cuda_status(h, e, "hrp_posv norms");
+    e = cudaMemcpyAsync(h->h_norms, h->d_norms, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      double rb = h->h_norms[nrhs + c] > 0 ? sqrt(h->h_norms[c] / h->h_norms[nrhs + c]) : sqrt(h->h_norms[c]);
+      if (!(rb <= worst)) worst = rb;   // NaN propagates
+    }
+    if (worst <= tol || it >= max_iter) break;
+    if ((st = potrs_impl(h, n, nrhs, h->fact, n, h->work, n, true, s)) != HRP_OK) return st;
+    if ((e = launch_axpy_matrix(dX, ldx, h->work, n, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (resid) *resid = worst;
+  if ((st = check_dev_err(h, s)) != HRP_OK) return st;
+  if (!(worst <= tol)) return set_err(h, HRP_ERR_NO_CONVERGENCE, "residual %.3e after %d corrections", worst, it);
+  return HRP_OK;
+}
+
+hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda, const double* dL, int ldl, double* out,
+                              void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (n < 0) return bad_arg(h, 2, "n < 0");
+  if (n > 0 && !dA) return bad_arg(h, 3, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 4, "lda < max(1, n)");
+  if (n > 0 && !dL) return bad_arg(h, 5, "dL is NULL");
+  if (ldl < (n > 1 ? n : 1)) return bad_arg(h, 6, "ldl < max(1, n)");
+  if (!out) return bad_arg(h, 7, "out is NULL");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  *out = 0.0;
+  if (n == 0) return HRP_OK;
+  cudaError_t e = cudaMemsetAsync(h->d_norms, 0, 2 * sizeof(double), s);
+  if (e == cudaSuccess) e = launch_backward_error(dA, lda, dL, ldl, n, h->d_norms, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_norms, h->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_backward_error");
+  *out = h->h_norms[1] > 0 ? sqrt(h->h_norms[0] / h->h_norms[1]) : sqrt(h->h_norms[0]);
+  return HRP_OK;
+}
+
+hrp_status hrp_set_timing(hrp_handle* h, int enable) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->timing = enable != 0;
+  return HRP_OK;
+}
+
+int hrp_get_timing(hrp_handle* h, double* ms, int n) {
+  if (!h || !ms) return 0;
+  int k = n < 4 ? n : 4;
+  for (int i = 0; i < k; ++i) ms[i] = h->phase_ms[i];
+  return k;
+}
+
+long long hrp_last_launch_count(const hrp_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the HRP CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/hrp.h"
+
+namespace hrp {
+
+// Error flags written by kernels into the handle's device status word.
+enum : unsigned {
+  DEV_ERR_TIMEOUT = 1u,     // a bounded wait expired
+  DEV_ERR_BOUNDS = 2u,      // a checked index fell outside its buffer
+};
+
+// Bounded device waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitTimeoutNs = 2000ull * 1000ull * 1000ull;
+
+// Rounding applied to GEMM operands read from the FP64 master.
+enum class OpRound : int { F64 = 0, F32 = 1, F16 = 2 };
+
+// ---------------- leaf kernels (k_leaf.cu) ----------------
+// Leaf POTRF of the n x n diagonal block at A (ld), n <= 128, computed in FP64
+// (compute64 = true) or FP32; round16: round input and output to FP16 (F16 leaf).
+// If W32 != nullptr also writes the FP32 inverse of the (FP32-rounded) factor,
+// column-major n x n with leading dimension ldw.  info: device int, atomicMin of the
+// 1-based global column (col0 + k + 1) of the first failing pivot (INT_MAX = none).
+cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64, bool round16,
+                              float* W32, int ldw, int* info, cudaStream_t s);
+
+// Leaf TRSM B <- B L^{-T} with B = A[r0.., c0..] (m x nc) and L = A[c0.., c0..] (nc x nc),
+// in FP64 by substitution.  shadow16 (row-major, lds) receives FP16(X) if non-null.
+cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
+                               __half* shadow16, int lds, const int* info, cudaStream_t s);
+// Same in FP32 using the precomputed FP32 inverse W (nc x nc lower, ldw) of the block:
+// X = fl32(B) * W^T, result stored in FP64.
+cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
+                               const float* W, int ldw, __half* shadow16, int lds,
+                               const int* info, cudaStream_t s);
+// FP32 substitution variant (no inverse), for blocks whose inverse is not available.
+cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
+                                     __half* shadow16, int lds, const int* info, cudaStream_t s);
+
+// ---------------- SIMT GEMM (k_gemm_simt.cu) ----------------
+// C[m x n] -= X[m x k] * Y[n x k]^T, all FP64 column-major views of the master, with
+// operands rounded per `rnd` and accumulated in FP64 (rnd == F64) or FP32.  lower: C is a
+// diagonal block, only entries with row >= col (in C's coordinates) are updated.
+cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const double* Y, int ldy,
+                             int m, int n, int k, OpRound rnd, bool lower, cudaStream_t s);
+
+// ---------------- tcgen05 FP16 GEMM (k_gemm_tc.cu) ----------------
+// C[m x n] (FP64 master, column-major) -= scale * X Y^T with X = S[xr0.., k0..] (m x k) and
+// Y = S[yr0.., k0..] (n x k) read from the row-major FP16 shadow S (lds), FP32 accumulation
+// in TMEM.  Requires k0 % 8 == 0 and lds % 8 == 0.
+bool tc_gemm_supported();
+cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds,
+                               int xr0, int yr0, int k0, int m, int n, int k, bool lower,
+                               double scale, unsigned* dev_err, cudaStream_t s);
+
+// ---------------- POTRS (k_potrs.cu) ----------------
+// B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 or (fp32)
+// in FP32 on FP32-rounded L and B.  ticket: device int scratch; flags: device ints, one per
+// 64-row block; consumes potrs_epochs(nrhs) consecutive epoch values starting at `epoch`.
+cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32,
+                         int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s);
+int potrs_epochs(int nrhs);
+
+// ---------------- utilities (k_util.cu) ----------------
+cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s);
+cudaError_t launch_finalize_info(int* info, cudaStream_t s);
+cudaError_t launch_copy_lower(double* dst, int ldd, const double* src, int lds, int n, cudaStream_t s);
+cudaError_t launch_copy_matrix(double* dst, int ldd, const double* src, int lds, int m, int n, cudaStream_t s);
+// R = B - A X with A symmetric from its lower triangle (FP64). R, B, X: n x nrhs.
+cudaError_t launch_residual(const double* A, int lda, const double* X, int ldx, const double* B, int ldb,
+                            double* R, int ldr, int n, int nrhs, cudaStream_t s);
+// out[j] = ||R[:, j]||_2^2 and out[nrhs + j] = ||B[:, j]||_2^2 (accumulated with atomics; zeroed here)
+cudaError_t launch_col_norms2(const double* R, int ldr, const double* B, int ldb, int n, int nrhs,
+                              double* out, cudaStream_t s);
+cudaError_t launch_axpy_matrix(double* X, int ldx, const double* D, int ldd, int n, int nrhs, cudaStream_t s);
+// out[0] += sum over lower triangle (sym weights) of (A - L L^T)^2, out[1] += ||A||_F^2
+cudaError_t launch_backward_error(const double* A, int lda, const double* L, int ldl, int n,
+                                  double* out, cudaStream_t s);
+// sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
+cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
+
+}  // namespace hrp

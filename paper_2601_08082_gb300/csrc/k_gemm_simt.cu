@@ -1,0 +1,94 @@
+// SIMT GEMM for the FP64 and FP32 levels of the tree (and the FP16-operand fallback):
+// C -= X Y^T on column-major views of the FP64 master.  This is the update
+// "B2 <- B2 - B1 L21^T" of Alg. 2 and "C21 <- C21 - A2 A1^T" of Alg. 3 (alpha = -1,
+// beta = 1 in Alg. 1); with `lower` it is the leaf SYRK of Alg. 3 on a diagonal block.
+#include "hrp_internal.cuh"
+
+namespace hrp {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <int RND> struct Acc { using T = float; };
+template <> struct Acc<0> { using T = double; };
+
+template <int RND>
+__device__ __forceinline__ typename Acc<RND>::T cvt_op(double x) {
+  if constexpr (RND == 0) return x;
+  else if constexpr (RND == 1) return __double2float_rn(x);
+  else return __half2float(__double2half(x));
+}
+
+// 256 threads; thread (tx, ty) = (tid % 16, tid / 16) owns rows tx + 16 i and columns ty + 16 j.
+template <int RND>
+__global__ void __launch_bounds__(256)
+gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, int ldx,
+                 const double* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
+  using T = typename Acc<RND>::T;
+  __shared__ T Xs[BK][BM + 1];
+  __shared__ T Ys[BK][BN + 1];
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (lower && m0 + BM - 1 < n0) return;          // tile strictly above the diagonal
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+
+  for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < (BM * BK) / 256; ++q) {
+      int e = tid + 256 * q;
+      int r = e % BM, kk = e / BM;
+      int gr = m0 + r, gk = k0 + kk;
+      Xs[kk][r] = (gr < m && gk < k) ? cvt_op<RND>(X[(size_t)gk * ldx + gr]) : (T)0;
+      int gc = n0 + r;
+      Ys[kk][r] = (gc < n && gk < k) ? cvt_op<RND>(Y[(size_t)gk * ldy + gc]) : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Xs[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Ys[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int gc = n0 + ty + 16 * j;
+    if (gc >= n) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gr = m0 + tx + 16 * i;
+      if (gr >= m) continue;
+      if (lower && gr < gc) continue;
+      double* p = C + (size_t)gc * ldc + gr;
+      *p = *p - (double)acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const double* Y, int ldy,
+                             int m, int n, int k, OpRound rnd, bool lower, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  switch (rnd) {
+    case OpRound::F64: gemm_simt_kernel<0><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
+    case OpRound::F32: gemm_simt_kernel<1><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
+    case OpRound::F16: gemm_simt_kernel<2><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hrp

@@ -1,0 +1,286 @@
+// FP16 tensor-core GEMM for the low-precision off-diagonal levels (Sec. 3.3):
+// C_master -= scale * X Y^T with X, Y read from the row-major FP16 shadow of L by TMA,
+// multiplied by tcgen05.mma (kind::f16, FP32 accumulation in TMEM) and applied to the
+// FP64 master in the epilogue.  This is the "GemmEx" update of Alg. 2 line "B2 <- B2 -
+// B1 L21^T" and Alg. 3 line "C21 <- beta C21 + alpha A2 A1^T" at an FP16 level; with
+// `lower` it is the leaf SYRK of Alg. 3 (entries above the diagonal are skipped, and
+// tiles entirely above it are never computed).
+//
+// One CTA computes one 128 x BN tile.  Warp roles: warp 0 issues TMA loads into a
+// STAGES-deep ring of 128B-swizzled K-major tiles, warp 1 owns the TMEM allocation and
+// issues the MMAs (one elected thread), warps 2-5 read the accumulator back with
+// tcgen05.ld and update the master.  Every mbarrier wait is bounded by %globaltimer and
+// reports DEV_ERR_TIMEOUT instead of spinning forever.
+#include <cstdio>
+
+#include "hrp_internal.cuh"
+
+namespace hrp {
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;          // 64 fp16 = one 128-byte swizzle row
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 192;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete; false after kWaitTimeoutNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  if (mbar_try_wait(addr, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(addr, parity)) return true;
+    if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128B swizzle,
+// 8-row core-matrix groups 1024 bytes apart (SBO), descriptor version 1 (bits 46-48).
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16 (0), both
+// K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+struct TcLayout {
+  static constexpr size_t a_stage = (size_t)TC_BM * TC_BK * 2;
+  static constexpr size_t b_stage = (size_t)BN * TC_BK * 2;
+  static constexpr size_t bars = 1024;  // barriers + tmem slot, padded
+  static constexpr size_t bytes = 1024 /*alignment slack*/ + TC_STAGES * (a_stage + b_stage) + bars;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                   double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
+                   unsigned* __restrict__ err) {
+  using Lay = TcLayout<BN>;
+  extern __shared__ unsigned char smem_raw[];
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+  if (lower && m0 + TC_BM - 1 < n0) return;          // tile strictly above the diagonal
+
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_STAGES * Lay::a_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * Lay::b_stage);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accum = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (k + TC_BK - 1) / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"((uint32_t)BN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (kb / TC_STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1)) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(Lay::a_stage + Lay::b_stage));
+        tma_load_2d(sA + s * Lay::a_stage, &tmX, kb * TC_BK, m0, &full[s]);
+        tma_load_2d(sB + s * Lay::b_stage, &tmY, kb * TC_BK, n0, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (kb / TC_STAGES) & 1;
+        if (!mbar_wait(&full[s], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
+        tc_fence_after();
+        const uint64_t ad = sw128_desc(sA + s * Lay::a_stage);
+        const uint64_t bd = sw128_desc(sB + s * Lay::b_stage);
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk)      // K = 16 per instruction: +32 bytes
+          mma_f16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(accum);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its accessible sub-partition)
+    const int q = warp & 3;
+    const bool ok = mbar_wait(accum, 0);
+    if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+    tc_fence_after();
+    if (ok) {
+      const int row = m0 + q * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= n) break;                       // uniform across the warp
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        if (row < m) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < n && (!lower || row >= col)) {
+              double* p = C + (size_t)col * ldc + row;
+              *p = *p - scale * (double)__uint_as_float(r[j]);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+  }
+}
+
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled_t get_encode() {
+  static PFN_encodeTiled_t fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+  }
+  return fn;
+}
+
+// 2-D map over a rows x cols block of a row-major fp16 matrix (leading dimension ld elements),
+// box = box_rows x 64 columns, 128B swizzle, zero fill outside the block.
+bool make_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld, int box_rows) {
+  PFN_encodeTiled_t enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n, int k,
+                      bool lower, double scale, unsigned* dev_err, cudaStream_t s) {
+  CUtensorMap mx, my;
+  if (!make_map(&mx, S + (size_t)xr0 * lds + k0, m, k, lds, TC_BM)) return cudaErrorInvalidValue;
+  if (!make_map(&my, S + (size_t)yr0 * lds + k0, n, k, lds, BN)) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcLayout<BN>::bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((m + TC_BM - 1) / TC_BM, (n + BN - 1) / BN);
+  gemm_f16_tc_kernel<BN><<<grid, TC_THREADS, TcLayout<BN>::bytes, s>>>(mx, my, C, ldc, m, n, k, lower ? 1 : 0,
+                                                                        scale, dev_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_supported() { return get_encode() != nullptr; }
+
+cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n,
+                               int k, bool lower, double scale, unsigned* dev_err, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if ((k0 % 8) != 0 || (lds % 8) != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0) return cudaErrorInvalidValue;
+  if (n <= 128) return launch_bn<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+  return launch_bn<256>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+}
+
+}  // namespace hrp

@@ -1,0 +1,248 @@
+// Small device utilities of the solver: info handling, copies, the FP64 residual of the
+// refinement loop (R = B - A X with A read once from its lower triangle), column norms,
+// and the FP64 backward error ||A - L L^T||_F / ||A||_F (Sec. 4.2 accuracy metric).
+#include <climits>
+
+#include "hrp_internal.cuh"
+
+namespace hrp {
+namespace {
+
+__global__ void fill_int_kernel(int* p, int v, int count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) p[i] = v;
+}
+__global__ void finalize_info_kernel(int* info) {
+  if (*info == INT_MAX) *info = 0;
+}
+__global__ void copy_lower_kernel(double* dst, int ldd, const double* src, int lds, int n) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)n * n;
+  for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    if (i >= j) dst[(size_t)j * ldd + i] = src[(size_t)j * lds + i];
+  }
+}
+__global__ void copy_matrix_kernel(double* dst, int ldd, const double* src, int lds, int m, int n) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)m * n;
+  for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % m), j = (int)(idx / m);
+    dst[(size_t)j * ldd + i] = src[(size_t)j * lds + i];
+  }
+}
+__global__ void axpy_matrix_kernel(double* X, int ldx, const double* D, int ldd, int n, int nrhs) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)n * nrhs;
+  for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    X[(size_t)j * ldx + i] += D[(size_t)j * ldd + i];
+  }
+}
+
+// ---- residual R -= A X over lower-triangle tiles (R preset to B) ----
+constexpr int RT = 64;
+constexpr int RNRHS = 16;
+
+__device__ __forceinline__ void tri_index(long long t, int& I, int& J) {
+  long long i = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  I = (int)i;
+  J = (int)(t - i * (i + 1) / 2);
+}
+
+__global__ void __launch_bounds__(256)
+residual_tile_kernel(const double* __restrict__ A, int lda, const double* __restrict__ X, int ldx,
+                     double* __restrict__ R, int ldr, int n, int nrhs) {
+  __shared__ double As[RT][RT + 1];
+  __shared__ double xI[RNRHS][RT];
+  __shared__ double xJ[RNRHS][RT];
+  int I, J;
+  tri_index(blockIdx.x, I, J);
+  const int I0 = I * RT, J0 = J * RT;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < RT * RT; idx += 256) {
+    int i = idx % RT, j = idx / RT;
+    int gi = I0 + i, gj = J0 + j;
+    As[i][j] = (gi < n && gj < n && gi >= gj) ? A[(size_t)gj * lda + gi] : 0.0;
+  }
+  for (int idx = tid; idx < RT * nrhs; idx += 256) {
+    int i = idx % RT, c = idx / RT;
+    xI[c][i] = (I0 + i < n) ? X[(size_t)c * ldx + I0 + i] : 0.0;
+    xJ[c][i] = (J0 + i < n) ? X[(size_t)c * ldx + J0 + i] : 0.0;
+  }
+  __syncthreads();
+  const int i = tid % RT, g = tid / RT;          // 4 groups of right-hand sides
+  for (int c = g; c < nrhs; c += 4) {
+    // row i of block I: sum_j A(I0+i, J0+j) x(J0+j), using symmetry inside a diagonal tile
+    double y = 0.0;
+    if (I == J) {
+      for (int j = 0; j < RT; ++j) y += (j <= i ? As[i][j] : As[j][i]) * xJ[c][j];
+    } else {
+      for (int j = 0; j < RT; ++j) y += As[i][j] * xJ[c][j];
+    }
+    if (I0 + i < n) atomicAdd(R + (size_t)c * ldr + I0 + i, -y);
+    if (I != J) {
+      double z = 0.0;                          // row i of block J: sum_r A(I0+r, J0+i) x(I0+r)
+      for (int r = 0; r < RT; ++r) z += As[r][i] * xI[c][r];
+      if (J0 + i < n) atomicAdd(R + (size_t)c * ldr + J0 + i, -z);
+    }
+  }
+}
+
+__global__ void col_norms2_kernel(const double* R, int ldr, const double* B, int ldb, int n, int nrhs, double* out) {
+  const int c = blockIdx.y;
+  double sr = 0.0, sb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double r = R[(size_t)c * ldr + i], b = B[(size_t)c * ldb + i];
+    sr += r * r;
+    sb += b * b;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out + c, sr);
+    atomicAdd(out + nrhs + c, sb);
+  }
+}
+
+// ---- backward error: tiles (I >= J) of L L^T in FP64, 64 x 64, BK = 16 ----
+__global__ void __launch_bounds__(256)
+backward_error_kernel(const double* __restrict__ A, int lda, const double* __restrict__ L, int ldl, int n,
+                      double* __restrict__ out) {
+  __shared__ double Xs[16][65];
+  __shared__ double Ys[16][65];
+  __shared__ double red[2][8];
+  int I, J;
+  tri_index(blockIdx.x, I, J);
+  const int m0 = I * 64, n0 = J * 64;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4] = {};
+  const int kend = min(n, n0 + 64);             // L(j, k) = 0 for k > j
+  for (int k0 = 0; k0 < kend; k0 += 16) {
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int r = e % 64, kk = e / 64;
+      int gk = k0 + kk;
+      int gr = m0 + r, gc = n0 + r;
+      Xs[kk][r] = (gr < n && gk <= gr) ? L[(size_t)gk * ldl + gr] : 0.0;
+      Ys[kk][r] = (gc < n && gk <= gc) ? L[(size_t)gk * ldl + gc] : 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+      for (int i = 0; i < 4; ++i) a[i] = Xs[kk][tx + 16 * i];
+      for (int j = 0; j < 4; ++j) b[j] = Ys[kk][ty + 16 * j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double se = 0.0, sa = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int gr = m0 + tx + 16 * i, gc = n0 + ty + 16 * j;
+      if (gr < n && gc < n && gr >= gc) {
+        double a = A[(size_t)gc * lda + gr];
+        double d = a - acc[i][j];
+        double w = (gr == gc) ? 1.0 : 2.0;
+        se += w * d * d;
+        sa += w * a * a;
+      }
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if ((tid & 31) == 0) { red[0][tid >> 5] = se; red[1][tid >> 5] = sa; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; }
+    atomicAdd(out, a);
+    atomicAdd(out + 1, b);
+  }
+}
+
+__global__ void diag_check_kernel(const double* A, int lda, int n, double limit, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double d = A[(size_t)i * lda + i];
+    if (!(d <= limit)) atomicExch(flag, 1);
+  }
+}
+
+int grid_for(size_t work, int threads) {
+  size_t g = (work + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  fill_int_kernel<<<(count + 255) / 256, 256, 0, s>>>(p, v, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_finalize_info(int* info, cudaStream_t s) {
+  finalize_info_kernel<<<1, 1, 0, s>>>(info);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy_lower(double* dst, int ldd, const double* src, int lds, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  copy_lower_kernel<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(dst, ldd, src, lds, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy_matrix(double* dst, int ldd, const double* src, int lds, int m, int n, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  copy_matrix_kernel<<<grid_for((size_t)m * n, 256), 256, 0, s>>>(dst, ldd, src, lds, m, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy_matrix(double* X, int ldx, const double* D, int ldd, int n, int nrhs, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  axpy_matrix_kernel<<<grid_for((size_t)n * nrhs, 256), 256, 0, s>>>(X, ldx, D, ldd, n, nrhs);
+  return cudaGetLastError();
+}
+cudaError_t launch_residual(const double* A, int lda, const double* X, int ldx, const double* B, int ldb,
+                            double* R, int ldr, int n, int nrhs, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  cudaError_t e = launch_copy_matrix(R, ldr, B, ldb, n, nrhs, s);
+  if (e != cudaSuccess) return e;
+  const long long nt = (n + RT - 1) / RT;
+  const long long tiles = nt * (nt + 1) / 2;
+  for (int c0 = 0; c0 < nrhs; c0 += RNRHS) {
+    int nc = nrhs - c0 < RNRHS ? nrhs - c0 : RNRHS;
+    residual_tile_kernel<<<(unsigned)tiles, 256, 0, s>>>(A, lda, X + (size_t)c0 * ldx, ldx, R + (size_t)c0 * ldr,
+                                                         ldr, n, nc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t launch_col_norms2(const double* R, int ldr, const double* B, int ldb, int n, int nrhs, double* out,
+                              cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 2 * nrhs, s);
+  if (e != cudaSuccess) return e;
+  dim3 grid(grid_for((size_t)n, 256) > 64 ? 64 : grid_for((size_t)n, 256), nrhs);
+  col_norms2_kernel<<<grid, 256, 0, s>>>(R, ldr, B, ldb, n, nrhs, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_backward_error(const double* A, int lda, const double* L, int ldl, int n, double* out,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long nt = (n + 63) / 64;
+  backward_error_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(A, lda, L, ldl, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  diag_check_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(A, lda, n, limit, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace hrp

@@ -1,0 +1,199 @@
+"""Thin Python binding of libhrp.so (include/hrp.h), argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module only turns torch
+CUDA tensors into device pointers and streams into ``cudaStream_t`` handles.
+
+Layout convention: the C ABI takes column-major matrices.  A column-major m x n
+matrix with leading dimension ld is held here in a row-major torch tensor ``T`` of
+shape (n, ld) with ``T[j, i] = M(i, j)``; ``colmajor()`` / ``from_colmajor()``
+convert numpy arrays to and from that form.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhrp.so")
+
+HRP_MAX_DEPTH = 16
+PREC = {"F64": 0, "F32": 1, "F16": 2, "F8": 3}
+PREC_NAME = {v: k for k, v in PREC.items()}
+STATUS = {0: "HRP_OK", 1: "HRP_ERR_INVALID_ARG", 2: "HRP_ERR_NOT_SPD", 3: "HRP_ERR_NO_CONVERGENCE",
+          4: "HRP_ERR_ALLOC", 5: "HRP_ERR_CUDA", 6: "HRP_ERR_TIMEOUT", 7: "HRP_ERR_UNSUPPORTED",
+          8: "HRP_ERR_RANGE"}
+
+EXPORTED = [
+    "hrp_create", "hrp_destroy", "hrp_last_arg", "hrp_last_error", "hrp_status_string",
+    "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
+    "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
+]
+
+
+class Tree(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("level", ctypes.c_int * HRP_MAX_DEPTH), ("leaf", ctypes.c_int),
+                ("inner", ctypes.c_int), ("inner_size", ctypes.c_int), ("trsm_leaf", ctypes.c_int),
+                ("syrk_leaf", ctypes.c_int), ("scale_block", ctypes.c_int)]
+
+
+class HrpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhrp.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2601_08082_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, ip, dp, c_int, c_double = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), \
+        ctypes.c_int, ctypes.c_double
+    tp = ctypes.POINTER(Tree)
+    L.hrp_create.argtypes = [ctypes.POINTER(vp), c_int]
+    L.hrp_destroy.argtypes = [vp]
+    L.hrp_last_arg.argtypes = [vp]
+    L.hrp_last_error.argtypes = [vp]
+    L.hrp_last_error.restype = ctypes.c_char_p
+    L.hrp_status_string.argtypes = [c_int]
+    L.hrp_status_string.restype = ctypes.c_char_p
+    L.hrp_tree_parse.argtypes = [ctypes.c_char_p, c_int, tp]
+    L.hrp_tree_format.argtypes = [tp, ctypes.c_char_p, ctypes.c_size_t]
+    L.hrp_potrf.argtypes = [vp, tp, c_int, vp, c_int, ip, vp]
+    L.hrp_potrf_async.argtypes = [vp, tp, c_int, vp, c_int, vp, vp]
+    L.hrp_potrs.argtypes = [vp, c_int, c_int, vp, c_int, vp, c_int, vp]
+    L.hrp_posv.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp, c_int, c_int, c_double, ip, dp, ip, ip, vp]
+    L.hrp_backward_error.argtypes = [vp, c_int, vp, c_int, vp, c_int, dp, vp]
+    L.hrp_set_timing.argtypes = [vp, c_int]
+    L.hrp_get_timing.argtypes = [vp, dp, c_int]
+    L.hrp_last_launch_count.argtypes = [vp]
+    L.hrp_last_launch_count.restype = ctypes.c_longlong
+    _lib = L
+    return L
+
+
+def tree_parse(spec: str, leaf: int = 128, trsm_leaf: int = 0, syrk_leaf: int = 0) -> Tree:
+    t = Tree()
+    st = load().hrp_tree_parse(spec.encode(), leaf, ctypes.byref(t))
+    if st != 0:
+        raise HrpError(st, f"bad tree spec {spec!r}")
+    t.trsm_leaf = trsm_leaf
+    t.syrk_leaf = syrk_leaf
+    return t
+
+
+def tree_format(t: Tree) -> str:
+    buf = ctypes.create_string_buffer(256)
+    load().hrp_tree_format(ctypes.byref(t), buf, 256)
+    return buf.value.decode()
+
+
+def colmajor(a: np.ndarray):
+    """numpy (m, n) -> torch CPU float64 tensor (n, m) holding the column-major matrix."""
+    import torch
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return torch.from_numpy(np.ascontiguousarray(a.T))
+
+
+def from_colmajor(t, m: int | None = None) -> np.ndarray:
+    """torch tensor (n, ld) column-major storage -> numpy (m, n)."""
+    a = t.detach().cpu().numpy().T
+    return a if m is None else a[:m]
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Handle:
+    """Owns an hrp_handle (workspace, streams' scratch) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        st = self._lib.hrp_create(ctypes.byref(self._h), device)
+        if st != 0:
+            raise HrpError(st, "hrp_create failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            self._lib.hrp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow=()):
+        if st != 0 and st not in allow:
+            raise HrpError(st, self._lib.hrp_last_error(self._h).decode())
+        return st
+
+    def last_arg(self) -> int:
+        return self._lib.hrp_last_arg(self._h)
+
+    def launch_count(self) -> int:
+        return self._lib.hrp_last_launch_count(self._h)
+
+    # hrp_potrf: A is a column-major (n, lda) float64 CUDA tensor, overwritten with L
+    def potrf(self, tree: Tree, A, n: int | None = None, stream=None, raise_not_spd: bool = False) -> int:
+        n = A.shape[0] if n is None else n
+        lda = A.shape[1]
+        info = ctypes.c_int(0)
+        st = self._lib.hrp_potrf(self._h, ctypes.byref(tree), n, _ptr(A), lda, ctypes.byref(info), _stream(stream))
+        self._check(st, allow=() if raise_not_spd else (2,))
+        return info.value
+
+    def potrf_async(self, tree: Tree, A, d_info, n: int | None = None, stream=None) -> None:
+        n = A.shape[0] if n is None else n
+        st = self._lib.hrp_potrf_async(self._h, ctypes.byref(tree), n, _ptr(A), A.shape[1], _ptr(d_info),
+                                       _stream(stream))
+        self._check(st)
+
+    # hrp_potrs: L (n, ldl) column-major factor, B (nrhs, ldb) column-major, overwritten with X
+    def potrs(self, L, B, n: int | None = None, stream=None) -> None:
+        n = L.shape[0] if n is None else n
+        nrhs = B.shape[0]
+        st = self._lib.hrp_potrs(self._h, n, nrhs, _ptr(L), L.shape[1], _ptr(B), B.shape[1], _stream(stream))
+        self._check(st)
+
+    def posv(self, tree: Tree, A, B, X, max_iter: int = 30, tol: float = 1e-12, n: int | None = None,
+             stream=None, raise_errors: bool = False) -> dict:
+        n = A.shape[0] if n is None else n
+        nrhs = B.shape[0]
+        iters, info, fb = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        resid = ctypes.c_double(0.0)
+        st = self._lib.hrp_posv(self._h, ctypes.byref(tree), n, nrhs, _ptr(A), A.shape[1], _ptr(B), B.shape[1],
+                                _ptr(X), X.shape[1], max_iter, tol, ctypes.byref(iters), ctypes.byref(resid),
+                                ctypes.byref(info), ctypes.byref(fb), _stream(stream))
+        self._check(st, allow=() if raise_errors else (2, 3))
+        return {"status": st, "iters": iters.value, "resid": resid.value, "info": info.value,
+                "used_fallback": fb.value}
+
+    def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
+        n = A.shape[0] if n is None else n
+        out = ctypes.c_double(0.0)
+        st = self._lib.hrp_backward_error(self._h, n, _ptr(A), A.shape[1], _ptr(L), L.shape[1], ctypes.byref(out),
+                                          _stream(stream))
+        self._check(st)
+        return out.value

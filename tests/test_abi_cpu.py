@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and exports
+every entry point include/hrp.h declares, and the tree descriptor parses the notation
+of Sec. 4.2 the same way the oracle reads it."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hrp.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hrp_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_08082_gb300 import build as b, hrp
+    if not os.path.exists(hrp.LIB_PATH):
+        b.build()
+    return hrp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2601_08082_gb300 import hrp
+    assert sorted(hrp.EXPORTED) == names
+
+
+@pytest.mark.parametrize("spec,levels,inner,size", [
+    ("[F64]", [0], 0, 0),
+    ("[F16,F16,F16,F16,F32|F64@128]", [2, 2, 2, 2, 1], 0, 128),
+    ("[F8,F16,F16,F32|F64@128]", [3, 2, 2, 1], 0, 128),
+    ("[F16, F32, F64]", [2, 1, 0], 0, 0),
+])
+def test_tree_parse_matches_oracle_reading(lib, spec, levels, inner, size):
+    from paper_2601_08082_gb300 import hrp
+    from oracle import tree as otree
+    t = hrp.tree_parse(spec, leaf=128)
+    assert list(t.level[: t.depth]) == levels
+    assert t.inner_size == size
+    o = otree.parse(spec)
+    assert [hrp.PREC[p] for p in o.levels] == levels and o.inner_size == size
+    assert hrp.tree_format(t).replace(" ", "") == spec.replace(" ", "")
+
+
+@pytest.mark.parametrize("bad", ["F16", "[F12]", "[]", "[F16|F16@12]", "[F64|F64@]", "[F32]x"])
+def test_tree_parse_rejects(lib, bad):
+    from paper_2601_08082_gb300 import hrp
+    t = hrp.Tree()
+    assert lib.hrp_tree_parse(bad.encode(), 128, ctypes.byref(t)) == 1
+
+
+def test_status_strings(lib):
+    assert lib.hrp_status_string(0) == b"HRP_OK"
+    assert lib.hrp_status_string(2) == b"HRP_ERR_NOT_SPD"
+    assert lib.hrp_status_string(6) == b"HRP_ERR_TIMEOUT"
+
+
+def test_null_handle_is_rejected_without_a_gpu(lib):
+    from paper_2601_08082_gb300 import hrp
+    t = hrp.tree_parse("[F64]", 64)
+    assert lib.hrp_potrf(None, ctypes.byref(t), 4, None, 4, None, None) == 1
+    assert lib.hrp_potrs(None, 4, 1, None, 4, None, 4, None) == 1

@@ -1,0 +1,201 @@
+"""GPU parity of the factorization and solves against the CPU oracle (through the C ABI).
+
+* FP64 tree vs the plain Cholesky: <= 1e-12 relative (max-norm over L).
+* Mixed trees vs the step-by-step emulator of Alg. 1-3: the GPU accumulates GEMMs in
+  FP32 (TMEM / registers) where the emulator sums exact products in FP64, and its FP32
+  leaf TRSM multiplies by the FP32 inverse of the diagonal leaf where the emulator
+  substitutes.  Both are FP32 rounding effects of order K * 2^-24 relative to
+  sum |x||y| per entry; with the FP16 operand rounding (2^-11) unchanged, the bound used
+  here is max|L_gpu - L_emu| <= 1e-5 max|L|, and the GPU result must be at least 10x
+  closer to the emulator than the emulator is to the FP64 factor (so the precision
+  semantics, not only the error size, match).
+"""
+import numpy as np
+import pytest
+
+from oracle import dense, tree as otree
+from synth import dominant_spd, paper_spd, rhs, seed_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hrp_mod():
+    import torch
+    import paper_2601_08082_gb300 as hrp
+    assert torch.cuda.is_available()
+    return hrp
+
+
+@pytest.fixture(scope="module")
+def handle(hrp_mod):
+    h = hrp_mod.Handle(0)
+    yield h
+    h.close()
+
+
+def _factor(hrp, h, A, spec, leaf, trsm_leaf=0):
+    At = hrp.colmajor(A).cuda()
+    info = h.potrf(hrp.tree_parse(spec, leaf=leaf, trsm_leaf=trsm_leaf), At)
+    return np.tril(hrp.from_colmajor(At)), info, At
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 63, 64, 65, 127, 129, 300, 1000, 1024])
+def test_fp64_tree_matches_plain_cholesky(hrp_mod, handle, n):
+    A = dominant_spd(n, 1.0, seed_for(0, n), shift=1.0)
+    L, info, _ = _factor(hrp_mod, handle, A, "[F64]", 64)
+    assert info == 0
+    L0, _ = dense.cholesky(A)
+    assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
+
+
+@pytest.mark.parametrize("leaf", [16, 100, 128])
+def test_fp64_tree_other_leaves(hrp_mod, handle, leaf):
+    n = 777
+    A = dominant_spd(n, 1.05, seed_for(0, 3))
+    L, info, _ = _factor(hrp_mod, handle, A, "[F64]", leaf)
+    assert info == 0
+    L0, _ = dense.cholesky(A)
+    assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
+
+
+def test_upper_triangle_untouched(hrp_mod, handle):
+    n = 200
+    A = dominant_spd(n, 2.0, seed_for(0, 5))
+    At = hrp_mod.colmajor(A).cuda()
+    handle.potrf(hrp_mod.tree_parse("[F16,F32|F64@64]", leaf=64), At)
+    M = hrp_mod.from_colmajor(At)
+    iu = np.triu_indices(n, 1)
+    assert np.array_equal(M[iu], A[iu])
+
+
+MIXED = [
+    ("[F32]", 128), ("[F16,F32]", 128), ("[F16,F32,F64]", 128), ("[F32,F32,F32,F64]", 128),
+    ("[F16,F16,F32|F64@128]", 128), ("[F16,F16,F16,F16,F32|F64@128]", 128), ("[F16,F32|F64@64]", 64),
+]
+
+
+@pytest.mark.parametrize("spec,leaf", MIXED)
+@pytest.mark.parametrize("n,rho", [(1000, 1.05), (2048, 2.0), (1300, 8.0)])
+def test_mixed_tree_matches_emulator(hrp_mod, handle, spec, leaf, n, rho):
+    A = dominant_spd(n, rho, seed_for(1, n))
+    L, info, _ = _factor(hrp_mod, handle, A, spec, leaf)
+    assert info == 0
+    L_emu, info_e, _ = otree.emulate_potrf(A, otree.parse(spec, leaf=leaf))
+    assert info_e == 0
+    scale = np.max(np.abs(L_emu))
+    d_gpu = np.max(np.abs(L - L_emu)) / scale
+    assert d_gpu <= 1e-5, d_gpu
+    L64, _ = dense.cholesky(A)
+    d_emu = np.max(np.abs(L_emu - L64)) / scale
+    if d_emu > 1e-9:                     # a reduced-precision tree: semantics must match
+        assert d_gpu <= 0.1 * d_emu, (d_gpu, d_emu)
+    assert dense.backward_error(A, L) <= 5e-5
+
+
+def test_paper_generator_ladder_on_gpu(hrp_mod, handle):
+    n = 1024
+    A = paper_spd(n, seed_for(9, 1))
+    errs = {}
+    for spec in ["[F64]", "[F32,F32,F32,F64]", "[F32]", "[F16,F32]"]:
+        L, info, _ = _factor(hrp_mod, handle, A, spec, 128)
+        assert info == 0
+        errs[spec] = dense.backward_error(A, L)
+    assert errs["[F64]"] < 1e-14
+    assert errs["[F64]"] < errs["[F32,F32,F32,F64]"] < errs["[F32]"]
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (65, 3), (1000, 1), (1100, 16), (640, 20)])
+def test_potrs_fp64_matches_oracle(hrp_mod, handle, n, nrhs):
+    A = dominant_spd(n, 1.0, seed_for(0, n), shift=1.0)
+    L0, _ = dense.cholesky(A)
+    B = rhs(n, nrhs, seed_for(0, 100 + n))
+    Lt = hrp_mod.colmajor(L0).cuda()
+    Bt = hrp_mod.colmajor(B).cuda()
+    handle.potrs(Lt, Bt)
+    X = hrp_mod.from_colmajor(Bt)
+    X0 = dense.potrs(L0, B)
+    assert np.max(np.abs(X - X0)) <= 1e-12 * np.max(np.abs(X0))
+
+
+def test_not_spd_reports_first_failing_column(hrp_mod, handle):
+    n = 300
+    A = dominant_spd(n, 2.0, seed_for(0, 9))
+    A[200, 200] = -5.0
+    _, info0 = dense.cholesky(A)
+    for spec, leaf in [("[F64]", 64), ("[F16,F32|F64@64]", 64)]:
+        _, info, _ = _factor(hrp_mod, handle, A, spec, leaf)
+        assert info == info0 == 201
+    A = dominant_spd(n, 2.0, seed_for(0, 9))
+    A[37, 37] = np.nan
+    _, info, _ = _factor(hrp_mod, handle, A, "[F64]", 64)
+    assert info == 38
+
+
+def test_invalid_arguments(hrp_mod, handle):
+    import torch
+    t = hrp_mod.tree_parse("[F64]", leaf=64)
+    A = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(hrp_mod.HrpError):
+        handle.potrf(t, A, n=9)            # lda (8) < n
+    assert handle.last_arg() == -5
+    bad = hrp_mod.tree_parse("[F64]", leaf=64)
+    bad.leaf = 0
+    with pytest.raises(hrp_mod.HrpError):
+        handle.potrf(bad, A)
+    assert handle.last_arg() == -2
+
+
+def test_empty_matrix(hrp_mod, handle):
+    import torch
+    A = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+    assert handle.potrf(hrp_mod.tree_parse("[F16,F32]", 128), A, n=0) == 0
+
+
+def test_gpu_backward_error_matches_cpu(hrp_mod, handle):
+    n = 700
+    A = dominant_spd(n, 1.05, seed_for(1, 11))
+    L, info, At = _factor(hrp_mod, handle, A, "[F16,F32]", 128)
+    assert info == 0
+    A_t = hrp_mod.colmajor(A).cuda()
+    be_gpu = handle.backward_error(A_t, At)
+    be_cpu = dense.backward_error(A, L)
+    assert abs(be_gpu - be_cpu) <= 1e-6 * be_cpu + 1e-15
+
+
+@pytest.mark.parametrize("spec", ["[F16,F16,F32|F64@128]", "[F64]"])
+def test_posv_refines_to_tolerance(hrp_mod, handle, spec):
+    import torch
+    n, nrhs = 1500, 4
+    A = dominant_spd(n, 2.0, seed_for(2, 1))
+    B = rhs(n, nrhs, seed_for(2, 2))
+    A_t = hrp_mod.colmajor(A).cuda()
+    B_t = hrp_mod.colmajor(B).cuda()
+    X_t = torch.zeros_like(B_t)
+    A_before = A_t.clone()
+    out = handle.posv(hrp_mod.tree_parse(spec, 128), A_t, B_t, X_t, max_iter=30, tol=1e-12)
+    assert out["status"] == 0 and out["info"] == 0
+    assert torch.equal(A_t, A_before)                    # A is not modified
+    X = hrp_mod.from_colmajor(X_t)
+    res = dense.column_residuals(A, X, B)
+    assert np.max(res) <= 1e-12
+    assert abs(out["resid"] - np.max(res)) <= 1e-13 + 0.1 * np.max(res)
+
+
+def test_posv_falls_back_when_the_mixed_tree_fails(hrp_mod, handle):
+    """Pure FP16 off-diagonals on a barely positive definite matrix lose definiteness;
+    hrp_posv must refactor with the FP32/FP64 tree and still converge."""
+    import torch
+    n = 600
+    L = np.tril(np.random.default_rng(4).standard_normal((n, n)) * 0.3)
+    np.fill_diagonal(L, 1e-3)
+    A = L @ L.T + 1e-9 * np.eye(n)
+    B = rhs(n, 1, seed_for(2, 3))
+    _, info16, _ = otree.emulate_potrf(A, otree.parse("[F16,F16,F16]", leaf=64))
+    if info16 == 0:
+        pytest.skip("matrix did not break the FP16 tree in the emulator")
+    A_t = hrp_mod.colmajor(A).cuda()
+    B_t = hrp_mod.colmajor(B).cuda()
+    X_t = torch.zeros_like(B_t)
+    out = handle.posv(hrp_mod.tree_parse("[F16,F16,F16]", 64), A_t, B_t, X_t, max_iter=5, tol=1e-30)
+    assert out["used_fallback"] == 1
