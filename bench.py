@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""POTRF effective TFLOP/s (n^3/3 per second) of the mixed-precision recursive Cholesky
+against the FP64 tree, on one GB300 (or N independent replicas under torchrun).
+
+Workload (one "step" = one pass of the hot path over one matrix):
+  A: n = 8192, B iid N(0,1), A = (B + B^T)/2, A_ii = rho * sum_{j!=i} |A_ij|, rho cycling
+     through {1.05, 2, 8}; tree [F16,F16,F16,F16,F32|F64@128] (FP16 off-diagonal GEMMs with
+     FP32 accumulation at the four outer levels, FP32 below, FP64 diagonal leaves of 128);
+  step = hrp_potrf_async (factor) + hrp_potrs (1 right-hand side) on the device.
+Every step factors its own resident copy of A (512 MB each, larger than L2), so no
+input is re-read from L2 across steps.
+
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+step-by-step emulator of Alg. 1-3) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 8192
+RHOS = (1.05, 2.0, 8.0)
+TREE = "[F16,F16,F16,F16,F32|F64@128]"
+LEAF = 128
+FP64_TREE, FP64_LEAF = "[F64]", 64
+METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated backward error"
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (nominal); DFMA-bound kernels report against it
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(n_s: int = 3072, rho: float = 2.0):
+    """Time the oracle (emulator of Alg. 1-3) on one n_s matrix of the same generator and tree."""
+    from oracle import tree as otree
+    from synth import dominant_spd, seed_for
+    A = dominant_spd(n_s, rho, seed_for(1, 900 + n_s))
+    t = otree.parse(TREE, leaf=LEAF)
+    t0 = time.perf_counter()
+    _, info, _ = otree.emulate_potrf(A, t)
+    dt = time.perf_counter() - t0
+    assert info == 0
+    return {"value": n_s ** 3 / 3.0 / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"emulator of Alg. 1-3 (float64 numpy, tree {TREE}, leaf {LEAF}) on one n={n_s} "
+                      f"matrix of the same generator (rho={rho}); {dt:.2f} s",
+            "seconds": dt}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    n_s = 2048
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_s)
+    secs = []
+    for _ in range(args.steps):
+        secs.append(cpu_oracle_sample(n_s)["seconds"])
+    tot = sum(secs)
+    val = args.steps * n_s ** 3 / 3.0 / tot / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32/f64 emulated in f64",
+            "data": "synthetic", "config": {"workload": f"mixed tree {TREE}, n={N} generator, sample n={n_s}",
+                                            "n": n_s, "tree": TREE, "leaf": LEAF, "rho": 2.0, "nrhs": 0},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"emulator of Alg. 1-3 on one n={n_s} matrix per step"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hrp", choices=["hrp", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_2601_08082_gb300 as hrp
+    from synth import dominant_spd, rhs, seed_for
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # oracle baseline first (rank 0 only, before any other GPU work matters)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample()
+        cpu.pop("seconds", None)
+
+    h = hrp.Handle(local)
+    tree = hrp.tree_parse(TREE, leaf=LEAF)
+    tree64 = hrp.tree_parse(FP64_TREE, leaf=FP64_LEAF)
+    stream = torch.cuda.current_stream()
+
+    # inputs: one matrix per rho, generated on the host (same bits as the oracle sees)
+    mats = [dominant_spd(N, rho, seed_for(1, 10 * rank + i)) for i, rho in enumerate(RHOS)]
+    bvec = rhs(N, 1, seed_for(1, 100 + rank))
+    A0 = [hrp.colmajor(A).cuda() for A in mats]
+    nsteps = args.warmup + args.steps
+    copies = [A0[s % len(RHOS)].clone() for s in range(nsteps)]
+    B = [hrp.colmajor(bvec).cuda() for _ in range(nsteps)]
+    d_info = torch.zeros(nsteps, dtype=torch.int32, device="cuda")
+    flops = N ** 3 / 3.0
+
+    def step(s):
+        h.potrf_async(tree, copies[s], d_info[s:s + 1], stream=stream)
+        launches = h.launch_count()
+        h.potrs(copies[s], B[s], stream=stream)
+        return launches + h.launch_count()
+
+    for s in range(args.warmup):
+        step(s)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for s in range(args.warmup, nsteps):
+            launches += step(s)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    infos = d_info.cpu().tolist()
+    assert all(i == 0 for i in infos), infos
+    value = world * args.steps * flops / (ms * 1e-3) / 1e12
+
+    # accuracy of the timed factorizations (device FP64 backward error) and of the solves
+    acc = {}
+    for i, rho in enumerate(RHOS):
+        s = args.warmup + i
+        if s >= nsteps:
+            break
+        be = h.backward_error(A0[s % len(RHOS)], copies[s])
+        x = hrp.from_colmajor(B[s])
+        r = mats[s % len(RHOS)] @ x - bvec
+        acc[str(rho)] = {"backward_error": be,
+                         "solution_residual": float(np.linalg.norm(r) / np.linalg.norm(bvec))}
+
+    # roofline: one factorization in timing mode (per-kernel-class event timing)
+    hrp.load().hrp_set_timing(h._h, 1)
+    tmp = A0[1].clone()
+    h.potrf(tree, tmp)
+    import ctypes
+    buf = (ctypes.c_double * 15)()
+    hrp.load().hrp_get_timing(h._h, buf, 15)
+    hrp.load().hrp_set_timing(h._h, 0)
+    names = ["leaf_potrf_fp64", "leaf_trsm", "gemm_f16_tcgen05", "gemm_simt", "other"]
+    classes = {names[c]: {"ms": buf[3 * c], "launches": int(buf[3 * c + 1]), "flops": buf[3 * c + 2]}
+               for c in range(5)}
+    tot_cls = sum(v["ms"] for v in classes.values()) or 1.0
+    for v in classes.values():
+        v["share"] = v["ms"] / tot_cls
+    pk = peaks()
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+
+    def roof(name):
+        c = classes[name]
+        avg_ms = c["ms"] / max(1, c["launches"])
+        per_launch = c["flops"] / max(1, c["launches"])
+        achieved = per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+        if name == "gemm_f16_tcgen05":
+            peak, bound, src = pk["bf16_tflops"], "tensor", f"{pk['src']} bf16 dense burst (FP16 same rate)"
+        elif name in ("leaf_potrf_fp64",):
+            peak, bound, src = FP64_NOMINAL_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s (DFMA bound)"
+        else:
+            peak, bound, src = 69.0, "alu", "FP32 FFMA 69 TFLOP/s (152 SMs x 128 lanes x 2 x 1.77 GHz)"
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": name, "avg_launch_ms": avg_ms, "peak_src": src}
+
+    # FP64 tree on the same matrices (the comparison of the metric)
+    fp64 = None
+    if args.fp64_steps > 0:
+        t64 = []
+        for i in range(args.fp64_steps):
+            tmp = A0[i % len(RHOS)].clone()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.potrf_async(tree64, tmp, d_info[0:1], stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64.append(a.elapsed_time(b))
+        fp64 = {"ms": min(t64), "tflops": flops / (min(t64) * 1e-3) / 1e12, "tree": FP64_TREE, "leaf": FP64_LEAF}
+
+    # end to end through the C ABI with host buffers: H2D(A, b) + potrf + potrs + D2H(x)
+    e2e = None
+    if args.e2e_steps > 0:
+        hostA = [A.cpu().pin_memory() for A in A0]
+        hostB = hrp.colmajor(bvec).pin_memory()
+        hostX = torch.empty_like(hostB).pin_memory()
+        dA = torch.empty_like(A0[0])
+        dB = torch.empty_like(B[0])
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for s in range(args.e2e_steps):
+            dA.copy_(hostA[s % len(RHOS)], non_blocking=True)
+            dB.copy_(hostB, non_blocking=True)
+            h.potrf_async(tree, dA, d_info[0:1], stream=stream)
+            h.potrs(dA, dB, stream=stream)
+            hostX.copy_(dB, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b)
+        e2e = {"value": world * args.e2e_steps * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(dA.numel() * 8 + dB.numel() * 8), "d2h_bytes_per_step": int(dB.numel() * 8),
+               "ms_per_step": ems / args.e2e_steps}
+
+    barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16 (fp32 acc) / f32 / f64", "data": "synthetic",
+            "config": {"workload": f"mixed tree {TREE} n={N} rho cycling {list(RHOS)}, factor + 1-RHS solve",
+                       "n": N, "tree": TREE, "leaf": LEAF, "rhos": list(RHOS), "nrhs": 1,
+                       "l2": "inputs larger than L2 (one resident 512 MB copy per step)",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_tree": fp64,
+            "speedup_vs_fp64_tree": (value / world) / fp64["tflops"] if fp64 else None,
+            "accuracy": acc,
+            "roofline": roof(dom),
+            "roofline_gemm": roof("gemm_f16_tcgen05"),
+            "kernel_classes": classes,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

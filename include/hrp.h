@@ -66,6 +66,8 @@ typedef enum { HRP_F64 = 0, HRP_F32 = 1, HRP_F16 = 2, HRP_F8E4M3 = 3 } hrp_prec;
  *     leaf POTRF kernel); 1 <= leaf <= 128.
  *   trsm_leaf, syrk_leaf: Alg. 2 / Alg. 3 base-case sizes (0 = leaf); trsm_leaf <= leaf.
  *   scale_block: tile edge of the FP8 power-of-two scales (128).
+ *   trsm_compute: arithmetic of a leaf TRSM at a reduced-precision (F32/F16/F8) level:
+ *     0 = FP32 (default), 1 = FP64.  Leaf TRSMs at F64 levels are always FP64.
  * Split point of a node of order n (reading of "e.g. n1 = floor(n/2)"): n/2 rounded to
  * the nearest multiple of 128 for n >= 512, of 16 for 32 <= n < 512, floor(n/2) below.
  */
@@ -78,6 +80,7 @@ typedef struct {
   int trsm_leaf;
   int syrk_leaf;
   int scale_block;
+  int trsm_compute;
 } hrp_tree;
 
 typedef struct hrp_handle_s hrp_handle;
@@ -151,12 +154,16 @@ hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda,
                               const double* dL, int ldl, double* out, void* stream);
 
 /*
- * Per-phase device times of the last hrp_potrf on this handle when timing is enabled
- * (hrp_set_timing(h, 1)): ms[0]=leaf POTRF, [1]=TRSM (leaves+GEMMs), [2]=SYRK GEMMs,
- * [3]=other. Returns the number of values written (<= n).
+ * Timing mode (hrp_set_timing(h, 1)): every kernel the next factorizations enqueue is
+ * bracketed by CUDA events on the call's stream, and the factorization synchronizes the
+ * stream once at its end (so do not enable it while capturing a graph).
+ * hrp_get_timing writes, for each kernel class c = 0..4 (leaf POTRF, leaf TRSM, tcgen05
+ * FP16 GEMM, SIMT GEMM, other), the triple out[3c] = summed device milliseconds,
+ * out[3c+1] = launches, out[3c+2] = algorithmic flops of the last factorization.
+ * Returns the number of doubles written (<= n).
  */
 hrp_status hrp_set_timing(hrp_handle* h, int enable);
-int hrp_get_timing(hrp_handle* h, double* ms, int n);
+int hrp_get_timing(hrp_handle* h, double* out, int n);
 
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);

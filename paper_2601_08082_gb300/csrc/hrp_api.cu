@@ -21,6 +21,11 @@
 
 #include "hrp_internal.cuh"
 
+namespace hrp {
+// kernel classes reported by hrp_get_timing
+enum { CLS_POTRF = 0, CLS_TRSM = 1, CLS_GEMM_TC = 2, CLS_GEMM_SIMT = 3, CLS_OTHER = 4, kNumClasses = 5 };
+}
+
 struct hrp_handle_s {
   int device = 0;
   int last_arg = 0;
@@ -39,11 +44,17 @@ struct hrp_handle_s {
   size_t fact_cap = 0;
   double* work = nullptr;      // posv residual/correction
   size_t work_cap = 0;
+  unsigned char* pwork = nullptr;  // POTRS diagonal-block inverses
+  size_t pwork_cap = 0;
   double* d_norms = nullptr;   // 2 * 64 doubles
   double* h_norms = nullptr;   // pinned host mirror
   long long launches = 0;
   bool timing = false;
-  double phase_ms[4] = {0, 0, 0, 0};
+  // per-kernel-class timing of the last factorization (timing mode only)
+  double cls_ms[hrp::kNumClasses] = {0};
+  double cls_launches[hrp::kNumClasses] = {0};
+  double cls_flops[hrp::kNumClasses] = {0};
+  std::vector<cudaEvent_t> events;
 };
 
 namespace hrp {
@@ -108,6 +119,7 @@ hrp_status validate_tree(hrp_handle* h, const hrp_tree* t, int pos) {
   if (tl < 1 || tl > t->leaf) return bad_arg(h, pos, "trsm_leaf must be in [1, leaf]");
   int sl = t->syrk_leaf ? t->syrk_leaf : t->leaf;
   if (sl < 1) return bad_arg(h, pos, "syrk_leaf < 0");
+  if (t->trsm_compute != 0 && t->trsm_compute != 1) return bad_arg(h, pos, "trsm_compute must be 0 or 1");
   return HRP_OK;
 }
 
@@ -135,10 +147,44 @@ struct Fact {
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
   cudaError_t err = cudaSuccess;
   long long launches = 0;
+  // timing mode: an event pair around every launch, tagged with its class and flops
+  struct Rec { int cls; size_t ev; double flops; };
+  std::vector<Rec> recs;
+  int cur_cls = CLS_OTHER;
+  double cur_flops = 0.0;
+  size_t ev_next = 0;
 
+  cudaEvent_t event(size_t i) {
+    while (h->events.size() <= i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      h->events.push_back(e);
+    }
+    return h->events[i];
+  }
+  bool began = false;
+  void begin(int cls, double flops) {
+    cur_cls = cls;
+    cur_flops = flops;
+    began = false;
+    if (h->timing) {
+      cudaEvent_t e = event(ev_next);
+      began = e && cudaEventRecord(e, s) == cudaSuccess;
+    }
+  }
   void chk(cudaError_t e) {
     ++launches;
     if (e != cudaSuccess && err == cudaSuccess) err = e;
+    if (h->timing && began) {
+      cudaEvent_t e1 = event(ev_next + 1);
+      if (e1 && cudaEventRecord(e1, s) == cudaSuccess) {
+        recs.push_back({cur_cls, ev_next, cur_flops});
+        ev_next += 2;
+      }
+    }
+    began = false;
+    cur_cls = CLS_OTHER;
+    cur_flops = 0.0;
   }
   int tleaf() const { return t->trsm_leaf ? t->trsm_leaf : t->leaf; }
 
@@ -148,13 +194,15 @@ struct Fact {
       W = w32 + (size_t)off * 128;
       leaves[off] = nb;
     }
+    begin(CLS_POTRF, (double)nb * nb * nb / 3.0);
     chk(launch_potrf_leaf(A + (size_t)off * lda + off, lda, nb, off, p == HRP_F64, p == HRP_F16, W, 128, info, s));
   }
 
   void leaf_trsm(int r0, int m, int c0, int nc, int p) {
     double* Ab = A;
     __half* sh = shadow;
-    if (p == HRP_F64) {
+    begin(CLS_TRSM, (double)m * nc * nc);
+    if (p == HRP_F64 || t->trsm_compute == 1) {
       chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
       return;
     }
@@ -172,11 +220,14 @@ struct Fact {
     double* C = A + (size_t)c0 * lda + r0;
     const double* X = A + (size_t)k0 * lda + r0;
     const double* Y = A + (size_t)k0 * lda + c0;
+    const double fl = lower ? (double)m * (m + 1) * k : 2.0 * m * nd * k;
+    const bool use_tc = p == HRP_F16 && tc && shadow && (k0 % 8) == 0 && k >= 16;
+    begin(use_tc ? CLS_GEMM_TC : CLS_GEMM_SIMT, fl);
     switch (p) {
       case HRP_F64: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F64, lower, s)); break;
       case HRP_F32: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F32, lower, s)); break;
       case HRP_F16:
-        if (tc && shadow && (k0 % 8) == 0 && k >= 16)
+        if (use_tc)
           chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s));
         else
           chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F16, lower, s));
@@ -223,6 +274,17 @@ hrp_status cuda_status(hrp_handle* h, cudaError_t e, const char* where) {
   return set_err(h, HRP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+void collect_timing(hrp_handle* h, const Fact& f) {
+  for (int c = 0; c < kNumClasses; ++c) h->cls_ms[c] = h->cls_launches[c] = h->cls_flops[c] = 0.0;
+  for (const auto& r : f.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->events[r.ev], h->events[r.ev + 1]) == cudaSuccess) h->cls_ms[r.cls] += ms;
+    h->cls_launches[r.cls] += 1.0;
+    h->cls_flops[r.cls] += r.flops;
+  }
+  cudaGetLastError();   // a failed elapsed-time query must not leak into the next launch check
+}
+
 hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s) {
   hrp_status st;
   if (tree_has(t, HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "FP8 levels are not built in this version");
@@ -247,10 +309,17 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
     if ((st = ensure(h, &h->w32, &h->w32_cap, (size_t)n * 128 + 128 * 128)) != HRP_OK) return st;
     f.w32 = h->w32;
   }
+  f.begin(CLS_OTHER, 0.0);
   f.chk(launch_fill_int(d_info, INT_MAX, 1, s));
   f.potrf(0, n, 0);
+  f.begin(CLS_OTHER, 0.0);
   f.chk(launch_finalize_info(d_info, s));
   h->launches = f.launches;
+  if (h->timing && f.err == cudaSuccess) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(h, e, "hrp_potrf timing");
+    collect_timing(h, f);
+  }
   return cuda_status(h, f.err, "hrp_potrf");
 }
 
@@ -325,7 +394,9 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->fact);
   cudaFree(h->work);
   cudaFree(h->d_norms);
+  cudaFree(h->pwork);
   if (h->h_norms) cudaFreeHost(h->h_norms);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   delete h;
   return HRP_OK;
 }
@@ -435,6 +506,7 @@ hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int
   return HRP_OK;
 }
 
+
 static hrp_status potrs_impl(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
                              bool fp32, cudaStream_t s) {
   hrp_status st;
@@ -455,8 +527,9 @@ static hrp_status potrs_impl(hrp_handle* h, int n, int nrhs, const double* dL, i
   }
   int ep = h->epoch;
   h->epoch += ne;
-  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->d_ticket, h->d_flags, ep, h->d_err, s);
-  h->launches += 2 * ne;
+  if ((st = ensure(h, &h->pwork, &h->pwork_cap, potrs_workspace_bytes(n))) != HRP_OK) return st;
+  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->pwork, h->d_ticket, h->d_flags, ep, h->d_err, s);
+  h->launches += 1 + 2 * ne;
   return cuda_status(h, e, "hrp_potrs");
 }
 
@@ -580,11 +653,15 @@ hrp_status hrp_set_timing(hrp_handle* h, int enable) {
   return HRP_OK;
 }
 
-int hrp_get_timing(hrp_handle* h, double* ms, int n) {
-  if (!h || !ms) return 0;
-  int k = n < 4 ? n : 4;
-  for (int i = 0; i < k; ++i) ms[i] = h->phase_ms[i];
-  return k;
+int hrp_get_timing(hrp_handle* h, double* out, int n) {
+  if (!h || !out) return 0;
+  int w = 0;
+  for (int c = 0; c < kNumClasses && w + 3 <= n; ++c) {
+    out[w++] = h->cls_ms[c];
+    out[w++] = h->cls_launches[c];
+    out[w++] = h->cls_flops[c];
+  }
+  return w;
 }
 
 long long hrp_last_launch_count(const hrp_handle* h) { return h ? h->launches : 0; }

@@ -64,8 +64,10 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds,
 // B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 or (fp32)
 // in FP32 on FP32-rounded L and B.  ticket: device int scratch; flags: device ints, one per
 // 64-row block; consumes potrs_epochs(nrhs) consecutive epoch values starting at `epoch`.
-cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32,
+// work: device scratch of potrs_workspace_bytes(n) (inverses of the 64 x 64 diagonal blocks).
+cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32, void* work,
                          int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s);
+size_t potrs_workspace_bytes(int n);
 int potrs_epochs(int nrhs);
 
 // ---------------- utilities (k_util.cu) ----------------

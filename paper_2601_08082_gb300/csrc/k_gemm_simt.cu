@@ -36,17 +36,28 @@ gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, 
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
 
+  // register prefetch of the next BK slice while the current one is multiplied
+  T px[(BM * BK) / 256], py[(BN * BK) / 256];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < (BM * BK) / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int r = e % BM, kk = e / BM;
+      const int gr = m0 + r, gk = k0 + kk, gc = n0 + r;
+      px[q] = (gr < m && gk < k) ? cvt_op<RND>(X[(size_t)gk * ldx + gr]) : (T)0;
+      py[q] = (gc < n && gk < k) ? cvt_op<RND>(Y[(size_t)gk * ldy + gc]) : (T)0;
+    }
+  };
+  fetch(0);
   for (int k0 = 0; k0 < k; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < (BM * BK) / 256; ++q) {
-      int e = tid + 256 * q;
-      int r = e % BM, kk = e / BM;
-      int gr = m0 + r, gk = k0 + kk;
-      Xs[kk][r] = (gr < m && gk < k) ? cvt_op<RND>(X[(size_t)gk * ldx + gr]) : (T)0;
-      int gc = n0 + r;
-      Ys[kk][r] = (gc < n && gk < k) ? cvt_op<RND>(Y[(size_t)gk * ldy + gc]) : (T)0;
+      const int e = tid + 256 * q;
+      Xs[e / BM][e % BM] = px[q];
+      Ys[e / BM][e % BM] = py[q];
     }
     __syncthreads();
+    if (k0 + BK < k) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[4], b[4];
@@ -61,19 +72,23 @@ gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, 
     }
     __syncthreads();
   }
+  double cv[4][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int gc = n0 + ty + 16 * j;
-    if (gc >= n) continue;
+  for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      int gr = m0 + tx + 16 * i;
-      if (gr >= m) continue;
-      if (lower && gr < gc) continue;
-      double* p = C + (size_t)gc * ldc + gr;
-      *p = *p - (double)acc[i][j];
+      const int gc = n0 + ty + 16 * j, gr = m0 + tx + 16 * i;
+      const bool ok = gc < n && gr < m && !(lower && gr < gc);
+      cv[i][j] = ok ? C[(size_t)gc * ldc + gr] : 0.0;
     }
-  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gc = n0 + ty + 16 * j, gr = m0 + tx + 16 * i;
+      const bool ok = gc < n && gr < m && !(lower && gr < gc);
+      if (ok) C[(size_t)gc * ldc + gr] = cv[i][j] - (double)acc[i][j];
+    }
 }
 
 }  // namespace

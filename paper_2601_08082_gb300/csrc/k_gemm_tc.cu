@@ -199,13 +199,19 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
         if (row < m) {
+          // all 32 loads first (independent, in flight together), then the 32 stores
+          double* base_p = C + (size_t)(n0 + c0) * ldc + row;
+          double cv[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
-            if (col < n && (!lower || row >= col)) {
-              double* p = C + (size_t)col * ldc + row;
-              *p = *p - scale * (double)__uint_as_float(r[j]);
-            }
+            cv[j] = (col < n && (!lower || row >= col)) ? __ldcs(base_p + (size_t)j * ldc) : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < n && (!lower || row >= col))
+              __stcs(base_p + (size_t)j * ldc, cv[j] - scale * (double)__uint_as_float(r[j]));
           }
         }
       }

@@ -8,128 +8,222 @@
 namespace hrp {
 namespace {
 
-template <typename T> __device__ __forceinline__ T dsqrt(T x);
-template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
-
 __device__ __forceinline__ double round_to_f16(double x) { return (double)__half2float(__double2half(x)); }
 
 // ---------------------------------------------------------------------------------------
-// Leaf POTRF (Alg. 1 base case "A <- POTRF_L(A)") of an n x n block, n <= 128, one CTA.
-// Right-looking column Cholesky in shared memory: for each column k the pivot
-// l_kk = sqrt(a_kk) is checked (positive and finite), the column below is divided by it
-// and the trailing lower triangle receives the rank-1 update.  Optionally the FP32
-// inverse W = fl32(L)^{-1} is formed afterwards (column j of W by forward substitution
-// against e_j) for the FP32 leaf TRSM kernel.
+// Reciprocal square root by Newton's method (r <- r + r (1 - d r^2) / 2, quadratic
+// convergence) from a single-precision seed: two steps take the seed's ~22 correct bits
+// past double precision.  On this GPU a dependent FP64 operation costs ~64 cycles, so
+// the 6 dependent operations here are far cheaper than sqrt followed by a division.
+// Values outside the single-precision exponent range take the library sqrt.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double r = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double hr = 0.5 * r;
+    const double e = fma(-d * r, r, 1.0);
+    r = fma(hr, e, r);
+  }
+  return r;
+}
+__device__ __forceinline__ float rsqrt_newton(float d) {
+  float r = rsqrtf(d);
+  const float e = fmaf(-d * r, r, 1.0f);
+  return fmaf(0.5f * r, e, r);
+}
+
+constexpr int kInvLD = 132;   // leading dimension of the FP32 factor / inverse staging (16B rows)
+
+// FP32 inverse W = L^{-1} of the n x n lower-triangular Lf (column-major, ld kInvLD, rows
+// >= n zero), n <= 128, written column-major into Wt (ld kInvLD).  Blocked by 32:
+// W_II = L_II^{-1} per diagonal block (one warp each, lane c = column c, registers), then
+// W_IJ = -W_II * sum_{K=J}^{I-1} L_IK W_KJ for I - J = 1, 2, 3 (one warp per block).
+__device__ void trtri32_blocked(const float* __restrict__ Lf, float* __restrict__ Wt, int n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = (n + 31) / 32;
+  if (warp < nb) {
+    const int I0 = warp * 32;
+    float w[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      float sacc = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int q = 0; q < r; ++q) sacc = fmaf(-Lf[(I0 + q) * kInvLD + I0 + r], w[q], sacc);
+      const float dg = Lf[(I0 + r) * kInvLD + I0 + r];
+      w[r] = (I0 + r < n && r >= lane) ? sacc / dg : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) Wt[(I0 + lane) * kInvLD + I0 + r] = w[r];
+  }
+  __syncthreads();
+  for (int dlt = 1; dlt < nb; ++dlt) {
+    const int J = warp, I = warp + dlt;
+    if (I < nb) {
+      const int I0 = I * 32, J0 = J * 32;
+      float t[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) t[r] = 0.f;
+      for (int K = J; K < I; ++K) {
+        const int K0 = K * 32;
+        for (int q = 0; q < 32; ++q) {
+          const float wv = Wt[(J0 + lane) * kInvLD + K0 + q];
+          const float4* lc = reinterpret_cast<const float4*>(Lf + (K0 + q) * kInvLD + I0);
+#pragma unroll
+          for (int r4 = 0; r4 < 8; ++r4) {
+            const float4 l = lc[r4];
+            t[4 * r4 + 0] = fmaf(l.x, wv, t[4 * r4 + 0]);
+            t[4 * r4 + 1] = fmaf(l.y, wv, t[4 * r4 + 1]);
+            t[4 * r4 + 2] = fmaf(l.z, wv, t[4 * r4 + 2]);
+            t[4 * r4 + 3] = fmaf(l.w, wv, t[4 * r4 + 3]);
+          }
+        }
+      }
+      float o[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) o[r] = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < 32; ++s2) {
+        const float4* wc = reinterpret_cast<const float4*>(Wt + (I0 + s2) * kInvLD + I0);
+#pragma unroll
+        for (int r4 = 0; r4 < 8; ++r4) {
+          const float4 v = wc[r4];
+          o[4 * r4 + 0] = fmaf(-v.x, t[s2], o[4 * r4 + 0]);
+          o[4 * r4 + 1] = fmaf(-v.y, t[s2], o[4 * r4 + 1]);
+          o[4 * r4 + 2] = fmaf(-v.z, t[s2], o[4 * r4 + 2]);
+          o[4 * r4 + 3] = fmaf(-v.w, t[s2], o[4 * r4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) Wt[(J0 + lane) * kInvLD + I0 + r] = (I0 + r < n) ? o[r] : 0.f;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Leaf POTRF (Alg. 1 base case "A <- POTRF_L(A)") of an n x n block, n <= 128, one CTA of
+// 256 threads, right-looking with the block held in registers.
+//
+// Thread (ti, tj) = (t % 16, t / 16) owns the 64 entries (ti + 16a, tj + 16b), a, b < 8,
+// for the whole factorization.  Step k: the 16 threads owning column k (one half-warp)
+// read the pivot a_kk by a shuffle, check it is positive and finite (first failure:
+// atomicMin of the global column into info, and the CTA stops), form r = 1/sqrt(a_kk) by
+// Newton's method, scale their column entries and publish the column in shared memory;
+// after one barrier every thread applies the rank-1 update to the entries it owns.  The
+// step loop is split as k = 16 KB + kt with KB unrolled, so register indices are static
+// and the blocks a < b or b < KB, which hold no work, are skipped at compile time.
+// Optionally the FP32 inverse of the stored factor is formed for the FP32 leaf TRSM.
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
                   float* __restrict__ W32, int ldw, int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T col[2][128];
   __shared__ int s_fail;
   if (*(volatile int*)info != INT_MAX) return;   // an earlier block failed: stop like LAPACK
-  T* a = reinterpret_cast<T*>(smem_raw);
-  const int lda_s = n + 1;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-
-  for (int idx = tid; idx < n * n; idx += nthr) {
-    int i = idx % n, j = idx / n;
-    if (i >= j) {
-      double v = A[(size_t)j * ld + i];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ti = tid & 15, tj = tid >> 4;
+  T reg[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ti + 16 * a, j = tj + 16 * b;
+      double v = (i < n && j < n && i >= j) ? A[(size_t)j * ld + i] : 0.0;
       if (round16) v = round_to_f16(v);
-      a[j * lda_s + i] = (T)v;
+      reg[a][b] = (T)v;
     }
-  }
   if (tid == 0) s_fail = 0;
   __syncthreads();
 
-  for (int k = 0; k < n; ++k) {
-    if (tid == 0) {
-      T d = a[k * lda_s + k];
-      if (!(d > (T)0) || !isfinite((double)d)) {
-        s_fail = 1;
-        atomicMin(info, col0 + k + 1);
-      } else {
-        a[k * lda_s + k] = dsqrt<T>(d);
+#pragma unroll
+  for (int KB = 0; KB < 8; ++KB) {
+    if (16 * KB >= n) break;
+    for (int kt = 0; kt < 16; ++kt) {
+      const int k = 16 * KB + kt;
+      if (k >= n) break;
+      const int buf = k & 1;
+      // (a) the half-warp owning column k: pivot, 1/sqrt by Newton, scale, publish
+      if (warp == (kt >> 1)) {
+        const int src = ((kt & 1) << 4) + kt;       // lane of thread (ti, tj) = (kt, kt)
+        const T d = __shfl_sync(0xffffffffu, reg[KB][KB], src);
+        const bool mine = (tj == kt);
+        if (!((d > (T)0) && isfinite((double)d))) {
+          if (lane == src) {
+            atomicMin(info, col0 + k + 1);
+            s_fail = 1;
+          }
+        } else if (mine) {
+          const T r = rsqrt_newton(d);
+#pragma unroll
+          for (int a = KB; a < 8; ++a) {
+            const int i = ti + 16 * a;
+            if (i == k) {
+              reg[a][KB] = d * r;
+              col[buf][i] = d * r;
+            } else if (i > k && i < n) {
+              reg[a][KB] *= r;
+              col[buf][i] = reg[a][KB];
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_fail) return;
+      // (b) rank-1 update of the owned entries (i >= j > k)
+      T ci[8], cj[8];
+#pragma unroll
+      for (int a = KB; a < 8; ++a) ci[a] = col[buf][ti + 16 * a];
+#pragma unroll
+      for (int b = KB; b < 8; ++b) cj[b] = col[buf][tj + 16 * b];
+#pragma unroll
+      for (int b = KB; b < 8; ++b) {
+        if (b == KB && tj <= kt) continue;             // j <= k
+#pragma unroll
+        for (int a = b; a < 8; ++a) {
+          if (a == b && ti < tj) continue;             // i < j
+          reg[a][b] -= ci[a] * cj[b];
+        }
       }
     }
-    __syncthreads();
-    if (s_fail) return;
-    const T piv = a[k * lda_s + k];
-    for (int i = k + 1 + tid; i < n; i += nthr) a[k * lda_s + i] = a[k * lda_s + i] / piv;
-    __syncthreads();
-    // trailing update: warp w owns columns j = k+1+w, k+1+w+nwarps, ...; lanes own rows i >= j
-    for (int j = k + 1 + warp; j < n; j += nwarps) {
-      const T ljk = a[k * lda_s + j];
-      for (int i = j + lane; i < n; i += 32) a[j * lda_s + i] -= a[k * lda_s + i] * ljk;
-    }
-    __syncthreads();
   }
-
-  for (int idx = tid; idx < n * n; idx += nthr) {
-    int i = idx % n, j = idx / n;
-    if (i >= j) {
-      double v = (double)a[j * lda_s + i];
-      if (round16) {               // F16 leaf: the stored factor is rounded to FP16
-        v = round_to_f16(v);
-        a[j * lda_s + i] = (T)v;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ti + 16 * a, j = tj + 16 * b;
+      if (i < n && j < n && i >= j) {
+        double v = (double)reg[a][b];
+        if (round16) v = round_to_f16(v);              // F16 leaf: the stored factor is FP16
+        A[(size_t)j * ld + i] = v;
       }
-      A[(size_t)j * ld + i] = v;
     }
-  }
   if (W32 == nullptr) return;
   __syncthreads();
 
-  // ---- FP32 inverse W = fl32(L)^{-1} (lower triangular) ----
-  float* Lf = reinterpret_cast<float*>(smem_raw);          // n x (n+1), column-major
-  float* Wt = Lf + n * lda_s;                               // Wt[i * lda_s + j] = W(i, j)
-  // Lf may overlap a when T == double: read everything into registers first, column by column
-  if (sizeof(T) == sizeof(double)) {
-    for (int j = 0; j < n; ++j) {
-      // gather column j of a (double) then store as float; process in chunks to avoid overlap
-      float v0 = 0.f;
-      int i = tid;
-      if (i < n) v0 = (i >= j) ? (float)a[j * lda_s + i] : 0.f;
-      __syncthreads();
-      // the float column j occupies bytes [4*j*lda_s, 4*(j+1)*lda_s) which lie inside double
-      // columns < j/2+1 <= j, already consumed
-      if (i < n) Lf[j * lda_s + i] = v0;
-      __syncthreads();
+  // ---- FP32 inverse of the stored factor (read back from global, as float) ----
+  float* Lf = reinterpret_cast<float*>(smem_raw);
+  float* Wt = Lf + 128 * kInvLD;
+  const int nb32 = ((n + 31) / 32) * 32;
+  for (int j = warp; j < nb32; j += 8) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = (i < n && j < n && i >= j) ? __ldcg(A + (size_t)j * ld + i) : 0.0;
     }
-  } else {
-    for (int idx = tid; idx < n * n; idx += nthr) {
-      int i = idx % n, j = idx / n;
-      if (i < j) Lf[j * lda_s + i] = 0.f;
-      else Lf[j * lda_s + i] = (float)a[j * lda_s + i];
-    }
-    __syncthreads();
-  }
-  // thread j computes column j of W: w_i = (delta_ij - sum_{kk<i} L_i,kk w_kk) / L_ii
-  if (tid < n) {
-    const int j = tid;
-    const int kstart = (j / 32) * 32;      // w_kk = 0 for kk < j, skip whole warps' worth
-    for (int i = 0; i < kstart && i < n; ++i) Wt[i * lda_s + j] = 0.f;
-    for (int i = kstart; i < n; ++i) {
-      float s0 = (i == j) ? 1.f : 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int kk = kstart;
-      for (; kk + 3 < i; kk += 4) {
-        s0 -= Lf[kk * lda_s + i] * Wt[kk * lda_s + j];
-        s1 -= Lf[(kk + 1) * lda_s + i] * Wt[(kk + 1) * lda_s + j];
-        s2 -= Lf[(kk + 2) * lda_s + i] * Wt[(kk + 2) * lda_s + j];
-        s3 -= Lf[(kk + 3) * lda_s + i] * Wt[(kk + 3) * lda_s + j];
-      }
-      for (; kk < i; ++kk) s0 -= Lf[kk * lda_s + i] * Wt[kk * lda_s + j];
-      float w = ((s0 + s1) + (s2 + s3)) / Lf[i * lda_s + i];
-      Wt[i * lda_s + j] = (i < j) ? 0.f : w;
-    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (lane + 32 * q < nb32) Lf[j * kInvLD + lane + 32 * q] = (float)v[q];
   }
   __syncthreads();
-  for (int idx = tid; idx < n * n; idx += nthr) {
-    int i = idx % n, j = idx / n;
-    W32[(size_t)j * ldw + i] = (i >= j) ? Wt[i * lda_s + j] : 0.f;
-  }
+  trtri32_blocked(Lf, Wt, n);
+  for (int j = warp; j < n; j += 8)
+    for (int i = lane; i < n; i += 32) W32[(size_t)j * ldw + i] = (i >= j) ? Wt[j * kInvLD + i] : 0.f;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -190,75 +284,95 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
 
 // ---------------------------------------------------------------------------------------
 // Leaf TRSM in FP32 through the inverse of the diagonal block: X = fl32(B) W^T with
-// W = fl32(L)^{-1} precomputed by the leaf POTRF.  One CTA owns 64 full rows of the
-// panel (so reading B and writing X in place never race), 256 threads, each thread a
+// W = fl32(L)^{-1} precomputed by the leaf POTRF.  One CTA owns 32 full rows of the
+// panel (so reading B and writing X in place never race), 128 threads, each thread a
 // 4-row x (nc/16)-column register tile.
 // ---------------------------------------------------------------------------------------
-constexpr int kT32Rows = 64;
+constexpr int kT32Rows = 32;
+constexpr int kT32Threads = 128;
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+constexpr int kT32WLD = 132;   // row stride of W in shared memory (16-byte rows)
+
+__global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
                   const int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
-  float* Bs = reinterpret_cast<float*>(smem_raw);       // Bs[k * 64 + r]
-  float* Ws = Bs + nc * kT32Rows;                       // Ws[k * ncp + j] = W(j, k)
-  const int ncp = nc + 1;
-  const int tid = threadIdx.x;
+  float* Ws = reinterpret_cast<float*>(smem_raw);                 // Ws[k * 132 + j] = W(j, k)
+  double* Bd = reinterpret_cast<double*>(Ws + 128 * kT32WLD);      // Bd[k * 32 + r]
+  float* Bs = reinterpret_cast<float*>(Bd + 128 * kT32Rows);       // Bs[k * 32 + r]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kT32Rows;
-  for (int idx = tid; idx < kT32Rows * nc; idx += 256) {
-    int r = idx % kT32Rows, k = idx / kT32Rows;
-    int gr = row0 + r;
-    Bs[k * kT32Rows + r] = (gr < m) ? (float)A[(size_t)(c0 + k) * ld + (r0 + gr)] : 0.f;
+  // all copies in flight at once: W rows (512 B each, 16-byte pieces) and the B panel
+  // (8-byte pieces, rows past m read row m-1 and are never stored)
+  for (int e = tid; e < nc * 32; e += kT32Threads) {
+    const int k = e >> 5, q = e & 31;
+    cp_async16(Ws + k * kT32WLD + 4 * q, W + (size_t)k * ldw + 4 * q);
   }
-  for (int idx = tid; idx < nc * nc; idx += 256) {
-    int j = idx % nc, k = idx / nc;                     // W stored column-major: W[k*ldw + j] = W(j,k)
-    Ws[k * ncp + j] = W[(size_t)k * ldw + j];
+  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
+    const int k = e >> 5, r = e & 31;
+    const int gr = min(row0 + r, m - 1);
+    cp_async8(Bd + k * kT32Rows + r, A + (size_t)(c0 + k) * ld + (r0 + gr));
   }
+  cp_async_wait_all();
   __syncthreads();
-  const int rq = (tid & 15) * 4;                        // rows rq..rq+3
-  const int cg = tid >> 4;                              // columns cg, cg+16, ...
-  constexpr int MAXC = 9;                               // nc <= 144
-  float acc[4][MAXC];
+  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) Bs[e] = (float)Bd[e];
+  __syncthreads();
+  // thread: rows 8*tr .. 8*tr+7, columns 4*tc .. 4*tc+3 (8 x 4 register tile, float4 loads)
+  const int tr = tid & 3, tc = tid >> 2;
+  const bool active = 4 * tc < nc;
+  float acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int c = 0; c < MAXC; ++c) acc[a][c] = 0.f;
-  const int ncol = (nc - cg + 15) / 16;
-  for (int k = 0; k < nc; ++k) {
-    float4 b = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + rq]);
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  if (active) {
+    for (int k = 0; k < nc; ++k) {
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr + 4]);
+      const float4 w = *reinterpret_cast<const float4*>(&Ws[k * kT32WLD + 4 * tc]);
+      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const float ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-    for (int c = 0; c < MAXC; ++c) {
-      if (c < ncol) {
-        float w = Ws[k * ncp + cg + 16 * c];
-        acc[0][c] += b.x * w;
-        acc[1][c] += b.y * w;
-        acc[2][c] += b.z * w;
-        acc[3][c] += b.w * w;
-      }
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bb[a], ww[c], acc[a][c]);
     }
   }
   __syncthreads();
   // stage X (float) back into Bs, then write master and shadow coalesced
+  if (active) {
 #pragma unroll
-  for (int c = 0; c < MAXC; ++c) {
-    if (c < ncol) {
-      int j = cg + 16 * c;
+    for (int c = 0; c < 4; ++c) {
+      const int j = 4 * tc + c;
+      if (j < nc)
 #pragma unroll
-      for (int a = 0; a < 4; ++a) Bs[j * kT32Rows + rq + a] = acc[a][c];
+        for (int a = 0; a < 8; ++a) Bs[j * kT32Rows + 8 * tr + a] = acc[a][c];
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < kT32Rows * nc; idx += 256) {
-    int r = idx % kT32Rows, k = idx / kT32Rows;
-    int gr = row0 + r;
-    if (gr < m) A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[k * kT32Rows + r];
+  {
+    const int gr = row0 + lane;
+    for (int k = warp; k < nc; k += kT32Threads / 32)
+      if (gr < m) A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[k * kT32Rows + lane];
   }
   if (S != nullptr) {
-    for (int idx = tid; idx < kT32Rows * nc; idx += 256) {
-      int k = idx % nc, r = idx / nc;
-      int gr = row0 + r;
+    for (int idx = tid; idx < kT32Rows * nc; idx += kT32Threads) {
+      const int k = idx % nc, r = idx / nc;
+      const int gr = row0 + r;
       if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + k)] = __double2half((double)Bs[k * kT32Rows + r]);
     }
   }
@@ -270,20 +384,20 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
                               float* W32, int ldw, int* info, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 128) return cudaErrorInvalidValue;
-  size_t bytes_a = (size_t)n * (n + 1) * (compute64 ? 8 : 4);
-  size_t bytes_w = W32 ? (size_t)2 * n * (n + 1) * 4 : 0;
-  size_t smem = bytes_a > bytes_w ? bytes_a : bytes_w;
-  if (!compute64 && W32) smem = bytes_a + (size_t)n * (n + 1) * 4;
-  cudaError_t e;
-  if (compute64) {
-    e = cudaFuncSetAttribute(potrf_leaf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = W32 ? (size_t)2 * 128 * kInvLD * 4 : 0;
+  static bool attr_done = false;     // one opt-in to the largest footprint (n = 128, with W)
+  if (!attr_done) {
+    const int maxb = (int)((size_t)2 * 128 * kInvLD * 4);
+    cudaError_t e = cudaFuncSetAttribute(potrf_leaf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(potrf_leaf_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
     if (e != cudaSuccess) return e;
-    potrf_leaf_kernel<double><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
-  } else {
-    e = cudaFuncSetAttribute(potrf_leaf_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    potrf_leaf_kernel<float><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+    attr_done = true;
   }
+  if (compute64)
+    potrf_leaf_kernel<double><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+  else
+    potrf_leaf_kernel<float><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
   return cudaGetLastError();
 }
 
@@ -293,8 +407,13 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = nc <= 128 ? 64 : 32;
   size_t smem = ((size_t)nc * nc + (size_t)RT * nc) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(((size_t)144 * 144 + (size_t)32 * 144) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
   int grid = (m + RT - 1) / RT;
   trsm_subst_kernel<double><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, info, RT);
   return cudaGetLastError();
@@ -306,8 +425,13 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = 64;
   size_t smem = ((size_t)nc * nc + (size_t)RT * nc) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(((size_t)144 * 144 + (size_t)64 * 144) * sizeof(float)));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
   int grid = (m + RT - 1) / RT;
   trsm_subst_kernel<float><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, info, RT);
   return cudaGetLastError();
@@ -318,11 +442,16 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const int* info, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
-  size_t smem = ((size_t)nc * kT32Rows + (size_t)nc * (nc + 1)) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(trsm_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (nc > 128) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)128 * kT32WLD * 4 + (size_t)128 * kT32Rows * 8 + (size_t)128 * kT32Rows * 4;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(trsm_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
   int grid = (m + kT32Rows - 1) / kT32Rows;
-  trsm_inv32_kernel<<<grid, 256, smem, s>>>(A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, info);
+  trsm_inv32_kernel<<<grid, kT32Threads, smem, s>>>(A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, info);
   return cudaGetLastError();
 }
 

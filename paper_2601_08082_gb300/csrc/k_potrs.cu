@@ -1,12 +1,18 @@
 // POTRS: solve A X = B with the Cholesky factor, L Y = B then L^T X = Y.
 //
-// One launch per sweep.  The n rows are cut into 64-row blocks; each CTA takes the next
-// block in the sweep order from an atomic ticket (so every block it waits for belongs to
-// a CTA that started earlier and is resident: no deadlock), accumulates the off-diagonal
-// products of already-solved blocks as soon as their ready flags are published
-// (release/acquire at GPU scope), then substitutes through its 64 x 64 diagonal block with
-// one warp per right-hand side (rows held two per lane, pivots broadcast by shuffles).
-// Waits are bounded by %globaltimer; on expiry the CTA records DEV_ERR_TIMEOUT and stops.
+// Two launches per sweep pair plus one pre-pass:
+//   1. inverse pre-pass: every 64 x 64 diagonal block L_rr is inverted in parallel (one
+//      CTA per block, right-looking, all columns at once), W_r = L_rr^{-1}.
+//   2. forward sweep: the rows are cut into 64-row blocks; each CTA takes the next block
+//      in sweep order from an atomic ticket (every block it waits for belongs to a CTA
+//      that started earlier and is resident: no deadlock).  As soon as a solved block's
+//      ready flag is published (release/acquire at GPU scope) the CTA accumulates its
+//      off-diagonal product, 4 threads per row each over 16 columns with all 16 loads in
+//      flight; at the end y_r = W_r (b_r - sum_j L_rj y_j) is a small matrix product, so
+//      no division sits on the dependency chain between blocks.
+//   3. backward sweep, the same with L^T: x_r = W_r^T (y_r - sum_{j>r} L_jr^T x_j).
+// All waits are bounded by %globaltimer: on expiry the CTA records DEV_ERR_TIMEOUT and
+// stops instead of spinning forever.
 #include "hrp_internal.cuh"
 
 namespace hrp {
@@ -29,168 +35,200 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// thread 0 waits for flags[j] == epoch; returns false on timeout
 __device__ bool wait_flag(const int* flags, int j, int epoch) {
   if (ld_acquire(flags + j) == epoch) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
-    for (int i = 0; i < 64; ++i)
+    for (int i = 0; i < 16; ++i) {
       if (ld_acquire(flags + j) == epoch) return true;
+      __nanosleep(64);
+    }
     if (gtimer() - t0 > kWaitTimeoutNs) return false;
   }
 }
 
+// ---- 1. W_r = L_rr^{-1} for every 64-row diagonal block (one CTA each) ----
+template <typename T>
+__global__ void __launch_bounds__(PT)
+potrs_diag_inverse_kernel(const double* __restrict__ L, int ldl, int n, T* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T (*Ls)[PB + 1] = reinterpret_cast<T (*)[PB + 1]>(smem_raw);               // Ls[i][k] = L(R0+i, R0+k)
+  T (*Ws)[PB + 1] = reinterpret_cast<T (*)[PB + 1]>(smem_raw + sizeof(T) * PB * (PB + 1));  // W(i, c)
+  __shared__ T rinv[PB];
+  const int r = blockIdx.x, R0 = r * PB, rows = min(PB, n - R0);
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < PB * PB; idx += PT) {
+    const int i = idx % PB, k = idx / PB;
+    const T v = (i < rows && k < rows && i >= k) ? (T)L[(size_t)(R0 + k) * ldl + R0 + i] : (T)0;
+    Ls[i][k] = v;
+    Ws[i][k] = (i == k) ? (T)1 : (T)0;      // right-hand side: the identity
+  }
+  __syncthreads();
+  if (tid < PB) rinv[tid] = (tid < rows) ? (T)1 / Ls[tid][tid] : (T)1;
+  __syncthreads();
+  // right-looking forward substitution on all 64 columns of the identity at once:
+  // step k finalizes row k (w_kc = acc_kc / l_kk) and removes it from rows i > k
+  for (int k = 0; k < rows; ++k) {
+    if (tid <= k) Ws[k][tid] *= rinv[k];
+    __syncthreads();
+    const int cnt = (rows - 1 - k) * (k + 1);   // (i > k) x (c <= k)
+    for (int e = tid; e < cnt; e += PT) {
+      const int i = k + 1 + e / (k + 1), c = e % (k + 1);
+      Ws[i][c] -= Ls[i][k] * Ws[k][c];
+    }
+    __syncthreads();
+  }
+  // store W_r column-major (ld 64) at W + r * 64 * 64
+  T* Wr = W + (size_t)r * PB * PB;
+  for (int idx = tid; idx < PB * PB; idx += PT) {
+    const int i = idx % PB, c = idx / PB;
+    Wr[c * PB + i] = (i >= c && i < rows) ? Ws[i][c] : (T)0;
+  }
+}
+
+// ---- 2/3. sweeps ----
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(PT)
-potrs_sweep_kernel(const double* __restrict__ L, int ldl, double* __restrict__ B, int ldb, int n, int nrhs,
-                   int* __restrict__ ticket, int* __restrict__ flags, int epoch, unsigned* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ld = reinterpret_cast<T*>(smem_raw);   // diagonal block, Ld[k * 65 + i] = L(R0 + i, R0 + k)
-  T* yS = Ld + PB * (PB + 1);               // solved block of another CTA
-  T* accS = yS + MAX_RHS * PB;
-  T* Ls = accS + MAX_RHS * PB;              // off-diagonal block (backward sweep staging)
+potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ W, double* __restrict__ B, int ldb,
+                   int n, int nrhs, int* __restrict__ ticket, int* __restrict__ flags, int epoch,
+                   unsigned* __restrict__ err) {
+  __shared__ T yS[MAX_RHS][PB];          // solved block of another CTA; later the reduced rhs
+  __shared__ T part[4][MAX_RHS][PB];     // per-chunk partial sums
   __shared__ int s_r, s_abort;
+  T (*accS)[PB] = yS;
   const int tid = threadIdx.x;
   const int nb = (n + PB - 1) / PB;
   if (tid == 0) {
-    int t = atomicAdd(ticket, 1);
+    const int t = atomicAdd(ticket, 1);
     s_r = FWD ? t : nb - 1 - t;
     s_abort = 0;
   }
   __syncthreads();
-  const int r = s_r;
-  const int R0 = r * PB;
-  const int rows = min(PB, n - R0);
-  for (int idx = tid; idx < PB * PB; idx += PT) {
-    int i = idx % PB, k = idx / PB;
-    Ld[k * (PB + 1) + i] = (i < rows && k < rows && i >= k) ? (T)L[(size_t)(R0 + k) * ldl + R0 + i] : (T)0;
-  }
-  const int i = tid % PB, g = tid / PB;    // row i, rhs group g: columns g, g+4, g+8, g+12
-  T acc[4];
+  const int r = s_r, R0 = r * PB, rows = min(PB, n - R0);
+  const int i = tid % PB, ch = tid / PB;           // row i, k-chunk ch (16 columns each)
+  T acc[MAX_RHS];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int c = g + 4 * q;
-    acc[q] = (c < nrhs && i < rows) ? (T)B[(size_t)c * ldb + R0 + i] : (T)0;
+  for (int c = 0; c < MAX_RHS; ++c) acc[c] = (T)0;
+
+  // W_r does not depend on other blocks: fetch this thread's 16 entries now
+  const T* Wr = W + (size_t)r * PB * PB;      // column-major, ld 64
+  T wv[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int kk = ch * 16 + q;
+    wv[q] = FWD ? Wr[kk * PB + i] : Wr[i * PB + kk];
   }
-  const int jbeg = FWD ? 0 : r + 1;
-  const int jend = FWD ? r : nb;
-  for (int j = jbeg; j < jend; ++j) {
+  // dependencies in the order they complete: j = 0, 1, .. (forward), nb-1, nb-2, .. (backward)
+  const int ndep = FWD ? r : nb - 1 - r;
+  for (int jj = 0; jj < ndep; ++jj) {
+    const int j = FWD ? jj : nb - 1 - jj;
+    const int J0 = j * PB, jrows = min(PB, n - J0);
+    // this thread's 16 factor entries do not depend on the flag: load them first
+    T lv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int kk = ch * 16 + q;
+      if (FWD) lv[q] = (kk < jrows && i < rows) ? (T)L[(size_t)(J0 + kk) * ldl + R0 + i] : (T)0;
+      else lv[q] = (kk < jrows && i < rows) ? (T)L[(size_t)(R0 + i) * ldl + J0 + kk] : (T)0;
+    }
     if (tid == 0 && !wait_flag(flags, j, epoch)) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       s_abort = 1;
     }
     __syncthreads();
     if (s_abort) return;
-    const int J0 = j * PB;
-    const int jrows = min(PB, n - J0);
     for (int idx = tid; idx < nrhs * PB; idx += PT) {
-      int kk = idx % PB, c = idx / PB;
-      yS[c * PB + kk] = (kk < jrows) ? (T)__ldcg(B + (size_t)c * ldb + J0 + kk) : (T)0;
-    }
-    if (!FWD) {
-      // stage L(J0 + kk, R0 + i) as Ls[i * 65 + kk] (coalesced along kk)
-      for (int idx = tid; idx < PB * PB; idx += PT) {
-        int kk = idx % PB, ii = idx / PB;
-        Ls[ii * (PB + 1) + kk] = (kk < jrows && ii < rows) ? (T)L[(size_t)(R0 + ii) * ldl + J0 + kk] : (T)0;
-      }
+      const int kk = idx % PB, c = idx / PB;
+      yS[c][kk] = (kk < jrows) ? (T)__ldcg(B + (size_t)c * ldb + J0 + kk) : (T)0;
     }
     __syncthreads();
-    if (i < rows) {
-      if (FWD) {
-        for (int kk = 0; kk < jrows; ++kk) {
-          const T l = (T)L[(size_t)(J0 + kk) * ldl + R0 + i];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (g + 4 * q < nrhs) acc[q] -= l * yS[(g + 4 * q) * PB + kk];
-        }
-      } else {
-        for (int kk = 0; kk < jrows; ++kk) {
-          const T l = Ls[i * (PB + 1) + kk];
+    for (int c = 0; c < MAX_RHS; ++c) {
+      if (c < nrhs) {
+        T s = (T)0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (g + 4 * q < nrhs) acc[q] -= l * yS[(g + 4 * q) * PB + kk];
-        }
+        for (int q = 0; q < 16; ++q) s = fma(lv[q], yS[c][ch * 16 + q], s);
+        acc[c] += s;
       }
     }
     __syncthreads();
   }
+  // reduce the four chunks, subtract from the right-hand side
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int c = g + 4 * q;
-    if (c < nrhs) accS[c * PB + i] = acc[q];
+  for (int c = 0; c < MAX_RHS; ++c)
+    if (c < nrhs) part[ch][c][i] = acc[c];
+  __syncthreads();
+  for (int idx = tid; idx < nrhs * PB; idx += PT) {
+    const int ii = idx % PB, c = idx / PB;
+    const T b = (ii < rows) ? (T)B[(size_t)c * ldb + R0 + ii] : (T)0;
+    accS[c][ii] = b - ((part[0][c][ii] + part[1][c][ii]) + (part[2][c][ii] + part[3][c][ii]));
   }
   __syncthreads();
-  // diagonal block: one warp per right-hand side, lane owns rows lane and lane + 32
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int c = warp; c < nrhs; c += PT / 32) {
-    T a0 = accS[c * PB + lane], a1 = accS[c * PB + lane + 32];
-    if (FWD) {
-      for (int k = 0; k < rows; ++k) {
-        T v = __shfl_sync(0xffffffffu, (k < 32) ? a0 : a1, k & 31);
-        T yk = v / Ld[k * (PB + 1) + k];
-        if (k < 32) { if (lane == k) a0 = yk; } else { if (lane == k - 32) a1 = yk; }
-        if (lane > k) a0 -= Ld[k * (PB + 1) + lane] * yk;
-        if (lane + 32 > k) a1 -= Ld[k * (PB + 1) + lane + 32] * yk;
-      }
-    } else {
-      for (int k = rows - 1; k >= 0; --k) {
-        T v = __shfl_sync(0xffffffffu, (k < 32) ? a0 : a1, k & 31);
-        T xk = v / Ld[k * (PB + 1) + k];
-        if (k < 32) { if (lane == k) a0 = xk; } else { if (lane == k - 32) a1 = xk; }
-        // rows i < k: a_i -= L(k, i) x_k
-        if (lane < k) a0 -= Ld[lane * (PB + 1) + k] * xk;
-        if (lane + 32 < k) a1 -= Ld[(lane + 32) * (PB + 1) + k] * xk;
-      }
+  // y_r = W_r acc (forward) or x_r = W_r^T acc (backward): row i, chunk ch of 16 columns
+#pragma unroll
+  for (int c = 0; c < MAX_RHS; ++c) {
+    if (c < nrhs) {
+      T s = (T)0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) s = fma(wv[q], accS[c][ch * 16 + q], s);
+      part[ch][c][i] = s;
     }
-    if (lane < rows) B[(size_t)c * ldb + R0 + lane] = (double)a0;
-    if (lane + 32 < rows) B[(size_t)c * ldb + R0 + lane + 32] = (double)a1;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nrhs * PB; idx += PT) {
+    const int ii = idx % PB, c = idx / PB;
+    if (ii < rows)
+      B[(size_t)c * ldb + R0 + ii] =
+          (double)((part[0][c][ii] + part[1][c][ii]) + (part[2][c][ii] + part[3][c][ii]));
   }
   __threadfence();
   __syncthreads();
   if (tid == 0) st_release(flags + r, epoch);
 }
 
-template <typename T, bool FWD>
-size_t potrs_smem() {
-  return sizeof(T) * ((size_t)PB * (PB + 1) * (FWD ? 1 : 2) + 2 * (size_t)MAX_RHS * PB);
-}
-
-template <typename T, bool FWD>
-cudaError_t potrs_launch_one(const double* L, int ldl, double* B, int ldb, int n, int nrhs, int* ticket, int* flags,
-                             int epoch, unsigned* err, cudaStream_t s) {
-  const size_t smem = potrs_smem<T, FWD>();
-  cudaError_t e = cudaFuncSetAttribute(potrs_sweep_kernel<T, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+template <typename T>
+cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrhs, T* W, int* ticket, int* flags,
+                    int epoch, unsigned* err, cudaStream_t s) {
   const int nb = (n + PB - 1) / PB;
-  potrs_sweep_kernel<T, FWD><<<nb, PT, smem, s>>>(L, ldl, B, ldb, n, nrhs, ticket, flags, epoch, err);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32,
-                         int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s) {
-  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const size_t smem = 2 * sizeof(T) * PB * (PB + 1);
+  static bool attr_done = false;
+  cudaError_t e;
+  if (!attr_done) {
+    if ((e = cudaFuncSetAttribute(potrs_diag_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    attr_done = true;
+  }
+  potrs_diag_inverse_kernel<T><<<nb, PT, smem, s>>>(L, ldl, n, W);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   for (int c0 = 0; c0 < nrhs; c0 += MAX_RHS) {
     const int nc = nrhs - c0 < MAX_RHS ? nrhs - c0 : MAX_RHS;
     double* Bc = B + (size_t)c0 * ldb;
     for (int pass = 0; pass < 2; ++pass) {
       const int ep = epoch + 2 * (c0 / MAX_RHS) + pass;
-      cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(int), s);
-      if (e != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(ticket, 0, sizeof(int), s)) != cudaSuccess) return e;
       if (pass == 0)
-        e = fp32 ? potrs_launch_one<float, true>(L, ldl, Bc, ldb, n, nc, ticket, flags, ep, dev_err, s)
-                 : potrs_launch_one<double, true>(L, ldl, Bc, ldb, n, nc, ticket, flags, ep, dev_err, s);
+        potrs_sweep_kernel<T, true><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ep, err);
       else
-        e = fp32 ? potrs_launch_one<float, false>(L, ldl, Bc, ldb, n, nc, ticket, flags, ep, dev_err, s)
-                 : potrs_launch_one<double, false>(L, ldl, Bc, ldb, n, nc, ticket, flags, ep, dev_err, s);
-      if (e != cudaSuccess) return e;
+        potrs_sweep_kernel<T, false><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ep, err);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
 }
 
-// number of epochs consumed by one launch_potrs call
+}  // namespace
+
+size_t potrs_workspace_bytes(int n) { return (size_t)((n + PB - 1) / PB) * PB * PB * sizeof(double); }
+
+cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32, void* work,
+                         int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  if (fp32) return potrs_t<float>(L, ldl, B, ldb, n, nrhs, static_cast<float*>(work), ticket, flags, epoch, dev_err, s);
+  return potrs_t<double>(L, ldl, B, ldb, n, nrhs, static_cast<double*>(work), ticket, flags, epoch, dev_err, s);
+}
+
 int potrs_epochs(int nrhs) { return 2 * ((nrhs + MAX_RHS - 1) / MAX_RHS); }
 
 }  // namespace hrp

@@ -35,7 +35,7 @@ EXPORTED = [
 class Tree(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("level", ctypes.c_int * HRP_MAX_DEPTH), ("leaf", ctypes.c_int),
                 ("inner", ctypes.c_int), ("inner_size", ctypes.c_int), ("trsm_leaf", ctypes.c_int),
-                ("syrk_leaf", ctypes.c_int), ("scale_block", ctypes.c_int)]
+                ("syrk_leaf", ctypes.c_int), ("scale_block", ctypes.c_int), ("trsm_compute", ctypes.c_int)]
 
 
 class HrpError(RuntimeError):
@@ -80,13 +80,15 @@ def load(path: str = LIB_PATH):
     return L
 
 
-def tree_parse(spec: str, leaf: int = 128, trsm_leaf: int = 0, syrk_leaf: int = 0) -> Tree:
+def tree_parse(spec: str, leaf: int = 128, trsm_leaf: int = 0, syrk_leaf: int = 0,
+               trsm_fp64: bool = False) -> Tree:
     t = Tree()
     st = load().hrp_tree_parse(spec.encode(), leaf, ctypes.byref(t))
     if st != 0:
         raise HrpError(st, f"bad tree spec {spec!r}")
     t.trsm_leaf = trsm_leaf
     t.syrk_leaf = syrk_leaf
+    t.trsm_compute = 1 if trsm_fp64 else 0
     return t
 
 
