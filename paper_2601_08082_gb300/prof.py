@@ -1,0 +1,53 @@
+"""Run a few factorizations (and optionally solves) of one workload, for profilers.
+
+Example (launch list of two factorizations of the n = 8192 mixed workload):
+    ncu --metrics gpu__time_duration.sum --clock-control none --csv \
+        python -m paper_2601_08082_gb300.prof --n 8192 --reps 2
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--rho", type=float, default=2.0)
+    ap.add_argument("--tree", default="[F16,F16,F16,F16,F32|F64@128]")
+    ap.add_argument("--leaf", type=int, default=128)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--nrhs", type=int, default=0, help="also solve with this many right-hand sides")
+    args = ap.parse_args()
+
+    import torch
+
+    from synth import dominant_spd, rhs, seed_for
+    from . import hrp
+
+    h = hrp.Handle(0)
+    A0 = hrp.colmajor(dominant_spd(args.n, args.rho, seed_for(1, 0))).cuda()
+    B0 = hrp.colmajor(rhs(args.n, args.nrhs, seed_for(1, 1))).cuda() if args.nrhs else None
+    tree = hrp.tree_parse(args.tree, leaf=args.leaf)
+    for _ in range(args.reps):
+        A = A0.clone()
+        info = h.potrf(tree, A)
+        if info:
+            print(f"info = {info}")
+            return 1
+        if B0 is not None:
+            B = B0.clone()
+            h.potrs(A, B)
+    torch.cuda.synchronize()
+    print(f"{args.reps} factorizations of n={args.n} tree {args.tree}: {h.launch_count()} launches each")
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
