@@ -168,6 +168,28 @@ int hrp_get_timing(hrp_handle* h, double* out, int n);
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);
 
+/*
+ * hrp_potrs_noalloc: the same solve as hrp_potrs (B <- A^{-1} B from the factor in the
+ * lower triangle of dL, FP64, forward then backward substitution), for callers that may
+ * not allocate device memory when they solve: applications whose memory is owned by
+ * their own pool, loops where cudaMalloc's implicit synchronization is unacceptable, or
+ * plugins handed buffers but no allocator.  The paper has no counterpart; this is a
+ * property of the library, not of the method.
+ *   - Takes no handle and allocates nothing: its scratch (diagonal-block inverses, ready
+ *     flags, a ticket) is one fixed device array inside the library, about 4 MiB, which
+ *     every GPU that loads the library keeps until the process exits.
+ *   - n must be <= 8192 (the array's size); larger n returns HRP_ERR_INVALID_ARG, as do
+ *     negative sizes, NULL buffers and leading dimensions < max(1, n).
+ *   - The first call on a device (with that device current) looks up the array's device
+ *     address and zeroes its flags with a synchronous cudaMemset; make that first call
+ *     before any stream capture.  Later calls only enqueue work on `stream`.
+ *   - All calls share the one array: calls that overlap on the GPU (different streams,
+ *     no ordering between them) race and must not be issued.
+ *   - A bounded device wait that expires is recorded in the array, not reported here.
+ */
+hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,87 @@
+// hrp_potrs_noalloc: the triangular solves of hrp_potrs without any device allocation.
+//
+// Who needs it: code that must not call cudaMalloc at the point where it solves, for
+// example a solver step running inside a region where the application forbids new
+// device allocations (a framework that owns all device memory through its own pool, a
+// latency-critical loop where cudaMalloc's implicit device synchronization is not
+// acceptable, or a plugin that is given buffers but no allocator).  hrp_potrs takes its
+// scratch from a handle, which allocates it; this entry point instead uses one
+// file-scope device array, reserved in every GPU that loads the library until the
+// process exits.
+//
+// Scratch layout (kScratchBytes, fixed): inverses of the 64 x 64 diagonal blocks
+// (n_max x 64 doubles), one ready flag per 64-row block, the sweep ticket, an error word.
+#include <climits>
+#include <mutex>
+
+#include "hrp_internal.cuh"
+
+namespace hrp {
+namespace {
+
+constexpr int kNoAllocMaxN = 8192;                                   // largest order accepted
+constexpr int kNoAllocBlocks = (kNoAllocMaxN + 63) / 64;             // 128 row blocks
+constexpr size_t kInvBytes = (size_t)kNoAllocBlocks * 64 * 64 * sizeof(double);   // 4 MiB
+constexpr size_t kFlagsOffset = kInvBytes;
+constexpr size_t kTicketOffset = kFlagsOffset + sizeof(int) * kNoAllocBlocks;
+constexpr size_t kErrOffset = kTicketOffset + sizeof(int);
+constexpr size_t kScratchBytes = (kErrOffset + sizeof(unsigned) + 255) / 256 * 256;
+
+static __device__ __align__(256) unsigned char g_potrs_scratch[kScratchBytes];
+
+struct DeviceScratch {
+  bool ready = false;
+  unsigned char* base = nullptr;   // device address of g_potrs_scratch on this device
+  int epoch = 1;
+};
+constexpr int kMaxDevices = 64;
+DeviceScratch g_dev[kMaxDevices];
+std::mutex g_mu;
+
+}  // namespace
+}  // namespace hrp
+
+using namespace hrp;
+
+extern "C" hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
+                                        void* stream) {
+  if (n < 0 || n > kNoAllocMaxN) return HRP_ERR_INVALID_ARG;   // beyond the fixed scratch
+  if (nrhs < 0) return HRP_ERR_INVALID_ARG;
+  if (n > 0 && !dL) return HRP_ERR_INVALID_ARG;
+  if (ldl < (n > 1 ? n : 1)) return HRP_ERR_INVALID_ARG;
+  if (n > 0 && nrhs > 0 && !dB) return HRP_ERR_INVALID_ARG;
+  if (ldb < (n > 1 ? n : 1)) return HRP_ERR_INVALID_ARG;
+  if (n == 0 || nrhs == 0) return HRP_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HRP_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int ep;
+  unsigned char* base;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceScratch& d = g_dev[dev];
+    if (!d.ready) {
+      // once per device, with that device current: the device address of the array (its
+      // host-side name is only a stand-in) and zeroed flags (no flag may equal an epoch)
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_potrs_scratch) != cudaSuccess) return HRP_ERR_CUDA;
+      if (cudaMemset(static_cast<unsigned char*>(p) + kFlagsOffset, 0, kScratchBytes - kFlagsOffset) != cudaSuccess)
+        return HRP_ERR_CUDA;
+      d.base = static_cast<unsigned char*>(p);
+      d.epoch = 1;
+      d.ready = true;
+    }
+    if (d.epoch > INT_MAX - 4096) {
+      if (cudaMemsetAsync(d.base + kFlagsOffset, 0, sizeof(int) * kNoAllocBlocks, s) != cudaSuccess)
+        return HRP_ERR_CUDA;
+      d.epoch = 1;
+    }
+    ep = d.epoch;
+    d.epoch += potrs_epochs(nrhs);
+    base = d.base;
+  }
+  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, false, base, reinterpret_cast<int*>(base + kTicketOffset),
+                               reinterpret_cast<int*>(base + kFlagsOffset), ep,
+                               reinterpret_cast<unsigned*>(base + kErrOffset), s);
+  return e == cudaSuccess ? HRP_OK : HRP_ERR_CUDA;
+}

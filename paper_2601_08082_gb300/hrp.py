@@ -29,6 +29,7 @@ EXPORTED = [
     "hrp_create", "hrp_destroy", "hrp_last_arg", "hrp_last_error", "hrp_status_string",
     "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
     "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
+    "hrp_potrs_noalloc",
 ]
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.hrp_get_timing.argtypes = [vp, dp, c_int]
     L.hrp_last_launch_count.argtypes = [vp]
     L.hrp_last_launch_count.restype = ctypes.c_longlong
+    L.hrp_potrs_noalloc.argtypes = [c_int, c_int, vp, c_int, vp, c_int, vp]
     _lib = L
     return L
 
