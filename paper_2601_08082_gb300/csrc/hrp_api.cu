@@ -40,6 +40,10 @@ struct hrp_handle_s {
   size_t shadow_cap = 0;       // elements
   float* w32 = nullptr;
   size_t w32_cap = 0;          // elements
+  __half* shadow8 = nullptr;   // E4M3 values (times 2^G, exact) in FP16 storage
+  size_t shadow8_cap = 0;
+  int* tile_exp = nullptr;     // power-of-two scale exponent of every 128 x 128 tile
+  size_t tile_exp_cap = 0;
   double* fact = nullptr;      // posv factor copy
   size_t fact_cap = 0;
   double* work = nullptr;      // posv residual/correction
@@ -120,6 +124,8 @@ hrp_status validate_tree(hrp_handle* h, const hrp_tree* t, int pos) {
   int sl = t->syrk_leaf ? t->syrk_leaf : t->leaf;
   if (sl < 1) return bad_arg(h, pos, "syrk_leaf < 0");
   if (t->trsm_compute != 0 && t->trsm_compute != 1) return bad_arg(h, pos, "trsm_compute must be 0 or 1");
+  if (t->level[t->depth - 1] == HRP_F8E4M3 && t->inner_size < t->leaf)
+    return bad_arg(h, pos, "the innermost (diagonal) precision cannot be F8");
   return HRP_OK;
 }
 
@@ -143,6 +149,8 @@ struct Fact {
   __half* shadow;       // null if no F16 level
   int lds;
   float* w32;           // null if every level is F64
+  __half* shadow8;      // null if no F8 level
+  int* tile_exp;
   bool tc;
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
   cudaError_t err = cudaSuccess;
@@ -204,6 +212,7 @@ struct Fact {
     begin(CLS_TRSM, (double)m * nc * nc);
     if (p == HRP_F64 || t->trsm_compute == 1) {
       chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
+      quant8(r0, m, c0, nc);
       return;
     }
     auto it = leaves.find(c0);
@@ -212,6 +221,15 @@ struct Fact {
     } else {
       chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
     }
+    quant8(r0, m, c0, nc);
+  }
+
+  // FP8 levels: E4M3 tiles of every finished panel (scale per 128 x 128 tile)
+  static constexpr int kG = 8;   // storage upshift: entries are 2^8 s e4m3(x/s)
+  void quant8(int r0, int m, int c0, int nc) {
+    if (!shadow8) return;
+    begin(CLS_OTHER, 0.0);
+    chk(launch_quant_e4m3(A, lda, r0, m, c0, nc, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
   }
 
   // C = A[r0:r0+m, c0:c0+nd] -= X Y^T, X = A[r0:r0+m, k0:k0+k], Y = A[c0:c0+nd, k0:k0+k]
@@ -221,7 +239,7 @@ struct Fact {
     const double* X = A + (size_t)k0 * lda + r0;
     const double* Y = A + (size_t)k0 * lda + c0;
     const double fl = lower ? (double)m * (m + 1) * k : 2.0 * m * nd * k;
-    const bool use_tc = p == HRP_F16 && tc && shadow && (k0 % 8) == 0 && k >= 16;
+    const bool use_tc = (p == HRP_F16 || p == HRP_F8E4M3) && tc && (k0 % 8) == 0 && k >= 16;
     begin(use_tc ? CLS_GEMM_TC : CLS_GEMM_SIMT, fl);
     switch (p) {
       case HRP_F64: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F64, lower, s)); break;
@@ -231,6 +249,12 @@ struct Fact {
           chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s));
         else
           chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F16, lower, s));
+        break;
+      case HRP_F8E4M3:
+        if (tc && shadow8 && (k0 % 8) == 0 && k >= 16)
+          chk(launch_gemm_f16_tc(C, lda, shadow8, lds, r0, c0, k0, m, nd, k, lower, ldexp(1.0, -2 * kG), h->d_err, s));
+        else if (err == cudaSuccess)
+          err = cudaErrorNotSupported;
         break;
       default:
         if (err == cudaSuccess) err = cudaErrorNotSupported;
@@ -287,7 +311,14 @@ void collect_timing(hrp_handle* h, const Fact& f) {
 
 hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s) {
   hrp_status st;
-  if (tree_has(t, HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "FP8 levels are not built in this version");
+  const bool has8 = tree_has(t, HRP_F8E4M3);
+  if (has8) {
+    // E4M3 tiles live on the global 128 x 128 grid: every node must split on it
+    bool pow2 = n >= 128 && (n % 128) == 0 && (((n / 128) & (n / 128 - 1)) == 0);
+    int tl = t->trsm_leaf ? t->trsm_leaf : t->leaf;
+    if (n > 0 && (!pow2 || t->leaf != 128 || tl != 128))
+      return set_err(h, HRP_ERR_UNSUPPORTED, "an F8 level needs n = 128 * 2^k and leaf = trsm_leaf = 128");
+  }
   Fact f{};
   f.h = h;
   f.t = t;
@@ -298,14 +329,22 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
   f.s = s;
   f.tc = tc_gemm_supported();
   f.shadow = nullptr;
-  f.lds = 0;
+  f.shadow8 = nullptr;
+  f.tile_exp = nullptr;
+  f.lds = (n + 63) / 64 * 64;
   f.w32 = nullptr;
   if (tree_has(t, HRP_F16)) {
-    f.lds = (n + 63) / 64 * 64;
     if ((st = ensure(h, &h->shadow, &h->shadow_cap, (size_t)n * f.lds)) != HRP_OK) return st;
     f.shadow = h->shadow;
   }
-  if (tree_has(t, HRP_F32) || tree_has(t, HRP_F16)) {
+  if (has8 && n > 0) {
+    if ((st = ensure(h, &h->shadow8, &h->shadow8_cap, (size_t)n * f.lds)) != HRP_OK) return st;
+    const size_t nt = (size_t)(n / 128);
+    if ((st = ensure(h, &h->tile_exp, &h->tile_exp_cap, nt * nt)) != HRP_OK) return st;
+    f.shadow8 = h->shadow8;
+    f.tile_exp = h->tile_exp;
+  }
+  if (tree_has(t, HRP_F32) || tree_has(t, HRP_F16) || has8) {
     if ((st = ensure(h, &h->w32, &h->w32_cap, (size_t)n * 128 + 128 * 128)) != HRP_OK) return st;
     f.w32 = h->w32;
   }
@@ -331,6 +370,10 @@ hrp_status check_dev_err(hrp_handle* h, cudaStream_t s) {
   if (e & DEV_ERR_TIMEOUT) {
     cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s);
     return set_err(h, HRP_ERR_TIMEOUT, "a bounded device wait expired");
+  }
+  if (e & DEV_ERR_RANGE) {
+    cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s);
+    return set_err(h, HRP_ERR_RANGE, "an E4M3 tile fell outside the exact FP16 storage window");
   }
   return HRP_OK;
 }
@@ -391,6 +434,8 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->d_flags);
   cudaFree(h->shadow);
   cudaFree(h->w32);
+  cudaFree(h->shadow8);
+  cudaFree(h->tile_exp);
   cudaFree(h->fact);
   cudaFree(h->work);
   cudaFree(h->d_norms);

@@ -14,6 +14,7 @@ namespace hrp {
 enum : unsigned {
   DEV_ERR_TIMEOUT = 1u,     // a bounded wait expired
   DEV_ERR_BOUNDS = 2u,      // a checked index fell outside its buffer
+  DEV_ERR_RANGE = 4u,       // an E4M3 tile fell outside the exact FP16 storage window
 };
 
 // Bounded device waits give up after this many nanoseconds of %globaltimer.
@@ -85,6 +86,11 @@ cudaError_t launch_axpy_matrix(double* X, int ldx, const double* D, int ldd, int
 // out[0] += sum over lower triangle (sym weights) of (A - L L^T)^2, out[1] += ||A||_F^2
 cudaError_t launch_backward_error(const double* A, int lda, const double* L, int ldl, int n,
                                   double* out, cudaStream_t s);
+// E4M3 quantization of the finished panel A[r0:r0+m, c0:c0+128] (r0, c0 multiples of 128)
+// into the FP8 shadow S8 (FP16 storage of 2^G s e4m3(x/s)), one power-of-two scale
+// exponent per 128 x 128 tile into tile_exp[(row tile) * ntile_ld + (col tile)].
+cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
+                              int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s);
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 

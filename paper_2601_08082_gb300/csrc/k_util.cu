@@ -246,3 +246,89 @@ cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int
 }
 
 }  // namespace hrp
+
+// ---------------------------------------------------------------------------------------
+// E4M3 quantization of finished L tiles (FP8 levels of the tree).
+//
+// One CTA per 128 x 128 tile of the global grid: amax over the tile, scale
+// s = 2^ceil(log2(amax / 448)) (exact power of two; 1 for an all-zero tile), each entry
+// rounded to E4M3FN (round to nearest even, saturating; written here from the OCP format
+// definition: 4 exponent bits with bias 7, 3 mantissa bits, subnormals k * 2^-9, largest
+// finite 448), then stored as the FP16 number 2^G * s * e4m3(x / s).  That number is
+// exact in FP16 whenever 2^G * amax <= 65504 and 2^(G-24) <= s * 2^-9 (checked; a tile
+// outside that window sets DEV_ERR_RANGE), so a kind::f16 tensor-core product of two such
+// operands, scaled by 2^-2G, equals the block-scaled E4M3 product.
+// ---------------------------------------------------------------------------------------
+namespace hrp {
+namespace {
+
+__device__ __forceinline__ double e4m3_rne(double y) {
+  // y = x / s with |y| <= 448 by construction of s
+  const double ay = fabs(y);
+  if (ay == 0.0) return 0.0;
+  int ex;
+  frexp(ay, &ex);                       // ay = f * 2^ex, f in [0.5, 1)
+  int e = ex - 1;
+  if (e < -6) e = -6;                   // subnormal binade
+  const double q = ldexp(1.0, e - 3);   // spacing of E4M3 values in this binade
+  double r = rint(ay / q) * q;          // exact division by a power of two; rint: ties to even
+  if (r > 448.0) r = 448.0;
+  return copysign(r, y);
+}
+
+__global__ void __launch_bounds__(256)
+quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, int nc, __half* __restrict__ S8,
+                  int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  __shared__ double red[8];
+  const int tr = blockIdx.x;                       // row tile within the panel
+  const int R0 = r0 + tr * 128;
+  const int rows = min(128, r0 + m - R0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double amax = 0.0;
+  for (int idx = tid; idx < 128 * nc; idx += 256) {
+    const int i = idx & 127, j = idx >> 7;
+    if (i < rows) amax = fmax(amax, fabs(A[(size_t)(c0 + j) * ld + R0 + i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) red[warp] = amax;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0;
+    for (int w = 0; w < 8; ++w) a = fmax(a, red[w]);
+    red[0] = a;
+  }
+  __syncthreads();
+  amax = red[0];
+  int sig = 0;                                     // s = 2^sig
+  if (amax > 0.0 && isfinite(amax)) {
+    int ex;
+    const double f = frexp(amax / 448.0, &ex);     // amax / 448 = f * 2^ex
+    sig = (f == 0.5) ? ex - 1 : ex;                // ceil(log2(amax / 448))
+  }
+  if (tid == 0) {
+    tile_exp[(size_t)(R0 / 128) * ntile_ld + c0 / 128] = sig;
+    const bool fits = !(amax > 0.0) || (ldexp(amax, G) <= 65504.0 && sig - 9 + G >= -24);
+    if (!fits || !isfinite(amax)) atomicOr(err, DEV_ERR_RANGE);
+  }
+  const double inv_s = ldexp(1.0, -sig);
+  for (int idx = tid; idx < 128 * nc; idx += 256) {
+    const int j = idx & (nc - 1), i = idx / nc;    // consecutive threads: consecutive columns
+    if (i < rows) {
+      const double x = A[(size_t)(c0 + j) * ld + R0 + i];
+      const double q = ldexp(e4m3_rne(x * inv_s), sig + G);
+      S8[(size_t)(R0 + i) * lds + c0 + j] = __double2half(q);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
+                              int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s) {
+  if (m <= 0 || nc <= 0) return cudaSuccess;
+  if ((r0 % 128) || (c0 % 128) || nc != 128) return cudaErrorInvalidValue;
+  quant_e4m3_kernel<<<(m + 127) / 128, 256, 0, s>>>(A, ld, r0, m, c0, nc, S8, lds, tile_exp, ntile_ld, G, err);
+  return cudaGetLastError();
+}
+
+}  // namespace hrp

@@ -221,3 +221,64 @@ def test_posv_falls_back_when_the_mixed_tree_fails(hrp_mod, handle):
     X_t = torch.zeros_like(B_t)
     out = handle.posv(hrp_mod.tree_parse("[F16,F16,F16]", 64), A_t, B_t, X_t, max_iter=5, tol=1e-30)
     assert out["used_fallback"] == 1
+
+
+# ---------------------------------------------------------------------------------------
+# FP8 E4M3 outermost level (per-128x128 power-of-two tile scales)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["[F8,F16,F32|F64@128]", "[F8,F32|F64@128]"])
+@pytest.mark.parametrize("n,rho", [(1024, 2.0), (2048, 1.05)])
+def test_fp8_tree_matches_emulator(hrp_mod, handle, spec, n, rho):
+    """E4M3 rounding moves an operand by up to 2^-4 of itself, so a rounding decision the
+    GPU and the emulator take differently (their FP32/FP64 accumulations differ before
+    the operand is quantized) changes one term by ~6%; such flips are rare and diluted
+    over K terms, so the bound is 1e-4 max|L| (1e-5 for the FP16 trees)."""
+    A = dominant_spd(n, rho, seed_for(3, n))
+    L, info, _ = _factor(hrp_mod, handle, A, spec, 128)
+    assert info == 0
+    L_emu, info_e, em = otree.emulate_potrf(A, otree.parse(spec, leaf=128))
+    assert info_e == 0 and any(c[0] == "F8" for c in em.gemm_calls)
+    scale = np.max(np.abs(L_emu))
+    d_gpu = np.max(np.abs(L - L_emu)) / scale
+    assert d_gpu <= 1e-4, d_gpu
+    be_gpu, be_emu = dense.backward_error(A, L), dense.backward_error(A, L_emu)
+    assert abs(be_gpu - be_emu) <= 0.05 * be_emu
+
+
+@pytest.mark.parametrize("spec", ["[F8,F64]", "[F8,F16,F64]"])
+def test_fp8_levels_reproduce_emulator_rounding(hrp_mod, handle, spec):
+    """With every leaf in FP64 only the E4M3 (and FP16) operand rounding remains: the GPU
+    factor must sit on the emulator's, far inside the size of the E4M3 effect."""
+    n = 1024
+    A = dominant_spd(n, 1.05, seed_for(3, 77))
+    At = hrp_mod.colmajor(A).cuda()
+    assert handle.potrf(hrp_mod.tree_parse(spec, leaf=128, trsm_fp64=True), At) == 0
+    L = np.tril(hrp_mod.from_colmajor(At))
+    L_emu, _, _ = otree.emulate_potrf(A, otree.parse(spec, leaf=128), leaf_compute="F64")
+    L64, _ = dense.cholesky(A)
+    f_gpu = np.linalg.norm(L - L_emu)
+    f_emu = np.linalg.norm(L_emu - L64)
+    assert f_emu > 1e-8 * np.linalg.norm(L64)
+    assert f_gpu <= 0.02 * f_emu, (f_gpu, f_emu)
+
+
+def test_fp8_requires_power_of_two_blocks(hrp_mod, handle):
+    A = dominant_spd(1000, 2.0, seed_for(3, 5))
+    At = hrp_mod.colmajor(A).cuda()
+    with pytest.raises(hrp_mod.HrpError) as e:
+        handle.potrf(hrp_mod.tree_parse("[F8,F32|F64@128]", leaf=128), At)
+    assert e.value.status == 7
+
+
+def test_posv_with_fp8_tree_refines(hrp_mod, handle):
+    import torch
+    n, nrhs = 2048, 16
+    A = dominant_spd(n, 2.0, seed_for(3, 9))
+    B = rhs(n, nrhs, seed_for(3, 10))
+    A_t = hrp_mod.colmajor(A).cuda()
+    B_t = hrp_mod.colmajor(B).cuda()
+    X_t = torch.zeros_like(B_t)
+    out = handle.posv(hrp_mod.tree_parse("[F8,F16,F16,F32|F64@128]", 128), A_t, B_t, X_t, tol=1e-12)
+    assert out["status"] == 0 and out["used_fallback"] == 0
+    X = hrp_mod.from_colmajor(X_t)
+    assert np.max(dense.column_residuals(A, X, B)) <= 1e-12
