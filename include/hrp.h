@@ -165,6 +165,24 @@ hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda,
 hrp_status hrp_set_timing(hrp_handle* h, int enable);
 int hrp_get_timing(hrp_handle* h, double* out, int n);
 
+/*
+ * Batched factorization of `batch` independent systems (BASELINE's many-systems
+ * workload; the paper factors one matrix at a time).  Host arrays: trees[i] (the tree of
+ * system i; entries may share one tree; F8 levels are not batched), n[i], dA[i] (device
+ * pointer), lda[i].  d_info: DEVICE array of batch ints, info of each system as in
+ * hrp_potrf.  Each system runs the recursion of Alg. 1-3 on one stream of an internal
+ * pool forked from `stream` (longest systems first) and joined back into it; the call only
+ * enqueues work (capturable into one CUDA graph once the workspace for these sizes exists).
+ */
+hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n,
+                             double* const* dA, const int* lda, int* d_info, void* stream);
+/*
+ * Batched POTRS (FP64): for each i, dB[i] (n[i] x nrhs, ldb[i]) <- A_i^{-1} dB[i] with the
+ * factor in the lower triangle of dL[i].  Same stream pool and capture rules as above.
+ */
+hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* const* dL, const int* ldl,
+                             int nrhs, double* const* dB, const int* ldb, void* stream);
+
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);
 

@@ -59,6 +59,11 @@ struct hrp_handle_s {
   double cls_launches[hrp::kNumClasses] = {0};
   double cls_flops[hrp::kNumClasses] = {0};
   std::vector<cudaEvent_t> events;
+  // batched calls: a pool of streams and per-system workspace
+  std::vector<cudaStream_t> bstreams;
+  std::vector<cudaEvent_t> bevents;
+  unsigned char* bwork = nullptr;
+  size_t bwork_cap = 0;
 };
 
 namespace hrp {
@@ -442,6 +447,9 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->pwork);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->bevents) cudaEventDestroy(e);
+  for (cudaStream_t st : h->bstreams) cudaStreamDestroy(st);
+  cudaFree(h->bwork);
   delete h;
   return HRP_OK;
 }
@@ -712,3 +720,196 @@ int hrp_get_timing(hrp_handle* h, double* out, int n) {
 long long hrp_last_launch_count(const hrp_handle* h) { return h ? h->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batched factorization and solve: many independent systems of different orders.
+// Each system runs the same recursion as hrp_potrf on one stream of a pool forked from
+// the caller's stream (systems assigned longest-processing-time first by n^3), with its
+// own slice of workspace, and the pool is joined back into the caller's stream.  The
+// whole call only enqueues work, so it can be captured into one CUDA graph.
+// ---------------------------------------------------------------------------------------
+namespace hrp {
+namespace {
+
+constexpr int kBatchStreams = 32;
+
+struct SysWork {
+  size_t shadow, w32, pinv, flags, ticket;   // byte offsets into h->bwork
+  int lds;
+};
+
+hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<SysWork>& ws, bool need_factor_ws) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  ws.resize(batch);
+  for (int i = 0; i < batch; ++i) {
+    const int ni = n[i];
+    SysWork& w = ws[i];
+    w.lds = (ni + 63) / 64 * 64;
+    w.shadow = need_factor_ws ? take((size_t)ni * w.lds * sizeof(__half)) : 0;
+    w.w32 = need_factor_ws ? take(((size_t)ni * 128 + 128 * 128) * sizeof(float)) : 0;
+    w.pinv = take(potrs_workspace_bytes(ni));
+    w.flags = take(sizeof(int) * (size_t)((ni + 63) / 64 + 1));
+    w.ticket = take(sizeof(int));
+  }
+  unsigned char* old = h->bwork;
+  size_t old_cap = h->bwork_cap;
+  hrp_status st = ensure(h, &h->bwork, &h->bwork_cap, off);
+  if (st != HRP_OK) return st;
+  if (h->bwork != old || h->bwork_cap != old_cap) {
+    if (cudaMemset(h->bwork, 0, h->bwork_cap) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "batch workspace");
+    h->epoch = std::max(h->epoch, 1);
+  }
+  while ((int)h->bstreams.size() < kBatchStreams) {
+    cudaStream_t st2;
+    if (cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "stream");
+    h->bstreams.push_back(st2);
+  }
+  while ((int)h->bevents.size() < kBatchStreams + 1) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "event");
+    h->bevents.push_back(ev);
+  }
+  return HRP_OK;
+}
+
+// longest processing time first: stream of each system
+std::vector<int> lpt_assign(int batch, const int* n, int nstreams) {
+  std::vector<int> order(batch), which(batch);
+  for (int i = 0; i < batch; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::vector<double> load(nstreams, 0.0);
+  for (int i : order) {
+    int best = 0;
+    for (int k = 1; k < nstreams; ++k)
+      if (load[k] < load[best]) best = k;
+    which[i] = best;
+    load[best] += (double)n[i] * n[i] * n[i];
+  }
+  return which;
+}
+
+hrp_status fork(hrp_handle* h, cudaStream_t s) {
+  if (cudaEventRecord(h->bevents[kBatchStreams], s) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "fork");
+  for (int k = 0; k < kBatchStreams; ++k)
+    if (cudaStreamWaitEvent(h->bstreams[k], h->bevents[kBatchStreams], 0) != cudaSuccess)
+      return set_err(h, HRP_ERR_CUDA, "fork");
+  return HRP_OK;
+}
+hrp_status join(hrp_handle* h, cudaStream_t s) {
+  for (int k = 0; k < kBatchStreams; ++k) {
+    if (cudaEventRecord(h->bevents[k], h->bstreams[k]) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "join");
+    if (cudaStreamWaitEvent(s, h->bevents[k], 0) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "join");
+  }
+  return HRP_OK;
+}
+
+hrp_status check_batch_args(hrp_handle* h, int batch, const int* n, double* const* dA, const int* lda) {
+  if (batch < 0) return bad_arg(h, 3, "batch < 0");
+  if (batch > 0 && (!n || !dA || !lda)) return bad_arg(h, 4, "NULL array");
+  for (int i = 0; i < batch; ++i) {
+    if (n[i] < 0) return bad_arg(h, 4, "n[i] < 0");
+    if (n[i] > 0 && !dA[i]) return bad_arg(h, 5, "dA[i] is NULL");
+    if (lda[i] < (n[i] > 1 ? n[i] : 1)) return bad_arg(h, 6, "lda[i] < max(1, n[i])");
+  }
+  return HRP_OK;
+}
+
+}  // namespace
+}  // namespace hrp
+
+extern "C" {
+
+hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n, double* const* dA,
+                             const int* lda, int* d_info, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (batch > 0 && !trees) return bad_arg(h, 2, "trees is NULL");
+  hrp_status st = check_batch_args(h, batch, n, dA, lda);
+  if (st != HRP_OK) return st;
+  if (batch > 0 && !d_info) return bad_arg(h, 7, "d_info is NULL");
+  for (int i = 0; i < batch; ++i) {
+    if ((st = validate_tree(h, trees[i], 2)) != HRP_OK) return st;
+    if (tree_has(trees[i], HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "F8 levels are not batched");
+  }
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<SysWork> ws;
+  if ((st = batch_prepare(h, batch, n, ws, true)) != HRP_OK) return st;
+  if (batch == 0) return HRP_OK;
+  const bool tc = tc_gemm_supported();
+  std::vector<int> which = lpt_assign(batch, n, kBatchStreams);
+  if ((st = fork(h, s)) != HRP_OK) return st;
+  long long launches = 0;
+  const bool timing = h->timing;
+  h->timing = false;                       // per-launch event timing is not used in batches
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < batch; ++i) {
+    Fact f{};
+    f.h = h;
+    f.t = trees[i];
+    f.A = dA[i];
+    f.lda = lda[i];
+    f.n = n[i];
+    f.info = d_info + i;
+    f.s = h->bstreams[which[i]];
+    f.tc = tc;
+    f.lds = ws[i].lds;
+    f.shadow = tree_has(f.t, HRP_F16) ? reinterpret_cast<__half*>(h->bwork + ws[i].shadow) : nullptr;
+    f.shadow8 = nullptr;
+    f.tile_exp = nullptr;
+    f.w32 = (tree_has(f.t, HRP_F32) || tree_has(f.t, HRP_F16)) ? reinterpret_cast<float*>(h->bwork + ws[i].w32)
+                                                                : nullptr;
+    f.begin(CLS_OTHER, 0.0);
+    f.chk(launch_fill_int(f.info, INT_MAX, 1, f.s));
+    f.potrf(0, f.n, 0);
+    f.begin(CLS_OTHER, 0.0);
+    f.chk(launch_finalize_info(f.info, f.s));
+    launches += f.launches;
+    if (f.err != cudaSuccess && err == cudaSuccess) err = f.err;
+  }
+  h->timing = timing;
+  if ((st = join(h, s)) != HRP_OK) return st;
+  h->launches = launches;
+  return cuda_status(h, err, "hrp_potrf_batched");
+}
+
+hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* const* dL, const int* ldl, int nrhs,
+                             double* const* dB, const int* ldb, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = check_batch_args(h, batch, n, dL, ldl);
+  if (st != HRP_OK) return st;
+  if (nrhs < 0) return bad_arg(h, 6, "nrhs < 0");
+  if (batch > 0 && nrhs > 0 && (!dB || !ldb)) return bad_arg(h, 7, "dB/ldb is NULL");
+  for (int i = 0; i < batch && nrhs > 0; ++i)
+    if ((n[i] > 0 && !dB[i]) || ldb[i] < (n[i] > 1 ? n[i] : 1)) return bad_arg(h, 7, "dB[i] / ldb[i]");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<SysWork> ws;
+  if ((st = batch_prepare(h, batch, n, ws, true)) != HRP_OK) return st;
+  if (batch == 0 || nrhs == 0) return HRP_OK;
+  std::vector<int> which = lpt_assign(batch, n, kBatchStreams);
+  if ((st = fork(h, s)) != HRP_OK) return st;
+  if (h->epoch > INT_MAX - 4096) h->epoch = 1;        // flags of every system are reset below
+  const int ep = h->epoch;
+  h->epoch += potrs_epochs(nrhs);
+  cudaError_t err = cudaSuccess;
+  long long launches = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (n[i] == 0) continue;
+    cudaStream_t si = h->bstreams[which[i]];
+    int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
+    if (ep == 1) cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n[i] + 63) / 64 + 1), si);
+    cudaError_t e = launch_potrs(dL[i], ldl[i], dB[i], ldb[i], n[i], nrhs, false, h->bwork + ws[i].pinv,
+                                 reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si);
+    launches += 1 + 2 * potrs_epochs(nrhs);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  if ((st = join(h, s)) != HRP_OK) return st;
+  h->launches = launches;
+  return cuda_status(h, err, "hrp_potrs_batched");
+}
+
+}  // extern "C"
+

@@ -29,7 +29,7 @@ EXPORTED = [
     "hrp_create", "hrp_destroy", "hrp_last_arg", "hrp_last_error", "hrp_status_string",
     "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
     "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
-    "hrp_potrs_noalloc",
+    "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched",
 ]
 
 
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
     L.hrp_last_launch_count.argtypes = [vp]
     L.hrp_last_launch_count.restype = ctypes.c_longlong
     L.hrp_potrs_noalloc.argtypes = [c_int, c_int, vp, c_int, vp, c_int, vp]
+    L.hrp_potrf_batched.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp]
+    L.hrp_potrs_batched.argtypes = [vp, c_int, vp, vp, vp, c_int, vp, vp, vp]
     _lib = L
     return L
 
@@ -193,6 +195,31 @@ class Handle:
         self._check(st, allow=() if raise_errors else (2, 3))
         return {"status": st, "iters": iters.value, "resid": resid.value, "info": info.value,
                 "used_fallback": fb.value}
+
+    # batched: lists of column-major CUDA tensors; trees: one Tree or a list of Trees
+    def potrf_batched(self, trees, As, d_info, stream=None) -> None:
+        batch = len(As)
+        if isinstance(trees, Tree):
+            trees = [trees] * batch
+        keep = list(trees)
+        tptr = (ctypes.POINTER(Tree) * batch)(*[ctypes.pointer(t) for t in keep])
+        n = (ctypes.c_int * batch)(*[A.shape[0] for A in As])
+        lda = (ctypes.c_int * batch)(*[A.shape[1] for A in As])
+        ptrs = (ctypes.c_void_p * batch)(*[A.data_ptr() for A in As])
+        st = self._lib.hrp_potrf_batched(self._h, ctypes.cast(tptr, ctypes.c_void_p), batch, n, ptrs, lda,
+                                         _ptr(d_info), _stream(stream))
+        self._check(st)
+
+    def potrs_batched(self, Ls, Bs, stream=None) -> None:
+        batch = len(Ls)
+        n = (ctypes.c_int * batch)(*[L.shape[0] for L in Ls])
+        ldl = (ctypes.c_int * batch)(*[L.shape[1] for L in Ls])
+        lp = (ctypes.c_void_p * batch)(*[L.data_ptr() for L in Ls])
+        nrhs = Bs[0].shape[0] if batch else 0
+        ldb = (ctypes.c_int * batch)(*[B.shape[1] for B in Bs])
+        bp = (ctypes.c_void_p * batch)(*[B.data_ptr() for B in Bs])
+        st = self._lib.hrp_potrs_batched(self._h, batch, n, lp, ldl, nrhs, bp, ldb, _stream(stream))
+        self._check(st)
 
     def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
         n = A.shape[0] if n is None else n

@@ -282,3 +282,73 @@ def test_posv_with_fp8_tree_refines(hrp_mod, handle):
     assert out["status"] == 0 and out["used_fallback"] == 0
     X = hrp_mod.from_colmajor(X_t)
     assert np.max(dense.column_residuals(A, X, B)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# batched factorization / solve (many independent systems, one stream pool, graph-capturable)
+# ---------------------------------------------------------------------------------------
+def test_batched_equals_one_by_one(hrp_mod, handle):
+    import torch
+    sizes = [64, 200, 128, 513, 96, 1000, 1, 300, 777, 65]
+    mats = [dominant_spd(n, 1.5, seed_for(4, i), shift=1.0) for i, n in enumerate(sizes)]
+    tree = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    d_info = torch.full((len(sizes),), -1, dtype=torch.int32, device="cuda")
+    handle.potrf_batched(tree, As, d_info)
+    torch.cuda.synchronize()
+    assert d_info.cpu().tolist() == [0] * len(sizes)
+    for A, At in zip(mats, As):
+        single = hrp_mod.colmajor(A).cuda()
+        assert handle.potrf(tree, single) == 0
+        assert torch.equal(torch.tril(single.T), torch.tril(At.T))     # same kernels, same order
+    Bs = [hrp_mod.colmajor(rhs(n, 4, seed_for(4, 100 + i))).cuda() for i, n in enumerate(sizes)]
+    B_single = [B.clone() for B in Bs]
+    handle.potrs_batched(As, Bs)
+    torch.cuda.synchronize()
+    for At, B, Bs1, A in zip(As, Bs, B_single, mats):
+        handle.potrs(At, Bs1)
+        assert torch.equal(B, Bs1)
+        L = np.tril(hrp_mod.from_colmajor(At))
+        X_ref = dense.potrs(L, rhs(A.shape[0], 4, seed_for(4, 100 + sizes.index(A.shape[0]))))
+        X = hrp_mod.from_colmajor(B)
+        assert np.max(np.abs(X - X_ref)) <= 1e-12 * np.max(np.abs(X_ref))
+
+
+def test_batched_reports_per_system_info(hrp_mod, handle):
+    import torch
+    sizes = [100, 150, 80]
+    mats = [dominant_spd(n, 2.0, seed_for(4, 50 + i)) for i, n in enumerate(sizes)]
+    mats[1][40, 40] = -1.0
+    _, info1 = dense.cholesky(mats[1])
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    d_info = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+    handle.potrf_batched(hrp_mod.tree_parse("[F64]", leaf=64), As, d_info)
+    torch.cuda.synchronize()
+    assert d_info.cpu().tolist() == [0, info1, 0] and info1 == 41
+
+
+def test_batched_graph_capture_replays(hrp_mod, handle):
+    import torch
+    sizes = [256, 384, 128, 640]
+    mats = [dominant_spd(n, 2.0, seed_for(4, 70 + i)) for i, n in enumerate(sizes)]
+    tree = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
+    A0 = [hrp_mod.colmajor(A).cuda() for A in mats]
+    As = [A.clone() for A in A0]
+    d_info = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+    handle.potrf_batched(tree, As, d_info)          # allocates the workspace (outside capture)
+    torch.cuda.synchronize()
+    ref = [A.clone() for A in As]
+    for A, a0 in zip(As, A0):
+        A.copy_(a0)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            handle.potrf_batched(tree, As, d_info, stream=s)
+    for rep in range(2):
+        for A, a0 in zip(As, A0):
+            A.copy_(a0)
+        g.replay()
+        torch.cuda.synchronize()
+        for A, R in zip(As, ref):
+            assert torch.equal(torch.tril(A.T), torch.tril(R.T))
