@@ -136,7 +136,8 @@ hrp_status hrp_potrs(hrp_handle* h, int n, int nrhs, const double* dL, int ldl,
  *   X_0 = POTRS(B); repeat R = B - A X (FP64, A's lower triangle read as symmetric),
  *   D = POTRS(R), X += D, until max_j ||r_j||_2/||b_j||_2 <= tol or max_iter corrections.
  *   If the tree's factorization fails (info > 0) the call refactors with the fallback
- *   tree "[F32|F64@128]" and reports it in *used_fallback.
+ *   tree "[F32|F64@128]" and reports it in *used_fallback.  tree == NULL: the learned
+ *   policy chooses the tree (see hrp_policy_set below).
  *   iters, resid, info, used_fallback: host pointers (may be NULL). Synchronous (one
  *   device->host read of the residual per iteration).
  */
@@ -182,6 +183,41 @@ hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int ba
  */
 hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* const* dL, const int* ldl,
                              int nrhs, double* const* dB, const int* ldb, void* stream);
+
+/*
+ * Learned precision policy (not in the paper; BASELINE's learned part).  A small network
+ * (MLP 12 -> 64 -> 64 -> 8, ReLU, FP32) maps cheap matrix features to one of eight
+ * candidate trees (hrp_policy_tree); hrp_posv with tree == NULL uses it, and falls back
+ * to the conservative tree (index 0, "[F32|F64@128]") when the chosen factorization fails.
+ *
+ * hrp_policy_features: the 12 features of the symmetric A (lower triangle of dA), host
+ *   float feat[12]: log2 n; min, mean and fraction > 1 of the row dominance ratios
+ *   a_ii / sum_{j!=i} |a_ij| (min clamped at 1e6); log10 ||A||_F; log10 of the diagonal
+ *   max, min and their ratio; log10 of the extreme Ritz values of `lanczos_steps` Lanczos
+ *   steps (start vector v_i ~ 1 + (i mod 7)/7), their ratio (condition estimate), and
+ *   log10(n lambda_min / ||A||_F).  FP64 on the device; synchronous.
+ * hrp_mlp_forward / hrp_mlp_grad / hrp_mlp_adam: the network's kernels on device arrays:
+ *   params (hrp_mlp_param_count() = 5512 floats: W1 64x12, b1, W2 64x64, b2, W3 8x64, b3,
+ *   row-major), X (batch x 12), logits Z (batch x 8), labels y (batch ints); grad gets the
+ *   gradient of the mean softmax cross-entropy and *d_loss the loss; Adam with
+ *   beta = (0.9, 0.999), eps 1e-8, bias-corrected at step `step` (1-based).  Asynchronous.
+ * hrp_policy_set: install trained parameters (host arrays) and the input standardization
+ *   (mean[12], scale[12]); hrp_policy_predict: index of the predicted tree for host
+ *   feat[12]; hrp_last_policy_choice: the index hrp_posv chose last (-1 if a tree was given).
+ */
+hrp_status hrp_policy_features(hrp_handle* h, int n, const double* dA, int lda, int lanczos_steps, float* feat,
+                               void* stream);
+hrp_status hrp_mlp_forward(hrp_handle* h, const float* d_params, int batch, const float* d_X, float* d_Z,
+                           void* stream);
+hrp_status hrp_mlp_grad(hrp_handle* h, const float* d_params, int batch, const float* d_X, const int* d_y,
+                        float* d_grad, float* d_loss, void* stream);
+hrp_status hrp_mlp_adam(hrp_handle* h, float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
+                        float lr, void* stream);
+int hrp_mlp_param_count(void);
+hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean, const float* scale);
+hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index);
+hrp_status hrp_policy_tree(int index, hrp_tree* out);
+int hrp_last_policy_choice(const hrp_handle* h);
 
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);

@@ -64,6 +64,13 @@ struct hrp_handle_s {
   std::vector<cudaEvent_t> bevents;
   unsigned char* bwork = nullptr;
   size_t bwork_cap = 0;
+  // learned policy: feature workspace and the (standardization-folded) MLP parameters
+  double* fwork = nullptr;
+  size_t fwork_cap = 0;
+  float* policy = nullptr;     // device, 5512 floats
+  float* pio = nullptr;        // device, 12 inputs + 8 logits
+  bool policy_set = false;
+  int last_choice = -1;
 };
 
 namespace hrp {
@@ -450,6 +457,9 @@ hrp_status hrp_destroy(hrp_handle* h) {
   for (cudaEvent_t e : h->bevents) cudaEventDestroy(e);
   for (cudaStream_t st : h->bstreams) cudaStreamDestroy(st);
   cudaFree(h->bwork);
+  cudaFree(h->fwork);
+  cudaFree(h->policy);
+  cudaFree(h->pio);
   delete h;
   return HRP_OK;
 }
@@ -605,6 +615,26 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
                     int* used_fallback, void* stream) {
   if (!h) return HRP_ERR_INVALID_ARG;
   h->last_arg = 0;
+  hrp_tree chosen;
+  h->last_choice = -1;
+  if (!tree && n > 0 && dA && lda >= n) {
+    // no tree given: the learned policy picks one (the fallback tree if none is loaded)
+    int idx = 0;
+    if (h->policy_set) {
+      float feat[12];
+      hrp_status fs = hrp_policy_features(h, n, dA, lda, 24, feat, stream);
+      if (fs != HRP_OK) return fs;
+      if ((fs = hrp_policy_predict(h, feat, &idx)) != HRP_OK) return fs;
+    }
+    // F8 trees need n = 128 * 2^k; otherwise take the same depth in FP16
+    hrp_policy_tree(idx, &chosen);
+    const bool pow2 = n >= 128 && n % 128 == 0 && (((n / 128) & (n / 128 - 1)) == 0);
+    if (!pow2)
+      for (int i = 0; i < chosen.depth; ++i)
+        if (chosen.level[i] == HRP_F8E4M3) chosen.level[i] = HRP_F16;
+    h->last_choice = idx;
+    tree = &chosen;
+  }
   hrp_status st = validate_tree(h, tree, 2);
   if (st != HRP_OK) return st;
   if (n < 0) return bad_arg(h, 3, "n < 0");
@@ -913,3 +943,209 @@ hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* con
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------------------
+// Learned precision policy: features, MLP, and the table of candidate trees.
+// ---------------------------------------------------------------------------------------
+namespace hrp {
+namespace {
+
+const char* kPolicyTrees[8] = {
+    "[F32|F64@128]",                 // 0: the conservative fallback
+    "[F16,F32|F64@128]",
+    "[F16,F16,F32|F64@128]",
+    "[F16,F16,F16,F32|F64@128]",
+    "[F16,F16,F16,F16,F32|F64@128]",
+    "[F16,F16,F16,F16,F16,F32|F64@128]",
+    "[F8,F16,F32|F64@128]",
+    "[F8,F16,F16,F16,F32|F64@128]",
+};
+
+// number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count)
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+    q = a[i] - x - (i ? bb / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+// k-th smallest eigenvalue (0-based) by bisection inside the Gershgorin interval
+double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int k) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double r = (i ? fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(fabs(lo), fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(a, b, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+}  // namespace hrp
+
+extern "C" {
+
+hrp_status hrp_policy_features(hrp_handle* h, int n, const double* dA, int lda, int lanczos_steps, float* feat,
+                               void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (n < 1) return bad_arg(h, 2, "n < 1");
+  if (!dA) return bad_arg(h, 3, "dA is NULL");
+  if (lda < n) return bad_arg(h, 4, "lda < n");
+  if (lanczos_steps < 1) return bad_arg(h, 5, "lanczos_steps < 1");
+  if (!feat) return bad_arg(h, 6, "feat is NULL");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hrp_status st;
+  if ((st = ensure(h, &h->fwork, &h->fwork_cap, (size_t)5 * n + 16)) != HRP_OK) return st;
+  double* rowsum = h->fwork;
+  double* v = rowsum + n;
+  double* vp = v + n;
+  double* R = vp + n;
+  double* zero = R + n;
+  double* sc = zero + n;               // 16 scalars
+  double init[8] = {0.0, 1e300, 0.0, 0.0, 1e300, 0.0, 0.0, 0.0};
+  cudaError_t e = cudaMemsetAsync(rowsum, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vp, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sc, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_rowsum(dA, lda, n, rowsum, sc, s);
+  double stats[8];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stats, sc, sizeof(stats), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_policy_features");
+  // Lanczos
+  const int k = std::min(lanczos_steps, n);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  e = launch_lanczos_start(v, n, s);
+  for (int j = 0; j < k && e == cudaSuccess; ++j) {
+    e = launch_residual(dA, lda, v, n, zero, n, R, n, n, 1, s);          // R = -A v
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc + 8, 0, 2 * sizeof(double), s);
+    if (e == cudaSuccess) e = launch_lanczos_dot(R, v, n, sc + 8, s);
+    if (e == cudaSuccess) e = launch_lanczos_axpy(R, v, vp, n, sc + 8, beta, sc + 9, s);
+    double ab[2];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ab, sc + 8, sizeof(ab), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    al.push_back(ab[0]);
+    beta = sqrt(ab[1]);
+    if (j + 1 < k) {
+      if (!(beta > 0.0)) break;
+      be.push_back(beta);
+      e = launch_lanczos_next(R, vp, v, n, 1.0 / beta, s);
+    }
+  }
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_policy_features lanczos");
+  be.resize(al.size() - 1);
+  const double lmin = tridiag_eig(al, be, 0), lmax = tridiag_eig(al, be, (int)al.size() - 1);
+  const double fro = sqrt(stats[0]);
+  auto lg = [](double x) { return log10(std::max(x, 1e-300)); };
+  double f[12];
+  f[0] = log2((double)n);
+  f[1] = std::min(stats[1], 1e6);
+  f[2] = stats[2] / n;
+  f[3] = stats[3] / n;
+  f[4] = lg(fro);
+  f[5] = lg(stats[5]);
+  f[6] = lg(stats[4]);
+  f[7] = f[5] - f[6];
+  f[8] = lg(lmax);
+  f[9] = lg(lmin);
+  f[10] = f[8] - f[9];
+  f[11] = lg(n * std::max(lmin, 1e-300) / fro);
+  for (int i = 0; i < 12; ++i) feat[i] = (float)f[i];
+  return HRP_OK;
+}
+
+hrp_status hrp_mlp_forward(hrp_handle* h, const float* d_params, int batch, const float* d_X, float* d_Z,
+                           void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  if (!d_params || batch < 0 || (batch > 0 && (!d_X || !d_Z))) return bad_arg(h, 2, "bad MLP argument");
+  cudaSetDevice(h->device);
+  return cuda_status(h, launch_mlp_forward(d_params, batch, d_X, d_Z, static_cast<cudaStream_t>(stream)),
+                     "hrp_mlp_forward");
+}
+
+hrp_status hrp_mlp_grad(hrp_handle* h, const float* d_params, int batch, const float* d_X, const int* d_y,
+                        float* d_grad, float* d_loss, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  if (!d_params || batch < 0 || !d_grad || !d_loss || (batch > 0 && (!d_X || !d_y)))
+    return bad_arg(h, 2, "bad MLP argument");
+  cudaSetDevice(h->device);
+  return cuda_status(h, launch_mlp_grad(d_params, batch, d_X, d_y, d_grad, d_loss, static_cast<cudaStream_t>(stream)),
+                     "hrp_mlp_grad");
+}
+
+hrp_status hrp_mlp_adam(hrp_handle* h, float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
+                        float lr, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  if (!d_params || !d_grad || !d_m || !d_v || step < 1) return bad_arg(h, 2, "bad Adam argument");
+  cudaSetDevice(h->device);
+  return cuda_status(h, launch_adam(d_params, d_grad, d_m, d_v, step, lr, static_cast<cudaStream_t>(stream)),
+                     "hrp_mlp_adam");
+}
+
+int hrp_mlp_param_count(void) { return policy_nparam(); }
+
+hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean, const float* scale) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  if (!params || !mean || !scale) return bad_arg(h, 2, "NULL policy array");
+  cudaSetDevice(h->device);
+  const int np = policy_nparam();
+  // fold the input standardization x' = (x - mean) / scale into the first layer
+  std::vector<float> p(params, params + np);
+  for (int j = 0; j < 64; ++j) {
+    double b = p[64 * 12 + j];
+    for (int k = 0; k < 12; ++k) {
+      const double w = params[j * 12 + k] / (double)scale[k];
+      p[j * 12 + k] = (float)w;
+      b -= w * mean[k];
+    }
+    p[64 * 12 + j] = (float)b;
+  }
+  size_t cap = h->policy ? (size_t)np : 0;
+  hrp_status st = ensure(h, &h->policy, &cap, (size_t)np);
+  if (st != HRP_OK) return st;
+  size_t cap2 = h->pio ? 32 : 0;
+  if ((st = ensure(h, &h->pio, &cap2, 32)) != HRP_OK) return st;
+  if (cudaMemcpy(h->policy, p.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_err(h, HRP_ERR_CUDA, "hrp_policy_set");
+  h->policy_set = true;
+  return HRP_OK;
+}
+
+hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  if (!feat || !index) return bad_arg(h, 2, "NULL argument");
+  if (!h->policy_set) return set_err(h, HRP_ERR_INVALID_ARG, "no policy loaded (hrp_policy_set)");
+  cudaSetDevice(h->device);
+  float z[8];
+  cudaError_t e = cudaMemcpy(h->pio, feat, 12 * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_mlp_forward(h->policy, 1, h->pio, h->pio + 16, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(z, h->pio + 16, sizeof(z), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_policy_predict");
+  int best = 0;
+  for (int i = 1; i < 8; ++i)
+    if (z[i] > z[best]) best = i;
+  *index = best;
+  return HRP_OK;
+}
+
+hrp_status hrp_policy_tree(int index, hrp_tree* out) {
+  if (index < 0 || index >= 8 || !out) return HRP_ERR_INVALID_ARG;
+  return hrp_tree_parse(kPolicyTrees[index], 128, out);
+}
+
+int hrp_last_policy_choice(const hrp_handle* h) { return h ? h->last_choice : -1; }
+
+}  // extern "C"

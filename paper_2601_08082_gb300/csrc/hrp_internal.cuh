@@ -94,4 +94,17 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 
+// ---------------- learned policy (k_policy.cu) ----------------
+int policy_nparam();
+cudaError_t launch_rowsum(const double* A, int lda, int n, double* rowsum, double* stats, cudaStream_t s);
+cudaError_t launch_lanczos_start(double* v, int n, cudaStream_t s);
+cudaError_t launch_lanczos_dot(const double* R, const double* v, int n, double* out, cudaStream_t s);
+cudaError_t launch_lanczos_axpy(double* R, const double* v, const double* vp, int n, const double* alpha, double beta,
+                                double* out, cudaStream_t s);
+cudaError_t launch_lanczos_next(const double* w, double* vp, double* v, int n, double inv_beta, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* p, int batch, const float* X, float* Z, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* p, int batch, const float* X, const int* y, float* g, float* loss,
+                            cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int t, float lr, cudaStream_t s);
+
 }  // namespace hrp

@@ -30,6 +30,8 @@ EXPORTED = [
     "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
     "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
     "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched",
+    "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
+    "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
 ]
 
 
@@ -80,6 +82,16 @@ def load(path: str = LIB_PATH):
     L.hrp_potrs_noalloc.argtypes = [c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_potrf_batched.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp]
     L.hrp_potrs_batched.argtypes = [vp, c_int, vp, vp, vp, c_int, vp, vp, vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.hrp_policy_features.argtypes = [vp, c_int, vp, c_int, c_int, fp, vp]
+    L.hrp_mlp_forward.argtypes = [vp, vp, c_int, vp, vp, vp]
+    L.hrp_mlp_grad.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp]
+    L.hrp_mlp_adam.argtypes = [vp, vp, vp, vp, vp, c_int, ctypes.c_float, vp]
+    L.hrp_mlp_param_count.argtypes = []
+    L.hrp_policy_set.argtypes = [vp, fp, fp, fp]
+    L.hrp_policy_predict.argtypes = [vp, fp, ip]
+    L.hrp_policy_tree.argtypes = [c_int, tp]
+    L.hrp_last_policy_choice.argtypes = [vp]
     _lib = L
     return L
 
@@ -183,13 +195,15 @@ class Handle:
         st = self._lib.hrp_potrs(self._h, n, nrhs, _ptr(L), L.shape[1], _ptr(B), B.shape[1], _stream(stream))
         self._check(st)
 
-    def posv(self, tree: Tree, A, B, X, max_iter: int = 30, tol: float = 1e-12, n: int | None = None,
+    def posv(self, tree, A, B, X, max_iter: int = 30, tol: float = 1e-12, n: int | None = None,
              stream=None, raise_errors: bool = False) -> dict:
+        """tree=None: the learned policy chooses the tree (see policy_set)."""
         n = A.shape[0] if n is None else n
         nrhs = B.shape[0]
         iters, info, fb = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         resid = ctypes.c_double(0.0)
-        st = self._lib.hrp_posv(self._h, ctypes.byref(tree), n, nrhs, _ptr(A), A.shape[1], _ptr(B), B.shape[1],
+        tref = ctypes.byref(tree) if tree is not None else None
+        st = self._lib.hrp_posv(self._h, tref, n, nrhs, _ptr(A), A.shape[1], _ptr(B), B.shape[1],
                                 _ptr(X), X.shape[1], max_iter, tol, ctypes.byref(iters), ctypes.byref(resid),
                                 ctypes.byref(info), ctypes.byref(fb), _stream(stream))
         self._check(st, allow=() if raise_errors else (2, 3))
@@ -221,6 +235,42 @@ class Handle:
         st = self._lib.hrp_potrs_batched(self._h, batch, n, lp, ldl, nrhs, bp, ldb, _stream(stream))
         self._check(st)
 
+    # ---- learned policy ----
+    def policy_features(self, A, lanczos_steps: int = 24, n: int | None = None, stream=None) -> np.ndarray:
+        n = A.shape[0] if n is None else n
+        f = (ctypes.c_float * 12)()
+        st = self._lib.hrp_policy_features(self._h, n, _ptr(A), A.shape[1], lanczos_steps, f, _stream(stream))
+        self._check(st)
+        return np.array(f[:], dtype=np.float32)
+
+    def mlp_forward(self, params, X, Z, stream=None) -> None:
+        self._check(self._lib.hrp_mlp_forward(self._h, _ptr(params), X.shape[0], _ptr(X), _ptr(Z), _stream(stream)))
+
+    def mlp_grad(self, params, X, y, grad, loss, stream=None) -> None:
+        self._check(self._lib.hrp_mlp_grad(self._h, _ptr(params), X.shape[0], _ptr(X), _ptr(y), _ptr(grad),
+                                           _ptr(loss), _stream(stream)))
+
+    def mlp_adam(self, params, grad, m, v, step: int, lr: float, stream=None) -> None:
+        self._check(self._lib.hrp_mlp_adam(self._h, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr,
+                                           _stream(stream)))
+
+    def policy_set(self, params, mean, scale) -> None:
+        def fa(a):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        (p, pp), (m, mp), (s, sp) = fa(params), fa(mean), fa(scale)
+        self._check(self._lib.hrp_policy_set(self._h, pp, mp, sp))
+
+    def policy_predict(self, feat) -> int:
+        f = np.ascontiguousarray(feat, dtype=np.float32)
+        idx = ctypes.c_int(-1)
+        self._check(self._lib.hrp_policy_predict(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 ctypes.byref(idx)))
+        return idx.value
+
+    def last_policy_choice(self) -> int:
+        return self._lib.hrp_last_policy_choice(self._h)
+
     def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
         n = A.shape[0] if n is None else n
         out = ctypes.c_double(0.0)
@@ -228,3 +278,15 @@ class Handle:
                                           _stream(stream))
         self._check(st)
         return out.value
+
+
+def policy_tree(index: int) -> Tree:
+    t = Tree()
+    st = load().hrp_policy_tree(index, ctypes.byref(t))
+    if st != 0:
+        raise HrpError(st, f"no policy tree {index}")
+    return t
+
+
+def mlp_param_count() -> int:
+    return load().hrp_mlp_param_count()
