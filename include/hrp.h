@@ -219,6 +219,20 @@ hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index);
 hrp_status hrp_policy_tree(int index, hrp_tree* out);
 int hrp_last_policy_choice(const hrp_handle* h);
 
+/*
+ * Batched hrp_posv: for each system i (host arrays as in hrp_potrf_batched, plus dB[i],
+ * ldb[i], dX[i], ldx[i]; 1 <= nrhs <= 16): factor a copy of A_i with trees[i] (dA[i] is not
+ * modified), refactor with "[F32|F64@128]" where that fails (used_fallback[i] = 1), solve,
+ * and refine in FP64 until ||b - A x||_2 / ||b||_2 <= tol per column or max_iter.  All
+ * systems advance together, one round of refinement at a time, on the internal stream
+ * pool.  info, iters, resid, used_fallback: host arrays of batch entries (may be NULL).
+ * Synchronous (one device->host read per round).
+ */
+hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n,
+                            double* const* dA, const int* lda, int nrhs, double* const* dB, const int* ldb,
+                            double* const* dX, const int* ldx, int max_iter, double tol, int* info, int* iters,
+                            double* resid, int* used_fallback, void* stream);
+
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);
 

@@ -22,6 +22,8 @@
 #include "hrp_internal.cuh"
 
 namespace hrp {
+// Lanczos steps of the policy's condition estimate (the training features use the same)
+constexpr int kPolicyLanczosSteps = 10;
 // kernel classes reported by hrp_get_timing
 enum { CLS_POTRF = 0, CLS_TRSM = 1, CLS_GEMM_TC = 2, CLS_GEMM_SIMT = 3, CLS_OTHER = 4, kNumClasses = 5 };
 }
@@ -622,7 +624,7 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
     int idx = 0;
     if (h->policy_set) {
       float feat[12];
-      hrp_status fs = hrp_policy_features(h, n, dA, lda, 24, feat, stream);
+      hrp_status fs = hrp_policy_features(h, n, dA, lda, kPolicyLanczosSteps, feat, stream);
       if (fs != HRP_OK) return fs;
       if ((fs = hrp_policy_predict(h, feat, &idx)) != HRP_OK) return fs;
     }
@@ -655,51 +657,57 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
   if (n == 0 || nrhs == 0) return HRP_OK;
   if ((st = ensure(h, &h->fact, &h->fact_cap, (size_t)n * n)) != HRP_OK) return st;
   if ((st = ensure(h, &h->work, &h->work_cap, (size_t)n * nrhs)) != HRP_OK) return st;
-  long long total_launches = 0;
+  if (!tree) return set_err(h, HRP_ERR_INVALID_ARG, "no tree");
   cudaError_t e;
-  // factor a copy of A (A itself is kept for the residual)
   hrp_tree fallback;
   hrp_tree_parse("[F32|F64@128]", 128, &fallback);
   const hrp_tree* use = tree;
-  int hinfo = 0;
+  int hinfo = 0, it = 0;
+  double worst = 0.0;
+  // attempt 0 uses the requested tree; attempt 1 (if needed) the conservative fallback:
+  // taken when the factorization fails (info > 0) or refinement diverges or stalls
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if ((e = launch_copy_lower(h->fact, n, dA, lda, n, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
-    if ((st = potrf_enqueue(h, use, n, h->fact, n, h->d_info, s)) != HRP_OK) return st;
-    total_launches += h->launches + 1;
-    e = cudaMemcpyAsync(&hinfo, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
-    if (hinfo == 0) break;
-    if (attempt == 0) {
+    if (attempt == 1) {
       use = &fallback;
       if (used_fallback) *used_fallback = 1;
     }
+    if ((e = launch_copy_lower(h->fact, n, dA, lda, n, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    if ((st = potrf_enqueue(h, use, n, h->fact, n, h->d_info, s)) != HRP_OK) return st;
+    e = cudaMemcpyAsync(&hinfo, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    if (hinfo) continue;
+    // X0 = POTRS(B) in FP32
+    if ((e = launch_copy_matrix(dX, ldx, dB, ldb, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    if ((st = potrs_impl(h, n, nrhs, h->fact, n, dX, ldx, true, s)) != HRP_OK) return st;
+    it = 0;
+    double prev = 1e300;
+    bool diverged = false;
+    while (true) {
+      if ((e = launch_residual(dA, lda, dX, ldx, dB, ldb, h->work, n, n, nrhs, s)) != cudaSuccess)
+        return cuda_status(h, e, "hrp_posv residual");
+      if ((e = launch_col_norms2(h->work, n, dB, ldb, n, nrhs, h->d_norms, s)) != cudaSuccess)
+        return cuda_status(h, e, "hrp_posv norms");
+      e = cudaMemcpyAsync(h->h_norms, h->d_norms, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+      worst = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        double rb = h->h_norms[nrhs + c] > 0 ? sqrt(h->h_norms[c] / h->h_norms[nrhs + c]) : sqrt(h->h_norms[c]);
+        if (!(rb <= worst)) worst = rb;   // NaN propagates
+      }
+      if (worst <= tol || it >= max_iter) break;
+      if (!(worst < prev)) { diverged = true; break; }   // no decrease: this factor will not get there
+      prev = worst;
+      if ((st = potrs_impl(h, n, nrhs, h->fact, n, h->work, n, true, s)) != HRP_OK) return st;
+      if ((e = launch_axpy_matrix(dX, ldx, h->work, n, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+      ++it;
+    }
+    if (worst <= tol || (!diverged && attempt == 1)) break;
+    if (attempt == 1) break;
   }
   if (info) *info = hinfo;
   if (hinfo) return set_err(h, HRP_ERR_NOT_SPD, "factorization failed at column %d (fallback tree too)", hinfo);
-  // X0 = POTRS(B) in FP32
-  if ((e = launch_copy_matrix(dX, ldx, dB, ldb, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
-  if ((st = potrs_impl(h, n, nrhs, h->fact, n, dX, ldx, true, s)) != HRP_OK) return st;
-  int it = 0;
-  double worst = 0.0;
-  while (true) {
-    if ((e = launch_residual(dA, lda, dX, ldx, dB, ldb, h->work, n, n, nrhs, s)) != cudaSuccess)
-      return cuda_status(h, e, "hrp_posv residual");
-    if ((e = launch_col_norms2(h->work, n, dB, ldb, n, nrhs, h->d_norms, s)) != cudaSuccess)
-      return cuda_status(h, e, "hrp_posv norms");
-    e = cudaMemcpyAsync(h->h_norms, h->d_norms, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
-    worst = 0.0;
-    for (int c = 0; c < nrhs; ++c) {
-      double rb = h->h_norms[nrhs + c] > 0 ? sqrt(h->h_norms[c] / h->h_norms[nrhs + c]) : sqrt(h->h_norms[c]);
-      if (!(rb <= worst)) worst = rb;   // NaN propagates
-    }
-    if (worst <= tol || it >= max_iter) break;
-    if ((st = potrs_impl(h, n, nrhs, h->fact, n, h->work, n, true, s)) != HRP_OK) return st;
-    if ((e = launch_axpy_matrix(dX, ldx, h->work, n, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
-    ++it;
-  }
   if (iters) *iters = it;
   if (resid) *resid = worst;
   if ((st = check_dev_err(h, s)) != HRP_OK) return st;
@@ -764,11 +772,13 @@ namespace {
 constexpr int kBatchStreams = 32;
 
 struct SysWork {
-  size_t shadow, w32, pinv, flags, ticket;   // byte offsets into h->bwork
+  size_t shadow, w32, pinv, flags, ticket, fact, res;   // byte offsets into h->bwork
   int lds;
 };
 
-hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<SysWork>& ws, bool need_factor_ws) {
+// per-system workspace; nrhs_ir > 0 adds an n x n factor copy and an n x nrhs residual
+hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<SysWork>& ws, bool need_factor_ws,
+                         int nrhs_ir = 0) {
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
   ws.resize(batch);
@@ -781,6 +791,8 @@ hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<Sys
     w.pinv = take(potrs_workspace_bytes(ni));
     w.flags = take(sizeof(int) * (size_t)((ni + 63) / 64 + 1));
     w.ticket = take(sizeof(int));
+    w.fact = nrhs_ir ? take(sizeof(double) * (size_t)ni * ni) : 0;
+    w.res = nrhs_ir ? take(sizeof(double) * (size_t)ni * nrhs_ir + sizeof(double) * 2 * nrhs_ir) : 0;
   }
   unsigned char* old = h->bwork;
   size_t old_cap = h->bwork_cap;
@@ -1023,30 +1035,40 @@ hrp_status hrp_policy_features(hrp_handle* h, int n, const double* dA, int lda, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(stats, sc, sizeof(stats), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(h, e, "hrp_policy_features");
-  // Lanczos
+  // Lanczos: alpha_j, beta_j stay on the device; one read at the end
   const int k = std::min(lanczos_steps, n);
-  std::vector<double> al, be;
-  double beta = 0.0;
+  if ((st = ensure(h, &h->fwork, &h->fwork_cap, (size_t)5 * n + 16 + 3 * (size_t)k)) != HRP_OK) return st;
+  rowsum = h->fwork;
+  v = rowsum + n;
+  vp = v + n;
+  R = vp + n;
+  zero = R + n;
+  sc = zero + n;
+  double* dal = sc + 16;          // alpha_j
+  double* dn2 = dal + k;          // ||w_j||^2
+  double* dbe = dn2 + k;          // beta_{j+1}
   e = launch_lanczos_start(v, n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vp, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dal, 0, sizeof(double) * 3 * k, s);
   for (int j = 0; j < k && e == cudaSuccess; ++j) {
-    e = launch_residual(dA, lda, v, n, zero, n, R, n, n, 1, s);          // R = -A v
-    if (e == cudaSuccess) e = cudaMemsetAsync(sc + 8, 0, 2 * sizeof(double), s);
-    if (e == cudaSuccess) e = launch_lanczos_dot(R, v, n, sc + 8, s);
-    if (e == cudaSuccess) e = launch_lanczos_axpy(R, v, vp, n, sc + 8, beta, sc + 9, s);
-    double ab[2];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ab, sc + 8, sizeof(ab), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) break;
-    al.push_back(ab[0]);
-    beta = sqrt(ab[1]);
-    if (j + 1 < k) {
-      if (!(beta > 0.0)) break;
-      be.push_back(beta);
-      e = launch_lanczos_next(R, vp, v, n, 1.0 / beta, s);
-    }
+    e = launch_symv32(dA, lda, v, R, n, s);                             // R = -A v
+    if (e == cudaSuccess) e = launch_lanczos_dot(R, v, n, dal + j, s);
+    if (e == cudaSuccess) e = launch_lanczos_axpy(R, v, vp, n, dal + j, j ? dbe + j - 1 : nullptr, dn2 + j, s);
+    if (e == cudaSuccess && j + 1 < k) e = launch_lanczos_next(R, vp, v, n, dn2 + j, dbe + j, s);
   }
+  std::vector<double> al(k), be;
+  std::vector<double> bev(k);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(al.data(), dal, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bev.data(), dbe, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(h, e, "hrp_policy_features lanczos");
-  be.resize(al.size() - 1);
+  // stop at a breakdown (beta = 0): the Krylov space is exhausted
+  int kk = k;
+  for (int j = 0; j + 1 < k; ++j)
+    if (!(bev[j] > 0.0)) { kk = j + 1; break; }
+  al.resize(kk);
+  be.assign(bev.begin(), bev.begin() + (kk - 1));
   const double lmin = tridiag_eig(al, be, 0), lmax = tridiag_eig(al, be, (int)al.size() - 1);
   const double fro = sqrt(stats[0]);
   auto lg = [](double x) { return log10(std::max(x, 1e-300)); };
@@ -1149,3 +1171,180 @@ hrp_status hrp_policy_tree(int index, hrp_tree* out) {
 int hrp_last_policy_choice(const hrp_handle* h) { return h ? h->last_choice : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batched solve with FP64 iterative refinement (the many-systems counterpart of hrp_posv).
+// ---------------------------------------------------------------------------------------
+extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n,
+                                       double* const* dA, const int* lda, int nrhs, double* const* dB, const int* ldb,
+                                       double* const* dX, const int* ldx, int max_iter, double tol, int* info,
+                                       int* iters, double* resid, int* used_fallback, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (batch > 0 && !trees) return bad_arg(h, 2, "trees is NULL");
+  hrp_status st = check_batch_args(h, batch, n, dA, lda);
+  if (st != HRP_OK) return st;
+  if (nrhs < 1 || nrhs > 16) return bad_arg(h, 7, "nrhs must be in [1, 16]");
+  if (batch > 0 && (!dB || !ldb || !dX || !ldx)) return bad_arg(h, 8, "NULL B or X arrays");
+  for (int i = 0; i < batch; ++i) {
+    if ((st = validate_tree(h, trees[i], 2)) != HRP_OK) return st;
+    if (tree_has(trees[i], HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "F8 levels are not batched");
+    if (ldb[i] < std::max(1, n[i]) || ldx[i] < std::max(1, n[i])) return bad_arg(h, 9, "ldb/ldx");
+  }
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<SysWork> ws;
+  if ((st = batch_prepare(h, batch, n, ws, true, nrhs)) != HRP_OK) return st;
+  if (batch == 0) return HRP_OK;
+  int* d_info = nullptr;
+  if (cudaMalloc(&d_info, sizeof(int) * batch) != cudaSuccess) return set_err(h, HRP_ERR_ALLOC, "info array");
+  std::vector<int> hinfo(batch, 0), fb(batch, 0), its(batch, 0), done(batch, 0), fresh(batch, 1), restart;
+  std::vector<double> res(batch, 1e300);
+  std::vector<double> norms(2 * nrhs);
+  hrp_tree fallback;
+  hrp_tree_parse("[F32|F64@128]", 128, &fallback);
+  const bool tc = tc_gemm_supported();
+  std::vector<int> which = lpt_assign(batch, n, kBatchStreams);
+  auto fact_of = [&](int i) { return reinterpret_cast<double*>(h->bwork + ws[i].fact); };
+  auto res_of = [&](int i) { return reinterpret_cast<double*>(h->bwork + ws[i].res); };
+  cudaError_t err = cudaSuccess;
+  auto note = [&](cudaError_t e) { if (e != cudaSuccess && err == cudaSuccess) err = e; };
+  const bool timing = h->timing;
+  h->timing = false;
+  // factor copies of every system (mixed trees), then the fallback tree where that failed
+  for (int pass = 0; pass < 2 && err == cudaSuccess; ++pass) {
+    if ((st = fork(h, s)) != HRP_OK) break;
+    for (int i = 0; i < batch; ++i) {
+      if (n[i] == 0 || (pass == 1 && hinfo[i] == 0)) continue;
+      cudaStream_t si = h->bstreams[which[i]];
+      note(launch_copy_lower(fact_of(i), n[i], dA[i], lda[i], n[i], si));
+      Fact f{};
+      f.h = h;
+      f.t = pass == 0 ? trees[i] : &fallback;
+      f.A = fact_of(i);
+      f.lda = n[i];
+      f.n = n[i];
+      f.info = d_info + i;
+      f.s = si;
+      f.tc = tc;
+      f.lds = ws[i].lds;
+      f.shadow = tree_has(f.t, HRP_F16) ? reinterpret_cast<__half*>(h->bwork + ws[i].shadow) : nullptr;
+      f.w32 = reinterpret_cast<float*>(h->bwork + ws[i].w32);
+      f.begin(CLS_OTHER, 0.0);
+      f.chk(launch_fill_int(f.info, INT_MAX, 1, si));
+      f.potrf(0, n[i], 0);
+      f.begin(CLS_OTHER, 0.0);
+      f.chk(launch_finalize_info(f.info, si));
+      note(f.err);
+      if (pass == 1) fb[i] = 1;
+    }
+    if ((st = join(h, s)) != HRP_OK) break;
+    note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
+    note(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int i = 0; i < batch; ++i) any |= hinfo[i] != 0;
+    if (!any) break;
+  }
+  h->timing = timing;
+  // X0 = POTRS(B) in FP32, then rounds of refinement over the systems not yet converged
+  for (int it = 0; st == HRP_OK && err == cudaSuccess; ++it) {
+    if ((st = fork(h, s)) != HRP_OK) break;
+    if (h->epoch > INT_MAX - 4096) h->epoch = 1;
+    const int ep = h->epoch;
+    h->epoch += potrs_epochs(nrhs);
+    for (int i = 0; i < batch; ++i) {
+      if (n[i] == 0 || hinfo[i] != 0 || done[i]) continue;
+      cudaStream_t si = h->bstreams[which[i]];
+      int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
+      if (ep == 1) note(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n[i] + 63) / 64 + 1), si));
+      double* R = res_of(i);
+      if (fresh[i]) {
+        fresh[i] = 0;
+        note(launch_copy_matrix(dX[i], ldx[i], dB[i], ldb[i], n[i], nrhs, si));
+        note(launch_potrs(fact_of(i), n[i], dX[i], ldx[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si));
+      } else {
+        note(launch_potrs(fact_of(i), n[i], R, n[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si));
+        note(launch_axpy_matrix(dX[i], ldx[i], R, n[i], n[i], nrhs, si));
+        ++its[i];
+      }
+      note(launch_residual(dA[i], lda[i], dX[i], ldx[i], dB[i], ldb[i], R, n[i], n[i], nrhs, si));
+      note(launch_col_norms2(R, n[i], dB[i], ldb[i], n[i], nrhs, R + (size_t)n[i] * nrhs, si));
+    }
+    if ((st = join(h, s)) != HRP_OK) break;
+    note(cudaStreamSynchronize(s));
+    if (err != cudaSuccess) break;
+    bool all = true;
+    for (int i = 0; i < batch; ++i) {
+      if (n[i] == 0 || hinfo[i] != 0 || done[i]) continue;
+      note(cudaMemcpy(norms.data(), res_of(i) + (size_t)n[i] * nrhs, sizeof(double) * 2 * nrhs,
+                      cudaMemcpyDeviceToHost));
+      double worst = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        const double rb = norms[nrhs + c] > 0 ? sqrt(norms[c] / norms[nrhs + c]) : sqrt(norms[c]);
+        if (!(rb <= worst)) worst = rb;
+      }
+      const bool stalled = its[i] > 0 && !(worst < res[i]);
+      res[i] = worst;
+      if (worst <= tol || (its[i] >= max_iter && fb[i]) || (stalled && fb[i])) {
+        done[i] = 1;
+      } else if ((stalled || its[i] >= max_iter) && !fb[i]) {
+        restart.push_back(i);          // this factor will not get there: fallback tree
+        all = false;
+      } else {
+        all = false;
+      }
+    }
+    if (!restart.empty()) {
+      // refactor the stalled systems with the fallback tree; they restart their solve
+      if ((st = fork(h, s)) != HRP_OK) break;
+      for (int i : restart) {
+        cudaStream_t si = h->bstreams[which[i]];
+        note(launch_copy_lower(fact_of(i), n[i], dA[i], lda[i], n[i], si));
+        Fact f{};
+        f.h = h;
+        f.t = &fallback;
+        f.A = fact_of(i);
+        f.lda = n[i];
+        f.n = n[i];
+        f.info = d_info + i;
+        f.s = si;
+        f.tc = tc;
+        f.lds = ws[i].lds;
+        f.shadow = nullptr;
+        f.w32 = reinterpret_cast<float*>(h->bwork + ws[i].w32);
+        f.begin(CLS_OTHER, 0.0);
+        f.chk(launch_fill_int(f.info, INT_MAX, 1, si));
+        f.potrf(0, n[i], 0);
+        f.begin(CLS_OTHER, 0.0);
+        f.chk(launch_finalize_info(f.info, si));
+        note(f.err);
+        fb[i] = 1;
+        fresh[i] = 1;
+        its[i] = 0;
+        res[i] = 1e300;
+      }
+      if ((st = join(h, s)) != HRP_OK) break;
+      note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
+      note(cudaStreamSynchronize(s));
+      restart.clear();
+    }
+    if (all) break;
+  }
+  cudaFree(d_info);
+  bool conv = true, spd = true;
+  for (int i = 0; i < batch; ++i) {
+    if (info) info[i] = hinfo[i];
+    if (iters) iters[i] = its[i];
+    if (resid) resid[i] = res[i];
+    if (used_fallback) used_fallback[i] = fb[i];
+    spd &= hinfo[i] == 0;
+    conv &= (hinfo[i] != 0) || n[i] == 0 || res[i] <= tol;
+  }
+  if (st != HRP_OK) return st;
+  if (err != cudaSuccess) return cuda_status(h, err, "hrp_posv_batched");
+  if (!spd) return set_err(h, HRP_ERR_NOT_SPD, "a system failed with the fallback tree too");
+  if (!conv) return set_err(h, HRP_ERR_NO_CONVERGENCE, "a system did not reach tol");
+  return HRP_OK;
+}

@@ -98,10 +98,13 @@ cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int
 int policy_nparam();
 cudaError_t launch_rowsum(const double* A, int lda, int n, double* rowsum, double* stats, cudaStream_t s);
 cudaError_t launch_lanczos_start(double* v, int n, cudaStream_t s);
+// R = -A v (A symmetric from its lower triangle, FP32 arithmetic)
+cudaError_t launch_symv32(const double* A, int lda, const double* v, double* R, int n, cudaStream_t s);
 cudaError_t launch_lanczos_dot(const double* R, const double* v, int n, double* out, cudaStream_t s);
-cudaError_t launch_lanczos_axpy(double* R, const double* v, const double* vp, int n, const double* alpha, double beta,
-                                double* out, cudaStream_t s);
-cudaError_t launch_lanczos_next(const double* w, double* vp, double* v, int n, double inv_beta, cudaStream_t s);
+cudaError_t launch_lanczos_axpy(double* R, const double* v, const double* vp, int n, const double* alpha,
+                                const double* beta, double* out, cudaStream_t s);
+cudaError_t launch_lanczos_next(const double* w, double* vp, double* v, int n, const double* norm2, double* beta,
+                                cudaStream_t s);
 cudaError_t launch_mlp_forward(const float* p, int batch, const float* X, float* Z, cudaStream_t s);
 cudaError_t launch_mlp_grad(const float* p, int batch, const float* X, const int* y, float* g, float* loss,
                             cudaStream_t s);

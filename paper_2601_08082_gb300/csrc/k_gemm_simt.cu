@@ -7,7 +7,11 @@
 namespace hrp {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BM = 64, BN = 64;
+// inner-dimension slice per stage: 16 for FP64, 64 for FP32 accumulation (fewer
+// latency-bound stages for the small GEMMs of the FP32 levels)
+template <int RND> struct Slice { static constexpr int BK = 64; };
+template <> struct Slice<0> { static constexpr int BK = 16; };
 
 template <int RND> struct Acc { using T = float; };
 template <> struct Acc<0> { using T = double; };
@@ -25,6 +29,7 @@ __global__ void __launch_bounds__(256)
 gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, int ldx,
                  const double* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
   using T = typename Acc<RND>::T;
+  constexpr int BK = Slice<RND>::BK;
   __shared__ T Xs[BK][BM + 1];
   __shared__ T Ys[BK][BN + 1];
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;

@@ -289,7 +289,7 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
 // 4-row x (nc/16)-column register tile.
 // ---------------------------------------------------------------------------------------
 constexpr int kT32Rows = 32;
-constexpr int kT32Threads = 128;
+constexpr int kT32Threads = 256;
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -331,16 +331,20 @@ trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   __syncthreads();
   for (int e = tid; e < nc * kT32Rows; e += kT32Threads) Bs[e] = (float)Bd[e];
   __syncthreads();
-  // thread: rows 8*tr .. 8*tr+7, columns 4*tc .. 4*tc+3 (8 x 4 register tile, float4 loads)
-  const int tr = tid & 3, tc = tid >> 2;
+  // thread: rows 8*tr .. 8*tr+7, columns 4*tc .. 4*tc+3 (8 x 4 register tile, float4 loads),
+  // half kh of the inner dimension; the two halves are added through shared memory
+  const int kh = tid >> 7, tt = tid & 127;
+  const int tr = tt & 3, tc = tt >> 2;
   const bool active = 4 * tc < nc;
   float acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  const int khalf = (nc + 1) / 2;
+  const int kbeg = kh ? khalf : 0, kend = kh ? nc : khalf;
   if (active) {
-    for (int k = 0; k < nc; ++k) {
+    for (int k = kbeg; k < kend; ++k) {
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr + 4]);
       const float4 w = *reinterpret_cast<const float4*>(&Ws[k * kT32WLD + 4 * tc]);
@@ -353,8 +357,23 @@ trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
     }
   }
   __syncthreads();
+  float* part = Ws;                                     // W no longer needed: reuse for the halves
+  if (kh == 1 && active) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) part[(8 * tr + a) * kT32WLD + 4 * tc + c] = acc[a][c];
+  }
+  __syncthreads();
+  if (kh == 0 && active) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] += part[(8 * tr + a) * kT32WLD + 4 * tc + c];
+  }
+  __syncthreads();
   // stage X (float) back into Bs, then write master and shadow coalesced
-  if (active) {
+  if (kh == 0 && active) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int j = 4 * tc + c;

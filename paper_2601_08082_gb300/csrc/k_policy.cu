@@ -94,6 +94,40 @@ __global__ void dominance_kernel(const double* __restrict__ A, int lda, int n, c
   }
 }
 
+// R -= A v over lower tiles (A read once in FP64, products and tile sums in FP32: the
+// features need the extreme Ritz values only to a few digits)
+__global__ void __launch_bounds__(256)
+symv32_tile_kernel(const double* __restrict__ A, int lda, const double* __restrict__ v, double* __restrict__ R, int n) {
+  __shared__ float As[FT][FT + 1];
+  __shared__ float vI[FT], vJ[FT];
+  int I, J;
+  tri_index64(blockIdx.x, I, J);
+  const int I0 = I * FT, J0 = J * FT, tid = threadIdx.x;
+  for (int idx = tid; idx < FT * FT; idx += 256) {
+    const int i = idx % FT, j = idx / FT, gi = I0 + i, gj = J0 + j;
+    As[i][j] = (gi < n && gj < n && gi >= gj) ? (float)A[(size_t)gj * lda + gi] : 0.f;
+  }
+  if (tid < FT) {
+    vI[tid] = (I0 + tid < n) ? (float)v[I0 + tid] : 0.f;
+    vJ[tid] = (J0 + tid < n) ? (float)v[J0 + tid] : 0.f;
+  }
+  __syncthreads();
+  if (tid < FT) {
+    float y = 0.f;
+    if (I == J) {
+      for (int j = 0; j < FT; ++j) y = fmaf(j <= tid ? As[tid][j] : As[j][tid], vJ[j], y);
+    } else {
+      for (int j = 0; j < FT; ++j) y = fmaf(As[tid][j], vJ[j], y);
+    }
+    if (I0 + tid < n) atomicAdd(R + I0 + tid, -(double)y);
+  } else if (tid < 2 * FT && I != J) {
+    const int c = tid - FT;
+    float z = 0.f;
+    for (int r = 0; r < FT; ++r) z = fmaf(As[r][c], vI[r], z);
+    if (J0 + c < n) atomicAdd(R + J0 + c, -(double)z);
+  }
+}
+
 __global__ void lanczos_start_kernel(double* v, int n, double inv_norm) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     v[i] = (1.0 + (double)(i % 7) / 7.0) * inv_norm;
@@ -105,10 +139,11 @@ __global__ void lanczos_dot_kernel(const double* R, const double* v, int n, doub
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
-// w = -R - alpha v - beta v_prev (stored into R); out[0] += ||w||^2
+// w = -R - alpha v - beta v_prev (stored into R); out[0] += ||w||^2; beta read from the device
 __global__ void lanczos_axpy_kernel(double* R, const double* v, const double* vp, int n, const double* alpha,
-                                    double beta, double* out) {
+                                    const double* beta_p, double* out) {
   const double a = *alpha;
+  const double beta = beta_p ? *beta_p : 0.0;
   double s = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double w = -R[i] - a * v[i] - beta * vp[i];
@@ -118,10 +153,15 @@ __global__ void lanczos_axpy_kernel(double* R, const double* v, const double* vp
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
-__global__ void lanczos_next_kernel(const double* w, double* vp, double* v, int n, double inv_beta) {
+// beta = ||w|| (from the accumulated square); v_prev = v; v = w / beta (0 if beta is 0)
+__global__ void lanczos_next_kernel(const double* w, double* vp, double* v, int n, const double* norm2,
+                                    double* beta_out) {
+  const double beta = sqrt(*norm2);
+  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *beta_out = beta;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     vp[i] = v[i];
-    v[i] = w[i] * inv_beta;
+    v[i] = w[i] * inv;
   }
 }
 
@@ -230,17 +270,25 @@ cudaError_t launch_lanczos_start(double* v, int n, cudaStream_t s) {
   lanczos_start_kernel<<<64, 256, 0, s>>>(v, n, 1.0 / sqrt(ss));
   return cudaGetLastError();
 }
+cudaError_t launch_symv32(const double* A, int lda, const double* v, double* R, int n, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(R, 0, sizeof(double) * n, s);
+  if (e != cudaSuccess) return e;
+  const long long nt = (n + FT - 1) / FT;
+  symv32_tile_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(A, lda, v, R, n);
+  return cudaGetLastError();
+}
 cudaError_t launch_lanczos_dot(const double* R, const double* v, int n, double* out, cudaStream_t s) {
   lanczos_dot_kernel<<<64, 256, 0, s>>>(R, v, n, out);
   return cudaGetLastError();
 }
-cudaError_t launch_lanczos_axpy(double* R, const double* v, const double* vp, int n, const double* alpha, double beta,
-                                double* out, cudaStream_t s) {
+cudaError_t launch_lanczos_axpy(double* R, const double* v, const double* vp, int n, const double* alpha,
+                                const double* beta, double* out, cudaStream_t s) {
   lanczos_axpy_kernel<<<64, 256, 0, s>>>(R, v, vp, n, alpha, beta, out);
   return cudaGetLastError();
 }
-cudaError_t launch_lanczos_next(const double* w, double* vp, double* v, int n, double inv_beta, cudaStream_t s) {
-  lanczos_next_kernel<<<64, 256, 0, s>>>(w, vp, v, n, inv_beta);
+cudaError_t launch_lanczos_next(const double* w, double* vp, double* v, int n, const double* norm2, double* beta,
+                                cudaStream_t s) {
+  lanczos_next_kernel<<<64, 256, 0, s>>>(w, vp, v, n, norm2, beta);
   return cudaGetLastError();
 }
 cudaError_t launch_mlp_forward(const float* p, int batch, const float* X, float* Z, cudaStream_t s) {

@@ -29,7 +29,7 @@ EXPORTED = [
     "hrp_create", "hrp_destroy", "hrp_last_arg", "hrp_last_error", "hrp_status_string",
     "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
     "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
-    "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched",
+    "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched", "hrp_posv_batched",
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
 ]
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
     L.hrp_potrs_noalloc.argtypes = [c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_potrf_batched.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp]
     L.hrp_potrs_batched.argtypes = [vp, c_int, vp, vp, vp, c_int, vp, vp, vp]
+    L.hrp_posv_batched.argtypes = [vp, vp, c_int, vp, vp, vp, c_int, vp, vp, vp, vp, c_int, c_double, ip, ip, dp,
+                                   ip, vp]
     fp = ctypes.POINTER(ctypes.c_float)
     L.hrp_policy_features.argtypes = [vp, c_int, vp, c_int, c_int, fp, vp]
     L.hrp_mlp_forward.argtypes = [vp, vp, c_int, vp, vp, vp]
@@ -236,7 +238,24 @@ class Handle:
         self._check(st)
 
     # ---- learned policy ----
-    def policy_features(self, A, lanczos_steps: int = 24, n: int | None = None, stream=None) -> np.ndarray:
+    TIMING_CLASSES = ("leaf_potrf_fp64", "leaf_trsm", "gemm_f16_tcgen05", "gemm_simt", "other")
+
+    def timing(self, tree, A, n: int | None = None) -> dict:
+        """Factor A once with per-launch event timing; per kernel class: device ms,
+        launches and the algorithmic flops those launches did (hrp_get_timing)."""
+        n = A.shape[0] if n is None else n
+        self._lib.hrp_set_timing(self._h, 1)
+        try:
+            self.potrf(tree, A, n=n)
+            buf = (ctypes.c_double * 15)()
+            if self._lib.hrp_get_timing(self._h, buf, 15) != 15:
+                raise HrpError("hrp_get_timing returned fewer than 15 values")
+        finally:
+            self._lib.hrp_set_timing(self._h, 0)
+        return {name: {"ms": buf[3 * c], "launches": int(buf[3 * c + 1]), "flops": buf[3 * c + 2]}
+                for c, name in enumerate(self.TIMING_CLASSES)}
+
+    def policy_features(self, A, lanczos_steps: int = 10, n: int | None = None, stream=None) -> np.ndarray:
         n = A.shape[0] if n is None else n
         f = (ctypes.c_float * 12)()
         st = self._lib.hrp_policy_features(self._h, n, _ptr(A), A.shape[1], lanczos_steps, f, _stream(stream))
@@ -270,6 +289,26 @@ class Handle:
 
     def last_policy_choice(self) -> int:
         return self._lib.hrp_last_policy_choice(self._h)
+
+    def posv_batched(self, trees, As, Bs, Xs, max_iter: int = 30, tol: float = 1e-12, stream=None) -> dict:
+        batch = len(As)
+        if isinstance(trees, Tree):
+            trees = [trees] * batch
+        keep = list(trees)
+        tptr = (ctypes.POINTER(Tree) * batch)(*[ctypes.pointer(t) for t in keep])
+        arr_i = lambda v: (ctypes.c_int * batch)(*v)
+        arr_p = lambda ts: (ctypes.c_void_p * batch)(*[t.data_ptr() for t in ts])
+        info, iters, fb = arr_i([0] * batch), arr_i([0] * batch), arr_i([0] * batch)
+        resid = (ctypes.c_double * batch)()
+        nrhs = Bs[0].shape[0] if batch else 1
+        st = self._lib.hrp_posv_batched(self._h, ctypes.cast(tptr, ctypes.c_void_p), batch,
+                                        arr_i([A.shape[0] for A in As]), arr_p(As), arr_i([A.shape[1] for A in As]),
+                                        nrhs, arr_p(Bs), arr_i([B.shape[1] for B in Bs]), arr_p(Xs),
+                                        arr_i([X.shape[1] for X in Xs]), max_iter, tol, info, iters, resid, fb,
+                                        _stream(stream))
+        self._check(st, allow=(2, 3))
+        return {"status": st, "info": list(info), "iters": list(iters), "resid": list(resid),
+                "used_fallback": list(fb)}
 
     def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
         n = A.shape[0] if n is None else n

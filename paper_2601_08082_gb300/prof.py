@@ -23,6 +23,8 @@ def main() -> int:
     ap.add_argument("--leaf", type=int, default=128)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=0, help="also solve with this many right-hand sides")
+    ap.add_argument("--timing", action="store_true",
+                    help="print per-kernel-class device time of the last factorization (event timing mode)")
     args = ap.parse_args()
 
     import torch
@@ -44,6 +46,19 @@ def main() -> int:
             B = B0.clone()
             h.potrs(A, B)
     torch.cuda.synchronize()
+    if args.timing:
+        import json
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        A = A0.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        h.potrf(tree, A)
+        e1.record()
+        torch.cuda.synchronize()
+        classes = h.timing(tree, A0.clone())
+        print(json.dumps({"n": args.n, "tree": args.tree, "leaf": args.leaf, "ms": e0.elapsed_time(e1),
+                          "classes": classes}))
     print(f"{args.reps} factorizations of n={args.n} tree {args.tree}: {h.launch_count()} launches each")
     h.close()
     return 0

@@ -65,7 +65,7 @@ def label_one(h, A, hrp, torch):
     from synth import rhs, seed_for
     n = A.shape[0]
     A = A.contiguous()
-    feat = h.policy_features(A)
+    feat = h.policy_features(A, lanczos_steps=10)
     B = hrp.colmajor(rhs(n, 1, seed_for(5, 7))).cuda()
     X = torch.zeros_like(B)
     times = np.full(NTREES, np.inf)

@@ -352,3 +352,23 @@ def test_batched_graph_capture_replays(hrp_mod, handle):
         torch.cuda.synchronize()
         for A, R in zip(As, ref):
             assert torch.equal(torch.tril(A.T), torch.tril(R.T))
+
+
+def test_posv_batched_refines_every_system(hrp_mod, handle):
+    import torch
+    from synth import rbf_spd
+    sizes = [64, 300, 129, 700, 512]
+    mats = [rbf_spd(n, seed_for(4, 200 + i)) for i, n in enumerate(sizes)]
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    Bs = [hrp_mod.colmajor(rhs(n, 4, seed_for(4, 300 + i))).cuda() for i, n in enumerate(sizes)]
+    Xs = [torch.zeros_like(B) for B in Bs]
+    keep = [A.clone() for A in As]
+    out = handle.posv_batched(hrp_mod.tree_parse("[F16,F32|F64@128]", 128), As, Bs, Xs, tol=1e-12)
+    assert out["status"] == 0 and out["info"] == [0] * len(sizes)
+    for A, K in zip(As, keep):
+        assert torch.equal(A, K)                           # inputs untouched
+    for i, A in enumerate(mats):
+        X = hrp_mod.from_colmajor(Xs[i])
+        B = hrp_mod.from_colmajor(Bs[i])
+        assert np.max(dense.column_residuals(A, X, B)) <= 1e-12
+        assert abs(out["resid"][i] - np.max(dense.column_residuals(A, X, B))) <= 1e-12
