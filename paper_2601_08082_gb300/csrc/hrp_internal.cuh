@@ -32,6 +32,11 @@ enum class OpRound : int { F64 = 0, F32 = 1, F16 = 2 };
 cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64, bool round16,
                               float* W32, int ldw, int* info, cudaStream_t s);
 
+// The same FP64 leaf POTRF (no FP16 rounding) on a cluster of 8 CTAs holding 16 x 16
+// tiles in shared memory (k_leaf_cluster.cu); launch_potrf_leaf uses it for n > 32.
+cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float* W32, int ldw, int* info,
+                                      cudaStream_t s);
+
 // Leaf TRSM B <- B L^{-T} with B = A[r0.., c0..] (m x nc) and L = A[c0.., c0..] (nc x nc),
 // in FP64 by substitution.  shadow16 (row-major, lds) receives FP16(X) if non-null.
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,

@@ -403,6 +403,7 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
                               float* W32, int ldw, int* info, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 128) return cudaErrorInvalidValue;
+  if (compute64 && !round16 && n > 32) return launch_potrf_leaf_cluster(A, ld, n, col0, W32, ldw, info, s);
   const size_t smem = W32 ? (size_t)2 * 128 * kInvLD * 4 : 0;
   static bool attr_done = false;     // one opt-in to the largest footprint (n = 128, with W)
   if (!attr_done) {

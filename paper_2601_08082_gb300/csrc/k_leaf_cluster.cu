@@ -1,0 +1,518 @@
+// Leaf POTRF (Alg. 1 base case) in FP64 spread over a cluster of 8 CTAs.
+//
+// FP64 on this GPU: each SM sub-partition issues one FP64 warp instruction per ~64
+// cycles (also the dependent latency), the SM as a whole about one per 19 cycles
+// (1.7 lane-FMAs per clock, 1.2 TFLOP/s for the device), and a warp instruction costs the
+// same however few lanes are active.  The n^3/6 FMAs of a 128 x 128 leaf therefore keep
+// one SM busy for ~100 us, and every leaf lies on the recursion's critical path.  Here the
+// block is cut into 16 x 16 tiles; tile (I, J), I >= J, lives in the shared memory of CTA
+// (I + J) mod 8 for the whole factorization (at most 5 tiles per CTA), and the block is
+// factored right-looking by tile columns p = 0, 1, ...:
+//   A  the owner D of (p, p) applies the update of panel p-1 to it, factors it
+//      (potrf16_chain) and stores L_pp into the shared memory of the CTAs that need it,
+//      while the other CTAs apply the update of panel p-1 to their tiles;
+//                                                                      cluster barrier
+//   B  the owners of (I, p), I > p, solve X L_pp^T = A_Ip (TRSM) and store the result
+//      into the shared memory of every CTA that updates a tile with it; D applies the
+//      update of panel p-1 to its other tiles;                         cluster barrier
+// Finished panel tiles are written into the consumers' shared memory (distributed shared
+// memory stores, double-buffered by panel parity), so no CTA waits on a remote load
+// inside the loop.  The only waits are the hardware cluster barriers, which every thread
+// of the cluster reaches the same number of times (a failed pivot is seen by all CTAs
+// after the same barrier).  The FP32 inverse W = L^{-1} for the FP32 leaf TRSM (when
+// requested) is built at the end by column blocks, one CTA per block:
+// W_JJ = L_JJ^{-1}, W_IJ = -L_II^{-1} sum_{K=J}^{I-1} L_IK W_KJ.
+#include <climits>
+#include <cooperative_groups.h>
+
+#include "hrp_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hrp {
+namespace {
+
+constexpr int kCL = 8;                  // CTAs per cluster (portable size)
+constexpr int kTS = 16;                 // tile edge
+constexpr int kTLD = 17;                // padded row length of a tile (elements)
+constexpr int kTileD = kTS * kTLD;      // elements per tile slot
+constexpr int kMaxOwn = 5;              // tiles per CTA for 8 x 8 tiles owned by (I + J) mod 8
+constexpr int kCThreads = 128;
+constexpr int kLowT = kTS * (kTS + 1) / 2;   // entries of a lower 16 x 16 triangle
+constexpr int kMaxGather = 36;               // W phase: tiles one CTA reads (28 of L, 8 inverses)
+
+struct ClusterLeafSmem {
+  double own[kMaxOwn][kTileD];          // owned tiles, row-major (row i at i * kTLD)
+  double pan[2][8][kTileD];             // pan[p & 1][I] = L_{I,p} (I > p) or L_pp (I = p)
+  double cv[kTS][kTS];                  // pivot chain: cv[k][i] = a_ik after the updates of columns < k
+  double dpr[kTS + 2];                  // pivot chain: a_kk after the updates of columns < k - 1
+  double usq[kTS + 2];                  // pivot chain: a_{k,k-1}^2 after the updates of columns < k - 1
+  double dk[kTS];                       // pivots d_k
+  double sk[kTS];                       // 1 / d_k
+  double rinv[kTS];                     // 1 / L_kk = d_k^{-1/2} of the diagonal tile factored last here
+  double rin_copy[kTS];                 // rinv of the diagonal tile the TRSM here uses
+  float ownf[kMaxOwn][kTileD];          // FP32 copies of the finished owned tiles
+  float winv[2][kTileD];                // FP32 inverses of the (up to 2) diagonal tiles owned
+  float gat[kMaxGather][kTileD];        // W phase: gathered FP32 tiles
+  float wcol[8][kTileD];                // W phase: W_KJ of this CTA's column block
+  float tmp[kTileD];                    // W phase: sum_K L_IK W_KJ
+  const float* gsrc[kMaxGather];        // W phase: where each gathered tile comes from
+  int fail;                             // read by the cluster: the last diagonal tile here failed
+  int cfail;                            // pivot chain: column of the failed pivot, or -1
+  signed char slot[8][8];               // slot of tile (I, J) in its owner's `own`
+};
+
+__device__ __forceinline__ int owner_of(int I, int J) { return (I + J) & (kCL - 1); }
+
+// (i, j) of entry e of a lower 16 x 16 triangle enumerated row by row
+__device__ __forceinline__ void lower_entry(int e, int& i, int& j) {
+  i = 0;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  j = e - i * (i + 1) / 2;
+}
+
+// 0: not positive or not finite; 1: positive finite outside the single-precision seed range;
+// 2: positive with |log2 d| < 120.  Integer tests on the bits (no FP64 instruction).
+__device__ __forceinline__ int pivot_class(double d) {
+  const long long b = __double_as_longlong(d);
+  if (b <= 0) return 0;
+  const int ex = (int)(b >> 52);
+  if (ex == 0x7ff) return 0;
+  return (ex > 1023 - 120 && ex < 1023 + 120) ? 2 : 1;
+}
+
+// 1/d from the single-precision reciprocal x0 and one third-order step of Householder's
+// iteration for 1/x - d = 0: with e = 1 - d x0, 1/d = x0 / (1 - e) = x0 (1 + e + e^2 + O(e^3)).
+// The seed (rounding of d plus the approximation, |e| < 2^-21) leaves a truncation error
+// below 2^-63; three dependent FP64 operations after the seed.  pivot_class(d) == 2.
+__device__ __forceinline__ double recip_third_order(double d) {
+  float xf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"((float)d));
+  const double x0 = (double)xf;
+  const double e = fma(-d, x0, 1.0);
+  const double w = fma(e, e, e);
+  return fma(x0, w, x0);
+}
+
+// 1/sqrt(d) from a single-precision seed r0 and one third-order step: with
+// e = 1 - d r0^2, d^{-1/2} = r0 (1 - e)^{-1/2} = r0 (1 + e/2 + 3e^2/8 + O(e^3)); the seed's
+// |e| < 2^-20 leaves a truncation error below 2^-60.  Values outside the single-precision
+// exponent range take the library sqrt.
+__device__ __forceinline__ double rsqrt_third_order(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  const double r = (double)rsqrtf((float)d);
+  const double e = fma(-d * r, r, 1.0);
+  const double t = fma(0.375, e, 0.5);
+  return fma(r * e, t, r);
+}
+
+// C -= LI * LJ^T for an off-diagonal 16 x 16 tile, by the 128 threads:
+// thread (i, cp) = (tid / 8, tid % 8) owns C[i][2cp], C[i][2cp + 1].
+__device__ __forceinline__ void tile_update(double* __restrict__ C, const double* __restrict__ LI,
+                                            const double* __restrict__ LJ, int tid) {
+  const int i = tid >> 3, j0 = 2 * (tid & 7);
+  double c0 = C[i * kTLD + j0], c1 = C[i * kTLD + j0 + 1];
+#pragma unroll
+  for (int k = 0; k < kTS; ++k) {
+    const double a = LI[i * kTLD + k];
+    c0 = fma(-a, LJ[j0 * kTLD + k], c0);
+    c1 = fma(-a, LJ[(j0 + 1) * kTLD + k], c1);
+  }
+  C[i * kTLD + j0] = c0;
+  C[i * kTLD + j0 + 1] = c1;
+}
+
+// C -= LI * LI^T on the lower triangle of a diagonal tile: the 136 entries are dealt to
+// the 128 threads (8 threads take two), so every warp issues about 16 FMAs.
+__device__ __forceinline__ void tile_update_diag(double* __restrict__ C, const double* __restrict__ LI, int tid) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + kCThreads * h;
+    if (e >= kLowT) break;
+    int i, j;
+    lower_entry(e, i, j);
+    double c = C[i * kTLD + j];
+#pragma unroll
+    for (int k = 0; k < kTS; ++k) c = fma(-LI[i * kTLD + k], LI[j * kTLD + k], c);
+    C[i * kTLD + j] = c;
+  }
+}
+
+// Cholesky of the 16 x 16 tile T (lower part, row-major kTLD) by the 128 threads.  The
+// column recurrence runs alone on thread 0 (warp 0, sub-partition 0):
+//   d_{k+1} = d'_{k+1} - u_{k+1} s_k,  s_k = 1/d_k,
+// with d'_{k+1} = a_{k+1,k+1} and u_{k+1} = a_{k+1,k}^2 after the updates of columns < k.
+// Warps 1 and 2 apply the update of column k, a_ij -= (a_ik s_k) a_jk for i >= j > k, one
+// step behind and publish what the next steps read; each of their threads holds up to
+// three consecutive entries of one row, so a warp issues at most five FP64 instructions
+// per column and the two of them stay below the SM's FP64 issue limit that would slow
+// the recurrence.  One CTA barrier per column.  At the end l_jj = d_j r_j and
+// l_ij = a_ij r_j (a_ij after the updates of columns < j), r_j = d_j^{-1/2}, also stored in
+// sm.rinv.  Returns the 0-based column of the first pivot that is not positive and
+// finite, or -1 (the same in every thread).
+__device__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+  const int warp = tid >> 5;
+  int wi = -1, wj0 = 0, wcnt = 0;
+  double a[3] = {0.0, 0.0, 0.0};
+  if (warp == 1 || warp == 2) {
+    const int w = tid - 32;
+    for (int i = 0, idx = 0; i < kTS; ++i) {       // row i has ceil((i + 1) / 3) segments
+      const int ns = (i + 3) / 3;
+      if (wi < 0 && w < idx + ns) {
+        wi = i;
+        wj0 = 3 * (w - idx);
+        wcnt = min(3, i + 1 - wj0);
+      }
+      idx += ns;
+    }
+    if (wi >= 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < wcnt) a[q] = T[wi * kTLD + wj0 + q];
+      if (wj0 == 0) sm.cv[0][wi] = a[0];
+      if (wi == 1) {
+        sm.dpr[1] = a[1];
+        sm.usq[1] = a[0] * a[0];
+      }
+    }
+  } else if (tid == 0) {
+    const double d0 = T[0];
+    const int c = pivot_class(d0);
+    sm.cfail = c ? -1 : 0;
+    sm.dk[0] = d0;
+    sm.sk[0] = (c == 2) ? recip_third_order(d0) : 1.0 / d0;
+  }
+  __syncthreads();
+  int bad = sm.cfail;
+  for (int k = 0; k + 1 < kTS && bad < 0; ++k) {
+    if (tid == 0) {
+      const double d = fma(-sm.usq[k + 1], sm.sk[k], sm.dpr[k + 1]);
+      const int c = pivot_class(d);
+      if (!c) sm.cfail = k + 1;
+      sm.dk[k + 1] = d;
+      sm.sk[k + 1] = (c == 2) ? recip_third_order(d) : 1.0 / d;
+    } else if (wi > k && wj0 + wcnt - 1 > k) {
+      const double t = sm.cv[k][wi] * sm.sk[k];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int j = wj0 + q;
+        if (q < wcnt && j > k) {
+          a[q] = fma(-t, sm.cv[k][j], a[q]);
+          if (j == k + 1) sm.cv[k + 1][wi] = a[q];
+          if (wi == k + 2) {
+            if (j == k + 2) sm.dpr[k + 2] = a[q];
+            else if (j == k + 1) sm.usq[k + 2] = a[q] * a[q];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    bad = sm.cfail;
+  }
+  if (bad >= 0) return bad;
+  if (tid < kTS) sm.rinv[tid] = rsqrt_third_order(sm.dk[tid]);
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + kCThreads * h;
+    if (e >= kLowT) break;
+    int i, j;
+    lower_entry(e, i, j);
+    T[i * kTLD + j] = (i == j ? sm.dk[j] : sm.cv[j][i]) * sm.rinv[j];
+  }
+  return -1;
+}
+
+// X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
+// threads: thread (i, cp) = (tid / 8, tid % 8) holds A[i][2cp], A[i][2cp + 1]; x_ik is
+// passed along the row's 8 threads by a shuffle.
+__device__ __forceinline__ void trsm16(double* __restrict__ A, const double* __restrict__ L,
+                                       const double* __restrict__ rinv, int tid) {
+  const int i = tid >> 3, cp = tid & 7, lane = tid & 31, j0 = 2 * cp;
+  double c0 = A[i * kTLD + j0], c1 = A[i * kTLD + j0 + 1];
+#pragma unroll
+  for (int k = 0; k < kTS; ++k) {
+    const int kc = k >> 1;
+    double x = 0.0;
+    if (cp == kc) {
+      if (k & 1) { c1 *= rinv[k]; x = c1; }
+      else { c0 *= rinv[k]; x = c0; }
+    }
+    x = __shfl_sync(0xffffffffu, x, (lane & ~7) | kc);
+    if (j0 > k) c0 = fma(-x, L[j0 * kTLD + k], c0);
+    if (j0 + 1 > k) c1 = fma(-x, L[(j0 + 1) * kTLD + k], c1);
+  }
+  A[i * kTLD + j0] = c0;
+  A[i * kTLD + j0 + 1] = c1;
+}
+
+// Store the 16 x 16 tile T into slot `dst` of the shared memory of every CTA in `mask`.
+__device__ __forceinline__ void push_tile(cg::cluster_group& cluster, const double* __restrict__ T, double* dst,
+                                          unsigned mask, int tid) {
+  const int e0 = tid, e1 = tid + kCThreads;
+  const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
+  const double v0 = T[o0], v1 = T[o1];
+  for (int r = 0; r < kCL; ++r)
+    if (mask & (1u << r)) {
+      double* d = cluster.map_shared_rank(dst, r);
+      d[o0] = v0;
+      d[o1] = v1;
+    }
+}
+
+// FP32 copy of the 16 x 16 tile
+__device__ __forceinline__ void to_f32(const double* __restrict__ T, float* __restrict__ F, int tid) {
+  const int e0 = tid, e1 = tid + kCThreads;
+  const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
+  F[o0] = (float)T[o0];
+  F[o1] = (float)T[o1];
+}
+
+// FP32 inverse of the lower 16 x 16 tile Lf (FP32, row-major kTLD) into Wv, by lanes
+// 0..15 of one warp: lane c forms column c by forward substitution, dividing by L_rr as a
+// product with the FP32 rounding of rinv[r] = 1/L_rr.
+__device__ __forceinline__ void trtri16_f32(const float* __restrict__ Lf, const double* __restrict__ rinv,
+                                            float* __restrict__ Wv, int lane) {
+  if (lane >= kTS) return;
+  const int c = lane;
+  float w[kTS];
+#pragma unroll
+  for (int r = 0; r < kTS; ++r) {
+    float s = (r == c) ? 1.f : 0.f;
+#pragma unroll
+    for (int q = 0; q < r; ++q) s = fmaf(-Lf[r * kTLD + q], w[q], s);
+    w[r] = (r >= c) ? s * (float)rinv[r] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < kTS; ++r) Wv[r * kTLD + c] = w[r];
+}
+
+// CTAs holding a tile that is updated with L_{I,p}: owners of (I, J), p < J <= I, and of (J, I), J >= I
+__device__ __forceinline__ unsigned consumers(int I, int p, int NT) {
+  unsigned m = 0;
+  for (int J = p + 1; J <= I; ++J) m |= 1u << owner_of(I, J);
+  for (int J = I; J < NT; ++J) m |= 1u << owner_of(J, I);
+  return m;
+}
+
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kCThreads, 1)
+potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
+                          int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ClusterLeafSmem& sm = *reinterpret_cast<ClusterLeafSmem*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int NT = (n + kTS - 1) / kTS;
+
+  // an earlier block failed: stop like LAPACK (every CTA reads the same value: nothing in
+  // this kernel writes info before the first cluster barrier)
+  const bool skip = *(volatile int*)info != INT_MAX;
+  if (tid == 0) {
+    int cnt[kCL] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int J = 0; J < 8; ++J)
+      for (int I = 0; I < 8; ++I) sm.slot[I][J] = (I >= J && I < NT) ? (signed char)(cnt[owner_of(I, J)]++) : -1;
+    sm.fail = 0;
+  }
+  __syncthreads();
+  // load the owned tiles; rows / columns past n are the identity
+  if (!skip) {
+    for (int J = 0; J < NT; ++J)
+      for (int I = J; I < NT; ++I) {
+        if (owner_of(I, J) != rank) continue;
+        double* T = sm.own[sm.slot[I][J]];
+        for (int e = tid; e < kTS * kTS; e += kCThreads) {
+          const int jj = e >> 4, ii = e & 15;        // column-major walk: coalesced reads
+          const int gi = kTS * I + ii, gj = kTS * J + jj;
+          double v;
+          if (gi < n && gj < n) v = (gi >= gj) ? A[(size_t)gj * ld + gi] : 0.0;
+          else v = (gi == gj) ? 1.0 : 0.0;
+          T[ii * kTLD + jj] = v;
+        }
+      }
+  }
+  cluster.sync();
+  if (skip) return;
+
+  bool failed = false;
+  for (int p = 0; p < NT; ++p) {
+    const int D = owner_of(p, p);
+    const int cur = p & 1, prev = cur ^ 1;
+    // ---- A ----
+    if (rank == D) {
+      double* T = sm.own[sm.slot[p][p]];
+      if (p > 0) {
+        tile_update_diag(T, sm.pan[prev][p], tid);
+        __syncthreads();
+      }
+      const int bad = potrf16_chain(T, sm, tid);
+      if (bad >= 0) {
+        if (tid == 0) {
+          atomicMin(info, col0 + kTS * p + bad + 1);
+          sm.fail = 1;
+        }
+      } else {
+        __syncthreads();                                       // L_pp and rinv complete
+        unsigned trsm_ctas = 0;
+        for (int I = p + 1; I < NT; ++I) trsm_ctas |= 1u << owner_of(I, p);
+        push_tile(cluster, T, sm.pan[cur][p], trsm_ctas, tid);
+        if (tid < kTS)
+          for (int r = 0; r < kCL; ++r)
+            if (trsm_ctas & (1u << r)) cluster.map_shared_rank(sm.rin_copy, r)[tid] = sm.rinv[tid];
+      }
+    } else if (p > 0) {
+      for (int J = p; J < NT; ++J)
+        for (int I = J; I < NT; ++I)
+          if (owner_of(I, J) == rank) {
+            double* C = sm.own[sm.slot[I][J]];
+            if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
+            else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
+          }
+    }
+    cluster.sync();                                              // S1
+    if (*(volatile int*)cluster.map_shared_rank(&sm.fail, D)) { failed = true; break; }
+    // ---- B ----
+    int mine = -1;
+    for (int I = p + 1; I < NT; ++I)
+      if (owner_of(I, p) == rank) mine = I;
+    if (mine >= 0) {
+      double* X = sm.own[sm.slot[mine][p]];
+      trsm16(X, sm.pan[cur][p], sm.rin_copy, tid);
+      __syncthreads();
+      push_tile(cluster, X, sm.pan[cur][mine], consumers(mine, p, NT), tid);
+      if (W32) to_f32(X, sm.ownf[sm.slot[mine][p]], tid);
+    }
+    if (rank == D) {
+      if (p > 0)
+        for (int J = p + 1; J < NT; ++J)
+          for (int I = J; I < NT; ++I)
+            if (owner_of(I, J) == rank) {
+              double* C = sm.own[sm.slot[I][J]];
+              if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
+              else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
+            }
+      if (W32) {
+        float* F = sm.ownf[sm.slot[p][p]];
+        to_f32(sm.own[sm.slot[p][p]], F, tid);
+        __syncthreads();
+        if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p >= 4 ? 1 : 0], lane);
+      }
+    }
+    cluster.sync();                                              // S2
+  }
+  if (!failed) {
+    // store the owned tiles (lower part inside the block)
+    for (int J = 0; J < NT; ++J)
+      for (int I = J; I < NT; ++I) {
+        if (owner_of(I, J) != rank) continue;
+        const double* T = sm.own[sm.slot[I][J]];
+        for (int e = tid; e < kTS * kTS; e += kCThreads) {
+          const int jj = e >> 4, ii = e & 15;
+          const int gi = kTS * I + ii, gj = kTS * J + jj;
+          if (gi < n && gj < n && gi >= gj) A[(size_t)gj * ld + gi] = T[ii * kTLD + jj];
+        }
+      }
+    // FP32 inverse, column block J = rank: gather L_IK (J <= K < I) and W_II (I >= J)
+    const int J = rank;
+    if (W32 && J < NT) {
+      const int m = NT - J;
+      const int nl = m * (m - 1) / 2, ng = nl + m;
+      if (tid < ng) {
+        const float* src;
+        if (tid < nl) {
+          int I = J + 1, t = tid;                 // enumerate (I, K), K = J .. I-1, row by row
+          while (t >= I - J) {
+            t -= I - J;
+            ++I;
+          }
+          const int K = J + t;
+          src = cluster.map_shared_rank(sm.ownf[sm.slot[I][K]], owner_of(I, K));
+        } else {
+          const int I = J + (tid - nl);
+          src = cluster.map_shared_rank(sm.winv[I >= 4 ? 1 : 0], owner_of(I, I));
+        }
+        sm.gsrc[tid] = src;
+      }
+      __syncthreads();
+      // kTileD = 272 floats = 68 float4 per tile; 8 loads in flight per thread
+      constexpr int kV4 = kTileD / 4;
+      const int nchunk = ng * kV4;
+      for (int c0 = tid; c0 < nchunk; c0 += 8 * kCThreads) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + u * kCThreads;
+          if (c < nchunk) v[u] = reinterpret_cast<const float4*>(sm.gsrc[c / kV4])[c % kV4];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + u * kCThreads;
+          if (c < nchunk) reinterpret_cast<float4*>(sm.gat[c / kV4])[c % kV4] = v[u];
+        }
+      }
+      __syncthreads();
+      // gathered index of L_IK: row I starts at (I-J-1)(I-J)/2; W_II follows the nl L tiles
+      for (int e = tid; e < kTileD; e += kCThreads) sm.wcol[J][e] = sm.gat[nl][e];
+      __syncthreads();
+      const int r = tid >> 3, q0 = (tid & 7) * 2;
+      for (int I = J + 1; I < NT; ++I) {
+        // tmp = sum_K L_IK W_KJ ; thread: row r, columns q0, q0 + 1
+        float s0 = 0.f, s1 = 0.f;
+        for (int K = J; K < I; ++K) {
+          const float* L = sm.gat[(I - J - 1) * (I - J) / 2 + (K - J)];
+#pragma unroll
+          for (int k = 0; k < kTS; ++k) {
+            const float l = L[r * kTLD + k];
+            s0 = fmaf(l, sm.wcol[K][k * kTLD + q0], s0);
+            s1 = fmaf(l, sm.wcol[K][k * kTLD + q0 + 1], s1);
+          }
+        }
+        sm.tmp[r * kTLD + q0] = s0;
+        sm.tmp[r * kTLD + q0 + 1] = s1;
+        __syncthreads();
+        const float* Wi = sm.gat[nl + (I - J)];
+        float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+        for (int mm = 0; mm < kTS; ++mm) {
+          const float wv = Wi[r * kTLD + mm];
+          o0 = fmaf(-wv, sm.tmp[mm * kTLD + q0], o0);
+          o1 = fmaf(-wv, sm.tmp[mm * kTLD + q0 + 1], o1);
+        }
+        sm.wcol[I][r * kTLD + q0] = o0;
+        sm.wcol[I][r * kTLD + q0 + 1] = o1;
+        __syncthreads();
+      }
+      // write column block J of W (column-major, zeros above the diagonal)
+      for (int jj = warp; jj < kTS; jj += kCThreads / 32) {
+        const int gj = kTS * J + jj;
+        if (gj >= n) break;
+        for (int gi = lane; gi < n; gi += 32) {
+          const int I = gi >> 4, ii = gi & 15;
+          float v = 0.f;
+          if (I > J || (I == J && ii >= jj)) v = sm.wcol[I][ii * kTLD + jj];
+          W32[(size_t)gj * ldw + gi] = v;
+        }
+      }
+    }
+  }
+  cluster.sync();                       // no CTA leaves while others may read its tiles
+}
+
+}  // namespace
+
+cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float* W32, int ldw, int* info,
+                                      cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (n > 128) return cudaErrorInvalidValue;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(potrf_leaf_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(ClusterLeafSmem));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  potrf_leaf_cluster_kernel<<<kCL, kCThreads, sizeof(ClusterLeafSmem), s>>>(A, ld, n, col0, W32, ldw, info);
+  return cudaGetLastError();
+}
+
+}  // namespace hrp

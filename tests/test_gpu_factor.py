@@ -59,6 +59,26 @@ def test_fp64_tree_other_leaves(hrp_mod, handle, leaf):
     assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
 
 
+@pytest.mark.parametrize("n", [33, 47, 64, 100, 127, 128])
+def test_single_fp64_leaf_on_a_cluster(hrp_mod, handle, n):
+    # one leaf of order n (the 8-CTA tile kernel for 32 < n <= 128, ragged last tile)
+    A = dominant_spd(n, 1.05, seed_for(0, 40 + n))
+    L, info, _ = _factor(hrp_mod, handle, A, "[F64]", 128)
+    assert info == 0
+    L0, _ = dense.cholesky(A)
+    assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
+
+
+@pytest.mark.parametrize("col", [1, 16, 17, 90, 127])
+def test_single_fp64_leaf_reports_failing_column(hrp_mod, handle, col):
+    n = 127
+    A = dominant_spd(n, 2.0, seed_for(0, 41))
+    A[col - 1, col - 1] = -1e3
+    _, info0 = dense.cholesky(A)
+    _, info, _ = _factor(hrp_mod, handle, A, "[F64]", 128)
+    assert info == info0 == col
+
+
 def test_upper_triangle_untouched(hrp_mod, handle):
     n = 200
     A = dominant_spd(n, 2.0, seed_for(0, 5))
