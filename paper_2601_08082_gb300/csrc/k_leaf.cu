@@ -284,17 +284,17 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
 
 // ---------------------------------------------------------------------------------------
 // Leaf TRSM in FP32 through the inverse of the diagonal block: X = fl32(B) W^T with
-// W = fl32(L)^{-1} precomputed by the leaf POTRF.  One CTA owns 32 full rows of the
-// panel (so reading B and writing X in place never race), 128 threads, each thread a
-// 4-row x (nc/16)-column register tile.
+// W = fl32(L)^{-1} precomputed by the leaf POTRF.  One CTA owns 16 full rows of the
+// panel (so reading B and writing X in place never race): 256 threads, warp w the rows
+// 2w and 2w + 1, lane c the columns 4c .. 4c + 3; per k one 16-byte load of W(4c.., k) and
+// one broadcast of B(row, k) per row feed 8 FMAs.  Small CTAs (about 76 KB of shared
+// memory, two per SM) keep many rows in flight: the kernel is bound by the latency of its
+// dependent FMA chains, not by bandwidth.
 // ---------------------------------------------------------------------------------------
-constexpr int kT32Rows = 32;
+constexpr int kT32Rows = 16;
 constexpr int kT32Threads = 256;
+constexpr int kT32WLD = 132;   // row stride (floats) of W and of the staged rows (16-byte rows)
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
@@ -303,96 +303,77 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-constexpr int kT32WLD = 132;   // row stride of W in shared memory (16-byte rows)
-
 __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
                   const int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
-  float* Ws = reinterpret_cast<float*>(smem_raw);                 // Ws[k * 132 + j] = W(j, k)
-  double* Bd = reinterpret_cast<double*>(Ws + 128 * kT32WLD);      // Bd[k * 32 + r]
-  float* Bs = reinterpret_cast<float*>(Bd + 128 * kT32Rows);       // Bs[k * 32 + r]
+  float* Ws = reinterpret_cast<float*>(smem_raw);          // Ws[k * 132 + j] = W(j, k)
+  float* Bs = Ws + 128 * kT32WLD;                          // Bs[r * 132 + k] = B(row0 + r, k); later X
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kT32Rows;
-  // all copies in flight at once: W rows (512 B each, 16-byte pieces) and the B panel
-  // (8-byte pieces, rows past m read row m-1 and are never stored)
-  for (int e = tid; e < nc * 32; e += kT32Threads) {
-    const int k = e >> 5, q = e & 31;
-    cp_async16(Ws + k * kT32WLD + 4 * q, W + (size_t)k * ldw + 4 * q);
+  const bool vecw = (nc == 128) && ((ldw & 3) == 0) && ((reinterpret_cast<uintptr_t>(W) & 15) == 0);
+  if (vecw) {
+    for (int e = tid; e < 128 * 32; e += kT32Threads) {
+      const int k = e >> 5, q = e & 31;
+      cp_async16(Ws + k * kT32WLD + 4 * q, W + (size_t)k * ldw + 4 * q);
+    }
+  } else {
+    for (int e = tid; e < 128 * 128; e += kT32Threads) {
+      const int k = e >> 7, j = e & 127;
+      Ws[k * kT32WLD + j] = (j < nc && k < nc) ? W[(size_t)k * ldw + j] : 0.f;
+    }
   }
-  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
-    const int k = e >> 5, r = e & 31;
-    const int gr = min(row0 + r, m - 1);
-    cp_async8(Bd + k * kT32Rows + r, A + (size_t)(c0 + k) * ld + (r0 + gr));
+  // B: 8 values per thread, all loads in flight before the conversions
+  double bv[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = tid + kT32Threads * u;                   // e = k * 16 + r: 16 rows of column k
+    const int k = e >> 4, r = e & 15;
+    const int gr = row0 + r;
+    bv[u] = (k < nc && gr < m) ? __ldcg(A + (size_t)(c0 + k) * ld + (r0 + gr)) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = tid + kT32Threads * u;
+    Bs[(e & 15) * kT32WLD + (e >> 4)] = (float)bv[u];
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) Bs[e] = (float)Bd[e];
-  __syncthreads();
-  // thread: rows 8*tr .. 8*tr+7, columns 4*tc .. 4*tc+3 (8 x 4 register tile, float4 loads),
-  // half kh of the inner dimension; the two halves are added through shared memory
-  const int kh = tid >> 7, tt = tid & 127;
-  const int tr = tt & 3, tc = tt >> 2;
-  const bool active = 4 * tc < nc;
-  float acc[8][4];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-  const int khalf = (nc + 1) / 2;
-  const int kbeg = kh ? khalf : 0, kend = kh ? nc : khalf;
-  if (active) {
-    for (int k = kbeg; k < kend; ++k) {
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k * kT32Rows + 8 * tr + 4]);
-      const float4 w = *reinterpret_cast<const float4*>(&Ws[k * kT32WLD + 4 * tc]);
-      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-      const float ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bb[a], ww[c], acc[a][c]);
-    }
+  const int ra = 2 * warp, rb = 2 * warp + 1;
+  float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
+  const float* Ba = Bs + ra * kT32WLD;
+  const float* Bb = Bs + rb * kT32WLD;
+#pragma unroll 8
+  for (int k = 0; k < nc; ++k) {
+    const float4 w = *reinterpret_cast<const float4*>(Ws + k * kT32WLD + 4 * lane);
+    const float a = Ba[k], b = Bb[k];
+    xa[0] = fmaf(a, w.x, xa[0]);
+    xa[1] = fmaf(a, w.y, xa[1]);
+    xa[2] = fmaf(a, w.z, xa[2]);
+    xa[3] = fmaf(a, w.w, xa[3]);
+    xb[0] = fmaf(b, w.x, xb[0]);
+    xb[1] = fmaf(b, w.y, xb[1]);
+    xb[2] = fmaf(b, w.z, xb[2]);
+    xb[3] = fmaf(b, w.w, xb[3]);
   }
+  __syncthreads();                                         // all reads of B done: reuse Bs for X
+  *reinterpret_cast<float4*>(Bs + ra * kT32WLD + 4 * lane) = make_float4(xa[0], xa[1], xa[2], xa[3]);
+  *reinterpret_cast<float4*>(Bs + rb * kT32WLD + 4 * lane) = make_float4(xb[0], xb[1], xb[2], xb[3]);
   __syncthreads();
-  float* part = Ws;                                     // W no longer needed: reuse for the halves
-  if (kh == 1 && active) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) part[(8 * tr + a) * kT32WLD + 4 * tc + c] = acc[a][c];
+  // master (column-major): 16 consecutive rows of one column per half-warp
+  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
+    const int k = e >> 4, r = e & 15;
+    const int gr = row0 + r;
+    if (gr < m) A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[r * kT32WLD + k];
   }
-  __syncthreads();
-  if (kh == 0 && active) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] += part[(8 * tr + a) * kT32WLD + 4 * tc + c];
-  }
-  __syncthreads();
-  // stage X (float) back into Bs, then write master and shadow coalesced
-  if (kh == 0 && active) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = 4 * tc + c;
-      if (j < nc)
-#pragma unroll
-        for (int a = 0; a < 8; ++a) Bs[j * kT32Rows + 8 * tr + a] = acc[a][c];
-    }
-  }
-  __syncthreads();
-  {
-    const int gr = row0 + lane;
-    for (int k = warp; k < nc; k += kT32Threads / 32)
-      if (gr < m) A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[k * kT32Rows + lane];
-  }
+  // FP16 shadow (row-major): consecutive columns of one row
   if (S != nullptr) {
-    for (int idx = tid; idx < kT32Rows * nc; idx += kT32Threads) {
-      const int k = idx % nc, r = idx / nc;
+    for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
+      const int r = e / nc, k = e - r * nc;
       const int gr = row0 + r;
-      if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + k)] = __double2half((double)Bs[k * kT32Rows + r]);
+      if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + k)] = __float2half_rn(Bs[r * kT32WLD + k]);
     }
   }
 }
@@ -461,9 +442,8 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const float* W, int ldw, __half* shadow16, int lds,
                                const int* info, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
-  if (nc > 144) return cudaErrorInvalidValue;
   if (nc > 128) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)128 * kT32WLD * 4 + (size_t)128 * kT32Rows * 8 + (size_t)128 * kT32Rows * 4;
+  const size_t smem = (size_t)(128 + kT32Rows) * kT32WLD * 4;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(trsm_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
