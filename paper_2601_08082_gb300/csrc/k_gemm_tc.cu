@@ -116,7 +116,7 @@ struct TcLayout {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, BN <= 64 ? 2 : 1)
 gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                    double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
                    unsigned* __restrict__ err) {
@@ -277,6 +277,27 @@ cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int
   return cudaGetLastError();
 }
 
+// tiles of a BN-wide grid that hold work (tiles wholly above the diagonal are skipped)
+long long active_tiles(int m, int n, bool lower, int bn) {
+  const int gm = (m + TC_BM - 1) / TC_BM, gn = (n + bn - 1) / bn;
+  if (!lower) return (long long)gm * gn;
+  long long t = 0;
+  for (int j = 0; j < gn; ++j) {
+    const int first = (j * bn) / TC_BM;          // first M-tile reaching the diagonal of column tile j
+    t += gm - first;
+  }
+  return t;
+}
+
+int pick_bn(int m, int n, bool lower) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  if (n > 128 && active_tiles(m, n, lower, 256) >= sms) return 256;
+  if (n > 64 && active_tiles(m, n, lower, 128) >= sms) return 128;
+  if (n > 32 && active_tiles(m, n, lower, 64) >= sms) return 64;
+  return 32;
+}
+
 }  // namespace
 
 bool tc_gemm_supported() { return get_encode() != nullptr; }
@@ -285,8 +306,15 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int
                                int k, bool lower, double scale, unsigned* dev_err, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   if ((k0 % 8) != 0 || (lds % 8) != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0) return cudaErrorInvalidValue;
-  if (n <= 128) return launch_bn<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
-  return launch_bn<256>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+  // The FP64 read-modify-write of the epilogue runs on the SM's FP64 pipe and costs about
+  // as much as the tile's MMAs, so small products are cut into narrower tiles until they
+  // cover the SMs (tiles of 64 or 32 columns also fit two CTAs per SM, one CTA's epilogue
+  // then overlapping the other's MMAs).
+  const int bn = pick_bn(m, n, lower);
+  if (bn == 256) return launch_bn<256>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+  if (bn == 128) return launch_bn<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+  if (bn == 64) return launch_bn<64>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
+  return launch_bn<32>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
 }
 
 }  // namespace hrp
