@@ -7,7 +7,6 @@
 namespace hrp {
 namespace {
 
-constexpr int BM = 64, BN = 64;
 // inner-dimension slice per stage: 16 for FP64, 64 for FP32 accumulation (fewer
 // latency-bound stages for the small GEMMs of the FP32 levels)
 template <int RND> struct Slice { static constexpr int BK = 64; };
@@ -23,23 +22,25 @@ __device__ __forceinline__ typename Acc<RND>::T cvt_op(double x) {
   else return __half2float(__double2half(x));
 }
 
-// 256 threads; thread (tx, ty) = (tid % 16, tid / 16) owns rows tx + 16 i and columns ty + 16 j.
-template <int RND>
+// TL x TL tile (TL = 64 or 32), 256 threads; thread (tx, ty) = (tid % 16, tid / 16) owns
+// rows tx + 16 i and columns ty + 16 j, i, j < TL / 16.
+template <int RND, int TL>
 __global__ void __launch_bounds__(256)
 gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, int ldx,
                  const double* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
   using T = typename Acc<RND>::T;
   constexpr int BK = Slice<RND>::BK;
+  constexpr int BM = TL, BN = TL, R = TL / 16;
   __shared__ T Xs[BK][BM + 1];
   __shared__ T Ys[BK][BN + 1];
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (lower && m0 + BM - 1 < n0) return;          // tile strictly above the diagonal
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int j = 0; j < R; ++j) acc[i][j] = (T)0;
 
   // register prefetch of the next BK slice while the current one is multiplied
   T px[(BM * BK) / 256], py[(BN * BK) / 256];
@@ -65,31 +66,31 @@ gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, 
     if (k0 + BK < k) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = Xs[kk][tx + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = Xs[kk][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Ys[kk][ty + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Ys[kk][ty + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
-  double cv[4][4];
+  double cv[R][R];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < R; ++j)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       const int gc = n0 + ty + 16 * j, gr = m0 + tx + 16 * i;
       const bool ok = gc < n && gr < m && !(lower && gr < gc);
       cv[i][j] = ok ? C[(size_t)gc * ldc + gr] : 0.0;
     }
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < R; ++j)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
       const int gc = n0 + ty + 16 * j, gr = m0 + tx + 16 * i;
       const bool ok = gc < n && gr < m && !(lower && gr < gc);
       if (ok) C[(size_t)gc * ldc + gr] = cv[i][j] - (double)acc[i][j];
@@ -101,13 +102,22 @@ gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, 
 cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const double* Y, int ldy,
                              int m, int n, int k, OpRound rnd, bool lower, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-  dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
+  // 64 x 64 tiles unless that leaves most SMs idle: the operand rounding and the FP64
+  // read-modify-write of C run on the FP64 pipe, so the small products of the FP32 levels
+  // are spread over 32 x 32 tiles
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const bool small = (long long)((m + 63) / 64) * ((n + 63) / 64) < sms;
+  const int tl = small ? 32 : 64;
+  dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);
   if (grid.y > 65535) return cudaErrorInvalidValue;
+#define HRP_SIMT(R_, T_) gemm_simt_kernel<R_, T_><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower)
   switch (rnd) {
-    case OpRound::F64: gemm_simt_kernel<0><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
-    case OpRound::F32: gemm_simt_kernel<1><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
-    case OpRound::F16: gemm_simt_kernel<2><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower); break;
+    case OpRound::F64: if (small) HRP_SIMT(0, 32); else HRP_SIMT(0, 64); break;
+    case OpRound::F32: if (small) HRP_SIMT(1, 32); else HRP_SIMT(1, 64); break;
+    case OpRound::F16: if (small) HRP_SIMT(2, 32); else HRP_SIMT(2, 64); break;
   }
+#undef HRP_SIMT
   return cudaGetLastError();
 }
 
