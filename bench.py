@@ -34,6 +34,20 @@ LEAF = 128
 FP64_TREE, FP64_LEAF = "[F64]", 64
 METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated backward error"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (nominal); DFMA-bound kernels report against it
+# DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture
+# (profiles/potrf_leaf_cluster_n2048.md), reported while the kernel source is the one captured
+LEAF_TRAFFIC = {"bytes": 141312 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "sha1": "13416e11383d86225b40891113d38c68edc73602"}
+
+
+def leaf_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, LEAF_TRAFFIC["source"]), "rb") as f:
+            ok = hashlib.sha1(f.read()).hexdigest() == LEAF_TRAFFIC["sha1"]
+    except OSError:
+        ok = False
+    return LEAF_TRAFFIC["bytes"] if ok else None
 
 
 def peaks():
@@ -102,20 +116,33 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(n_s: int = 3072, rho: float = 2.0):
-    """Time the oracle (emulator of Alg. 1-3) on one n_s matrix of the same generator and tree."""
+def cpu_oracle_sample(n_s: int = 3072, rho: float = 2.0, mats=None, budget_s: float = 10.0):
+    """Time the oracle (emulator of Alg. 1-3) with the same tree: on `mats` (the workload's
+    own matrices, one after another until `budget_s` seconds of emulation have run), or on one
+    n_s matrix of the same generator."""
     from oracle import tree as otree
     from synth import dominant_spd, seed_for
-    A = dominant_spd(n_s, rho, seed_for(1, 900 + n_s))
     t = otree.parse(TREE, leaf=LEAF)
-    t0 = time.perf_counter()
-    _, info, _ = otree.emulate_potrf(A, t)
-    dt = time.perf_counter() - t0
-    assert info == 0
-    return {"value": n_s ** 3 / 3.0 / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"emulator of Alg. 1-3 (float64 numpy, tree {TREE}, leaf {LEAF}) on one n={n_s} "
-                      f"matrix of the same generator (rho={rho}); {dt:.2f} s",
-            "seconds": dt}
+    if mats is None:
+        mats = [dominant_spd(n_s, rho, seed_for(1, 900 + n_s))]
+        what = f"one n={n_s} matrix of the same generator (rho={rho})"
+    else:
+        what = None
+    done, secs, flops = 0, 0.0, 0.0
+    for A in mats:
+        t0 = time.perf_counter()
+        _, info, _ = otree.emulate_potrf(A, t)
+        secs += time.perf_counter() - t0
+        assert info == 0
+        done += 1
+        flops += A.shape[0] ** 3 / 3.0
+        if secs >= budget_s:
+            break
+    if what is None:
+        what = f"{done} of the workload's n={mats[0].shape[0]} matrices (rho {list(RHOS)[:done]})"
+    return {"value": flops / secs / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"emulator of Alg. 1-3 (float64 numpy, tree {TREE}, leaf {LEAF}) on {what}; {secs:.1f} s",
+            "seconds": secs}
 
 
 def run_reference(args, rank):
@@ -274,10 +301,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # oracle baseline first (rank 0 only, before any other GPU work matters)
+    # inputs: one matrix per rho, generated on the host (same bits as the oracle sees)
+    mats = [dominant_spd(N, rho, seed_for(1, 10 * rank + i)) for i, rho in enumerate(RHOS)]
+
+    # oracle baseline on the same matrices (rank 0 only, before the GPU work)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_oracle_sample()
+        cpu = cpu_oracle_sample(mats=mats)
         cpu.pop("seconds", None)
 
     h = hrp.Handle(local)
@@ -285,8 +315,6 @@ def main():
     tree64 = hrp.tree_parse(FP64_TREE, leaf=FP64_LEAF)
     stream = torch.cuda.current_stream()
 
-    # inputs: one matrix per rho, generated on the host (same bits as the oracle sees)
-    mats = [dominant_spd(N, rho, seed_for(1, 10 * rank + i)) for i, rho in enumerate(RHOS)]
     bvec = rhs(N, 1, seed_for(1, 100 + rank))
     A0 = [hrp.colmajor(A).cuda() for A in mats]
     nsteps = args.warmup + args.steps
@@ -364,7 +392,8 @@ def main():
         else:
             peak, bound, src = 69.0, "alu", "FP32 FFMA 69 TFLOP/s (152 SMs x 128 lanes x 2 x 1.77 GHz)"
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": name, "avg_launch_ms": avg_ms, "peak_src": src}
+                "traffic": leaf_traffic() if name == "leaf_potrf_fp64" else None, "kernel": name,
+                "avg_launch_ms": avg_ms, "peak_src": src}
 
     # FP64 tree on the same matrices (the comparison of the metric)
     fp64 = None
