@@ -64,10 +64,12 @@ struct ClusterLeafSmem {
 
 __device__ __forceinline__ int owner_of(int I, int J) { return (I + J) & (kCL - 1); }
 
-// (i, j) of entry e of a lower 16 x 16 triangle enumerated row by row
+// (i, j) of entry e < 136 of a lower 16 x 16 triangle enumerated row by row:
+// i = floor((sqrt(8e + 1) - 1) / 2), exact in single precision for these e (checked below)
 __device__ __forceinline__ void lower_entry(int e, int& i, int& j) {
-  i = 0;
-  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  i = (int)((sqrtf((float)(8 * e + 1)) - 1.0f) * 0.5f);
+  if ((i + 1) * (i + 2) / 2 <= e) ++i;              // guard against a rounding below an integer
+  if (i * (i + 1) / 2 > e) --i;
   j = e - i * (i + 1) / 2;
 }
 
@@ -122,20 +124,25 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
   C[i * kTLD + j0 + 1] = c1;
 }
 
-// C -= LI * LI^T on the lower triangle of a diagonal tile: the 136 entries are dealt to
-// the 128 threads (8 threads take two), so every warp issues about 16 FMAs.
+// C -= LI * LI^T on the lower triangle of a diagonal tile (136 entries x 16 terms), spread
+// evenly over the 128 threads: entry t (t < 128) is summed by thread t, and each of the last
+// 8 entries (row 15, columns 8..15) is split over the 16 threads of a half-warp, one term
+// each, and reduced by shuffles; every thread issues 17 FMAs.
 __device__ __forceinline__ void tile_update_diag(double* __restrict__ C, const double* __restrict__ LI, int tid) {
+  int i, j;
+  lower_entry(tid, i, j);
+  double c0 = 0.0, c1 = 0.0;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int e = tid + kCThreads * h;
-    if (e >= kLowT) break;
-    int i, j;
-    lower_entry(e, i, j);
-    double c = C[i * kTLD + j];
-#pragma unroll
-    for (int k = 0; k < kTS; ++k) c = fma(-LI[i * kTLD + k], LI[j * kTLD + k], c);
-    C[i * kTLD + j] = c;
+  for (int k = 0; k < kTS; k += 2) {
+    c0 = fma(LI[i * kTLD + k], LI[j * kTLD + k], c0);
+    c1 = fma(LI[i * kTLD + k + 1], LI[j * kTLD + k + 1], c1);
   }
+  const int jx = 8 + (tid >> 4), kx = tid & 15;            // entry (15, jx), term kx
+  double x = LI[15 * kTLD + kx] * LI[jx * kTLD + kx];
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  C[i * kTLD + j] -= c0 + c1;
+  if (kx == 0) C[15 * kTLD + jx] -= x;
 }
 
 // Cholesky of the 16 x 16 tile T (lower part, row-major kTLD) by the 128 threads.  The
