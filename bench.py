@@ -262,6 +262,87 @@ def run_batched(args, rank, world):
     return 0
 
 
+def run_fp8posv(args, rank, world):
+    """n = 32768, A = (B + B^T)/2 with B iid N(0,1) and A_ii = 2 sum_{j!=i} |A_ij|, tree
+    [F8,F16,F16,F32|F64@128] (E4M3 outermost off-diagonal level with one power-of-two scale per
+    128 x 128 tile, FP16 at the next two levels, FP32 diagonal regions, FP64 leaves of 128):
+    factorization rate, then hrp_posv with 16 right-hand sides refined to 1e-12.  The input
+    (8.6 GB) is drawn on the device from a seeded torch generator; the oracle is not run at
+    this size."""
+    import torch
+
+    import paper_2601_08082_gb300 as hrp
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n, nrhs, rho, spec = args.n3, 16, 2.0, "[F8,F16,F16,F32|F64@128]"
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2601008082 + 2000 + rank)
+    Bt = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    A = Bt + Bt.T
+    del Bt
+    A.mul_(0.5)
+    A.diagonal().zero_()
+    A.diagonal().copy_(rho * A.abs().sum(dim=1))
+    Bm = torch.randn((nrhs, n), generator=g, device="cuda", dtype=torch.float64)   # column-major n x nrhs
+    X = torch.zeros_like(Bm)
+    h = hrp.Handle(local)
+    tree = hrp.tree_parse(spec, leaf=128)
+    d_info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Af = torch.empty_like(A)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    tf = []
+    with Clocks(local) as clk:
+        for rep in range(args.warmup + args.steps):
+            Af.copy_(A)
+            _, t = timed(lambda: h.potrf_async(tree, Af, d_info, stream=stream))
+            if rep >= args.warmup:
+                tf.append(t)
+    info = int(d_info.item())
+    be = h.backward_error(A, Af)
+    tp = []
+    out = None
+    for rep in range(1 + max(1, args.steps // 2)):
+        out, t = timed(lambda: h.posv(tree, A, Bm, X, max_iter=30, tol=1e-12))
+        if rep >= 1:
+            tp.append(t)
+    fp64 = None
+    if args.fp64_steps > 0:
+        Af.copy_(A)
+        _, t64 = timed(lambda: h.potrf_async(hrp.tree_parse("[F64]", leaf=64), Af, d_info, stream=stream))
+        fp64 = {"ms": t64, "tflops": n ** 3 / 3.0 / (t64 * 1e-3) / 1e12, "tree": "[F64]", "leaf": 64}
+    ms = statistics.median(tf)
+    flops = n ** 3 / 3.0
+    line = {"metric": METRIC + " (n=32768 FP8 posv)", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "e4m3 (in f16 storage) / f16 (fp32 acc) / f32 / f64", "data": "synthetic (device generator)",
+            "config": {"workload": f"n={n} rho={rho} tree {spec}, factor; posv with {nrhs} RHS to 1e-12",
+                       "n": n, "tree": spec, "leaf": 128, "nrhs": nrhs,
+                       "l2": "inputs larger than L2 (8.6 GB matrix, fresh copy per step)"},
+            "info": info, "backward_error": be,
+            "posv": {"ms": statistics.median(tp), "status": out["status"], "iters": out["iters"],
+                     "resid": out["resid"], "used_fallback": out["used_fallback"],
+                     "tflops_incl_refinement": flops / (statistics.median(tp) * 1e-3) / 1e12},
+            "fp64_tree": fp64, "speedup_vs_fp64_tree": (fp64["ms"] / ms) if fp64 else None,
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,7 +352,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched"])
+    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768"])
+    ap.add_argument("--n3", type=int, default=32768, help="order of the fp8posv32768 workload")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-tree", default="[F16,F32|F64@128]")
     args = ap.parse_args()
@@ -283,6 +365,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batched":
         return run_batched(args, rank, world)
+    if args.workload == "fp8posv32768":
+        return run_fp8posv(args, rank, world)
 
     import numpy as np
     import torch
