@@ -40,6 +40,8 @@ constexpr int kMaxOwn = 5;              // tiles per CTA for 8 x 8 tiles owned b
 constexpr int kCThreads = 128;
 constexpr int kLowT = kTS * (kTS + 1) / 2;   // entries of a lower 16 x 16 triangle
 constexpr int kMaxGather = 36;               // W phase: tiles one CTA reads (28 of L, 8 inverses)
+constexpr int kChainWarps = 3;               // worker warps of the 16 x 16 pivot chain
+constexpr int kChainSeg = 2;                 // entries of one row per worker thread
 
 struct ClusterLeafSmem {
   double own[kMaxOwn][kTileD];          // owned tiles, row-major (row i at i * kTLD)
@@ -149,59 +151,65 @@ __device__ __forceinline__ void tile_update_diag(double* __restrict__ C, const d
 // column recurrence runs alone on thread 0 (warp 0, sub-partition 0):
 //   d_{k+1} = d'_{k+1} - u_{k+1} s_k,  s_k = 1/d_k,
 // with d'_{k+1} = a_{k+1,k+1} and u_{k+1} = a_{k+1,k}^2 after the updates of columns < k.
-// Warps 1 and 2 apply the update of column k, a_ij -= (a_ik s_k) a_jk for i >= j > k, one
-// step behind and publish what the next steps read; each of their threads holds up to
-// three consecutive entries of one row, so a warp issues at most five FP64 instructions
-// per column and the two of them stay below the SM's FP64 issue limit that would slow
-// the recurrence.  One CTA barrier per column.  At the end l_jj = d_j r_j and
-// l_ij = a_ij r_j (a_ij after the updates of columns < j), r_j = d_j^{-1/2}, also stored in
-// sm.rinv.  Returns the 0-based column of the first pivot that is not positive and
-// finite, or -1 (the same in every thread).
-__device__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+// NW worker warps (1 .. NW) apply the update of column k, a_ij -= (a_ik s_k) a_jk for
+// i >= j > k, one step behind, and publish what the next steps read; each worker thread holds
+// up to SEG consecutive entries of one row (one multiply per row and column, then one FMA
+// per entry).  One CTA barrier per column; it also carries the recurrence's failure flag
+// (__syncthreads_or).  At the end l_jj = d_j r_j and l_ij = a_ij r_j (a_ij after the updates
+// of columns < j), r_j = d_j^{-1/2}, also stored in sm.rinv.  Returns the 0-based column of
+// the first pivot that is not positive and finite, or -1 (the same in every thread).
+template <int NW, int SEG>
+__device__ int potrf16_chain_t(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
   const int warp = tid >> 5;
   int wi = -1, wj0 = 0, wcnt = 0;
-  double a[3] = {0.0, 0.0, 0.0};
-  if (warp == 1 || warp == 2) {
+  double a[SEG];
+#pragma unroll
+  for (int q = 0; q < SEG; ++q) a[q] = 0.0;
+  int fail = 0;                                   // thread 0: the recurrence met a bad pivot
+  if (warp >= 1 && warp <= NW) {
     const int w = tid - 32;
-    for (int i = 0, idx = 0; i < kTS; ++i) {       // row i has ceil((i + 1) / 3) segments
-      const int ns = (i + 3) / 3;
+    for (int i = 0, idx = 0; i < kTS; ++i) {       // row i has ceil((i + 1) / SEG) segments
+      const int ns = (i + SEG) / SEG;
       if (wi < 0 && w < idx + ns) {
         wi = i;
-        wj0 = 3 * (w - idx);
-        wcnt = min(3, i + 1 - wj0);
+        wj0 = SEG * (w - idx);
+        wcnt = min(SEG, i + 1 - wj0);
       }
       idx += ns;
     }
     if (wi >= 0) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
+      for (int q = 0; q < SEG; ++q)
         if (q < wcnt) a[q] = T[wi * kTLD + wj0 + q];
       if (wj0 == 0) sm.cv[0][wi] = a[0];
       if (wi == 1) {
-        sm.dpr[1] = a[1];
+        sm.dpr[1] = a[1];                          // row 1: one segment holding columns 0, 1
         sm.usq[1] = a[0] * a[0];
       }
     }
   } else if (tid == 0) {
     const double d0 = T[0];
     const int c = pivot_class(d0);
+    fail = c ? 0 : 1;
     sm.cfail = c ? -1 : 0;
     sm.dk[0] = d0;
     sm.sk[0] = (c == 2) ? recip_third_order(d0) : 1.0 / d0;
   }
-  __syncthreads();
-  int bad = sm.cfail;
-  for (int k = 0; k + 1 < kTS && bad < 0; ++k) {
+  int bad = __syncthreads_or(fail);
+  for (int k = 0; k + 1 < kTS && !bad; ++k) {
     if (tid == 0) {
       const double d = fma(-sm.usq[k + 1], sm.sk[k], sm.dpr[k + 1]);
       const int c = pivot_class(d);
-      if (!c) sm.cfail = k + 1;
+      if (!c) {
+        sm.cfail = k + 1;
+        fail = 1;
+      }
       sm.dk[k + 1] = d;
       sm.sk[k + 1] = (c == 2) ? recip_third_order(d) : 1.0 / d;
     } else if (wi > k && wj0 + wcnt - 1 > k) {
       const double t = sm.cv[k][wi] * sm.sk[k];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < SEG; ++q) {
         const int j = wj0 + q;
         if (q < wcnt && j > k) {
           a[q] = fma(-t, sm.cv[k][j], a[q]);
@@ -213,10 +221,9 @@ __device__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int ti
         }
       }
     }
-    __syncthreads();
-    bad = sm.cfail;
+    bad = __syncthreads_or(fail);
   }
-  if (bad >= 0) return bad;
+  if (bad) return sm.cfail;
   if (tid < kTS) sm.rinv[tid] = rsqrt_third_order(sm.dk[tid]);
   __syncthreads();
 #pragma unroll
@@ -228,6 +235,10 @@ __device__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int ti
     T[i * kTLD + j] = (i == j ? sm.dk[j] : sm.cv[j][i]) * sm.rinv[j];
   }
   return -1;
+}
+
+__device__ __forceinline__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+  return potrf16_chain_t<kChainWarps, kChainSeg>(T, sm, tid);
 }
 
 // X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
