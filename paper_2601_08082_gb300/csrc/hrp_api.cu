@@ -242,6 +242,15 @@ struct Fact {
   static constexpr int kG = 8;   // storage upshift: entries are 2^8 s e4m3(x/s)
   void quant8(int r0, int m, int c0, int nc) {
     if (!shadow8) return;
+    // only panels some F8-level GEMM reads: the left half (L11 and A21 columns) of the nodes
+    // at an F8 depth (F8 trees have n = 128 * 2^k, so node starts are multiples of the order)
+    bool needed = false;
+    for (int d = 0; d < t->depth && !needed; ++d)
+      if (t->level[d] == HRP_F8E4M3) {
+        const int N = n >> d;
+        needed = N >= 256 && (c0 % N) < N / 2;
+      }
+    if (!needed) return;
     begin(CLS_OTHER, 0.0);
     chk(launch_quant_e4m3(A, lda, r0, m, c0, nc, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
   }

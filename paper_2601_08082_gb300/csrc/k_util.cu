@@ -262,34 +262,72 @@ cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int
 namespace hrp {
 namespace {
 
-__device__ __forceinline__ double e4m3_rne(double y) {
-  // y = x / s with |y| <= 448 by construction of s
-  const double ay = fabs(y);
-  if (ay == 0.0) return 0.0;
-  int ex;
-  frexp(ay, &ex);                       // ay = f * 2^ex, f in [0.5, 1)
-  int e = ex - 1;
-  if (e < -6) e = -6;                   // subnormal binade
-  const double q = ldexp(1.0, e - 3);   // spacing of E4M3 values in this binade
-  double r = rint(ay / q) * q;          // exact division by a power of two; rint: ties to even
-  if (r > 448.0) r = 448.0;
-  return copysign(r, y);
+// FP16 bit pattern of 2^(sig + G) e4m3(x 2^-sig), e4m3 = round to nearest even onto the E4M3
+// grid (3 mantissa bits, normal exponents -6 .. 8, subnormal spacing 2^-9, saturating at
+// 448), computed by integer operations on the bits of x (this GPU runs FP64 arithmetic and
+// FP64 conversions on its slow FP64 pipe).  |x 2^-sig| <= 448 and the product's
+// representability in FP16 are guaranteed by the caller's choice of sig and range check.
+__device__ __forceinline__ unsigned short quant_e4m3_h(double x, int sig, int G) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63) << 15;
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return (unsigned short)sign;                   // zero or FP64 subnormal: rounds to 0
+  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+  const int ey = E - 1023 - sig;                             // binade of y = x 2^-sig
+  // y = r * 2^qe on the E4M3 grid of y's binade: spacing 2^(ey-3) (normal) or 2^-9 (subnormal)
+  int qe = ey >= -6 ? ey - 3 : -9;
+  const int sh = 52 - (ey - qe);                             // y / spacing = M >> sh (before rounding)
+  unsigned r = 0;
+  if (sh <= 54) {
+    r = (unsigned)(M >> sh);
+    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    r += (rem > half) || (rem == half && (r & 1u));
+  }
+  if (r == 0) return (unsigned short)sign;
+  if (ey > 8 || (ey == 8 && r > 14u)) {                      // saturate at 448 = 14 * 2^5
+    r = 14u;
+    qe = 5;
+  }
+  // value = r 2^e2 with 1 <= r <= 16, exact in FP16 (normal or subnormal): bits by integer ops
+  const int e2 = qe + sig + G;
+  const int pw = 31 - __clz((int)r);                         // r = 1.f 2^pw
+  const int be = pw + e2 + 15;                               // FP16 biased exponent
+  unsigned h;
+  if (be >= 1) h = ((unsigned)be << 10) | ((r - (1u << pw)) << (10 - pw));
+  else h = r << (e2 + 24);                                   // subnormal: units of 2^-24
+  return (unsigned short)(h | sign);
 }
 
+constexpr int kQLD = 129;   // row stride (doubles) of the staged 128 x 128 tile
+
+// One CTA per 128 x 128 tile of the panel: the tile is read once from the master
+// (coalesced along rows) into shared memory, its amax gives the power-of-two scale
+// s = 2^sig = 2^ceil(log2(amax / 448)), and the FP16 shadow is written row by row (coalesced
+// along columns).
 __global__ void __launch_bounds__(256)
 quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, int nc, __half* __restrict__ S8,
                   int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  extern __shared__ double tileq[];                  // [128][kQLD]
   __shared__ double red[8];
   const int tr = blockIdx.x;                       // row tile within the panel
   const int R0 = r0 + tr * 128;
   const int rows = min(128, r0 + m - R0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double amax = 0.0;
+  // amax over finite entries, as the largest |x| bit pattern (non-negative doubles order like
+  // their bits)
+  unsigned long long abits = 0;
   for (int idx = tid; idx < 128 * nc; idx += 256) {
     const int i = idx & 127, j = idx >> 7;
-    if (i < rows) amax = fmax(amax, fabs(A[(size_t)(c0 + j) * ld + R0 + i]));
+    const double x = i < rows ? A[(size_t)(c0 + j) * ld + R0 + i] : 0.0;
+    tileq[i * kQLD + j] = x;
+    const unsigned long long v = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    if (v < 0x7ff0000000000000ull && v > abits) abits = v;
   }
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, abits, o);
+    if (w > abits) abits = w;
+  }
+  double amax = __longlong_as_double((long long)abits);
   if (lane == 0) red[warp] = amax;
   __syncthreads();
   if (tid == 0) {
@@ -310,14 +348,9 @@ quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, i
     const bool fits = !(amax > 0.0) || (ldexp(amax, G) <= 65504.0 && sig - 9 + G >= -24);
     if (!fits || !isfinite(amax)) atomicOr(err, DEV_ERR_RANGE);
   }
-  const double inv_s = ldexp(1.0, -sig);
   for (int idx = tid; idx < 128 * nc; idx += 256) {
     const int j = idx & (nc - 1), i = idx / nc;    // consecutive threads: consecutive columns
-    if (i < rows) {
-      const double x = A[(size_t)(c0 + j) * ld + R0 + i];
-      const double q = ldexp(e4m3_rne(x * inv_s), sig + G);
-      S8[(size_t)(R0 + i) * lds + c0 + j] = __double2half(q);
-    }
+    if (i < rows) S8[(size_t)(R0 + i) * lds + c0 + j] = __ushort_as_half(quant_e4m3_h(tileq[i * kQLD + j], sig, G));
   }
 }
 
@@ -327,7 +360,14 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
                               int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if ((r0 % 128) || (c0 % 128) || nc != 128) return cudaErrorInvalidValue;
-  quant_e4m3_kernel<<<(m + 127) / 128, 256, 0, s>>>(A, ld, r0, m, c0, nc, S8, lds, tile_exp, ntile_ld, G, err);
+  const size_t smem = (size_t)128 * kQLD * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(quant_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  quant_e4m3_kernel<<<(m + 127) / 128, 256, smem, s>>>(A, ld, r0, m, c0, nc, S8, lds, tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ def main() -> int:
     ap.add_argument("--leaf", type=int, default=128)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=0, help="also solve with this many right-hand sides")
+    ap.add_argument("--device-gen", action="store_true",
+                    help="draw the matrix on the device (seeded torch generator) instead of the host generator")
     ap.add_argument("--timing", action="store_true",
                     help="print per-kernel-class device time of the last factorization (event timing mode)")
     args = ap.parse_args()
@@ -33,7 +35,17 @@ def main() -> int:
     from . import hrp
 
     h = hrp.Handle(0)
-    A0 = hrp.colmajor(dominant_spd(args.n, args.rho, seed_for(1, 0))).cuda()
+    if args.device_gen:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed_for(1, 0))
+        Bt = torch.randn((args.n, args.n), generator=g, device="cuda", dtype=torch.float64)
+        A0 = Bt + Bt.T
+        del Bt
+        A0.mul_(0.5)
+        A0.diagonal().zero_()
+        A0.diagonal().copy_(args.rho * A0.abs().sum(dim=1))
+    else:
+        A0 = hrp.colmajor(dominant_spd(args.n, args.rho, seed_for(1, 0))).cuda()
     B0 = hrp.colmajor(rhs(args.n, args.nrhs, seed_for(1, 1))).cuda() if args.nrhs else None
     tree = hrp.tree_parse(args.tree, leaf=args.leaf)
     for _ in range(args.reps):
