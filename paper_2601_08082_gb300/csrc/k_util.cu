@@ -264,31 +264,37 @@ namespace {
 
 // FP16 bit pattern of 2^(sig + G) e4m3(x 2^-sig), e4m3 = round to nearest even onto the E4M3
 // grid (3 mantissa bits, normal exponents -6 .. 8, subnormal spacing 2^-9, saturating at
-// 448), computed by integer operations on the bits of x (this GPU runs FP64 arithmetic and
-// FP64 conversions on its slow FP64 pipe).  |x 2^-sig| <= 448 and the product's
-// representability in FP16 are guaranteed by the caller's choice of sig and range check.
+// 448), by 32-bit integer operations on the bits of x (this GPU runs FP64 arithmetic and FP64
+// conversions on its slow FP64 pipe).  |x 2^-sig| <= 448 and the product's representability
+// in FP16 are guaranteed by the caller's choice of sig and range check.
 __device__ __forceinline__ unsigned short quant_e4m3_h(double x, int sig, int G) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 63) << 15;
-  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = (hi >> 31) << 15;
+  const int E = (int)((hi >> 20) & 0x7ff);
   if (E == 0) return (unsigned short)sign;                   // zero or FP64 subnormal: rounds to 0
-  const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
-  const int ey = E - 1023 - sig;                             // binade of y = x 2^-sig
-  // y = r * 2^qe on the E4M3 grid of y's binade: spacing 2^(ey-3) (normal) or 2^-9 (subnormal)
-  int qe = ey >= -6 ? ey - 3 : -9;
-  const int sh = 52 - (ey - qe);                             // y / spacing = M >> sh (before rounding)
-  unsigned r = 0;
-  if (sh <= 54) {
-    r = (unsigned)(M >> sh);
-    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    r += (rem > half) || (rem == half && (r & 1u));
+  if (E == 0x7ff) {                                          // NaN stays NaN; infinity saturates
+    if ((hi & 0xfffffu) | lo) return (unsigned short)(sign | 0x7e00u);
+    const int ef = 5 + sig + G + 15;                         // 448 = 1.75 * 2^8 -> 14 * 2^5
+    return (unsigned short)(sign | ((unsigned)(ef + 3) << 10) | (3u << 8));
   }
+  const unsigned S = (hi & 0xfffffu) | 0x100000u;            // top 21 bits of the 53-bit significand
+  const int ey = E - 1023 - sig;                             // binade of y = x 2^-sig
+  // y / spacing = significand >> sh, spacing 2^(ey-3) (normal) or 2^-9 (subnormal); sh in [49, 54]
+  int qe = ey >= -6 ? ey - 3 : -9;
+  const int sh = 52 - (ey - qe);
+  if (sh > 54) return (unsigned short)sign;                  // below half the smallest E4M3 step
+  const int s32 = sh - 32;                                   // 17 .. 22: shift within S
+  unsigned r = S >> s32;
+  const unsigned halfbit = (S >> (s32 - 1)) & 1u;
+  const unsigned sticky = (S & ((1u << (s32 - 1)) - 1u)) | lo;
+  r += halfbit & ((sticky != 0u) | (r & 1u));
   if (r == 0) return (unsigned short)sign;
   if (ey > 8 || (ey == 8 && r > 14u)) {                      // saturate at 448 = 14 * 2^5
     r = 14u;
     qe = 5;
   }
-  // value = r 2^e2 with 1 <= r <= 16, exact in FP16 (normal or subnormal): bits by integer ops
+  // value = r 2^e2 with 1 <= r <= 16, exact in FP16 (normal or subnormal)
   const int e2 = qe + sig + G;
   const int pw = 31 - __clz((int)r);                         // r = 1.f 2^pw
   const int be = pw + e2 + 15;                               // FP16 biased exponent
@@ -298,26 +304,30 @@ __device__ __forceinline__ unsigned short quant_e4m3_h(double x, int sig, int G)
   return (unsigned short)(h | sign);
 }
 
-constexpr int kQLD = 129;   // row stride (doubles) of the staged 128 x 128 tile
+constexpr int kQT = 128;     // tile edge (rows and columns)
+constexpr int kQLD = 129;    // row stride (doubles) of the staged tile
+constexpr int kQThreads = 1024;
 
 // One CTA per 128 x 128 tile of the panel: the tile is read once from the master
 // (coalesced along rows) into shared memory, its amax gives the power-of-two scale
 // s = 2^sig = 2^ceil(log2(amax / 448)), and the FP16 shadow is written row by row (coalesced
 // along columns).
-__global__ void __launch_bounds__(256)
-quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, int nc, __half* __restrict__ S8,
+__global__ void __launch_bounds__(kQThreads)
+quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, __half* __restrict__ S8,
                   int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
   extern __shared__ double tileq[];                  // [128][kQLD]
-  __shared__ double red[8];
+  __shared__ unsigned long long red[kQThreads / 32];
+  __shared__ int s_sig;
   const int tr = blockIdx.x;                       // row tile within the panel
-  const int R0 = r0 + tr * 128;
-  const int rows = min(128, r0 + m - R0);
+  const int R0 = r0 + tr * kQT;
+  const int rows = min(kQT, r0 + m - R0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // amax over finite entries, as the largest |x| bit pattern (non-negative doubles order like
   // their bits)
   unsigned long long abits = 0;
-  for (int idx = tid; idx < 128 * nc; idx += 256) {
-    const int i = idx & 127, j = idx >> 7;
+#pragma unroll 4
+  for (int idx = tid; idx < kQT * kQT; idx += kQThreads) {
+    const int i = idx & (kQT - 1), j = idx >> 7;
     const double x = i < rows ? A[(size_t)(c0 + j) * ld + R0 + i] : 0.0;
     tileq[i * kQLD + j] = x;
     const unsigned long long v = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
@@ -327,29 +337,28 @@ quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, i
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, abits, o);
     if (w > abits) abits = w;
   }
-  double amax = __longlong_as_double((long long)abits);
-  if (lane == 0) red[warp] = amax;
+  if (lane == 0) red[warp] = abits;
   __syncthreads();
   if (tid == 0) {
-    double a = 0.0;
-    for (int w = 0; w < 8; ++w) a = fmax(a, red[w]);
-    red[0] = a;
-  }
-  __syncthreads();
-  amax = red[0];
-  int sig = 0;                                     // s = 2^sig
-  if (amax > 0.0 && isfinite(amax)) {
-    int ex;
-    const double f = frexp(amax / 448.0, &ex);     // amax / 448 = f * 2^ex
-    sig = (f == 0.5) ? ex - 1 : ex;                // ceil(log2(amax / 448))
-  }
-  if (tid == 0) {
-    tile_exp[(size_t)(R0 / 128) * ntile_ld + c0 / 128] = sig;
+    unsigned long long a = 0;
+    for (int w = 0; w < kQThreads / 32; ++w) a = red[w] > a ? red[w] : a;
+    const double amax = __longlong_as_double((long long)a);
+    int sig = 0;                                   // s = 2^sig
+    if (amax > 0.0) {
+      int ex;
+      const double f = frexp(amax / 448.0, &ex);   // amax / 448 = f * 2^ex
+      sig = (f == 0.5) ? ex - 1 : ex;              // ceil(log2(amax / 448))
+    }
+    tile_exp[(size_t)(R0 / kQT) * ntile_ld + c0 / kQT] = sig;
     const bool fits = !(amax > 0.0) || (ldexp(amax, G) <= 65504.0 && sig - 9 + G >= -24);
-    if (!fits || !isfinite(amax)) atomicOr(err, DEV_ERR_RANGE);
+    if (!fits) atomicOr(err, DEV_ERR_RANGE);
+    s_sig = sig;
   }
-  for (int idx = tid; idx < 128 * nc; idx += 256) {
-    const int j = idx & (nc - 1), i = idx / nc;    // consecutive threads: consecutive columns
+  __syncthreads();
+  const int sig = s_sig;
+#pragma unroll 4
+  for (int idx = tid; idx < kQT * kQT; idx += kQThreads) {
+    const int j = idx & (kQT - 1), i = idx >> 7;   // consecutive threads: consecutive columns
     if (i < rows) S8[(size_t)(R0 + i) * lds + c0 + j] = __ushort_as_half(quant_e4m3_h(tileq[i * kQLD + j], sig, G));
   }
 }
@@ -367,7 +376,7 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  quant_e4m3_kernel<<<(m + 127) / 128, 256, smem, s>>>(A, ld, r0, m, c0, nc, S8, lds, tile_exp, ntile_ld, G, err);
+  quant_e4m3_kernel<<<(m + 127) / 128, kQThreads, smem, s>>>(A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
 }
 
