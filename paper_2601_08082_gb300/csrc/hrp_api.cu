@@ -44,6 +44,8 @@ struct hrp_handle_s {
   size_t w32_cap = 0;          // elements
   __half* shadow8 = nullptr;   // E4M3 values (times 2^G, exact) in FP16 storage
   size_t shadow8_cap = 0;
+  float* shadow32 = nullptr;   // FP32 copy of L (column-major, ld n) for the FP32-level GEMMs
+  size_t shadow32_cap = 0;
   int* tile_exp = nullptr;     // power-of-two scale exponent of every 128 x 128 tile
   size_t tile_exp_cap = 0;
   double* fact = nullptr;      // posv factor copy
@@ -165,6 +167,8 @@ struct Fact {
   float* w32;           // null if every level is F64
   __half* shadow8;      // null if no F8 level
   int* tile_exp;
+  float* shadow32;      // null: FP32-level GEMMs round their operands from the master
+  int ld32;
   bool tc;
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
   cudaError_t err = cudaSuccess;
@@ -225,15 +229,16 @@ struct Fact {
     __half* sh = shadow;
     begin(CLS_TRSM, (double)m * nc * nc);
     if (p == HRP_F64 || t->trsm_compute == 1) {
-      chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
+      chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
       quant8(r0, m, c0, nc);
       return;
     }
     auto it = leaves.find(c0);
     if (w32 && it != leaves.end() && it->second == nc) {
-      chk(launch_trsm_leaf32(Ab, lda, r0, m, c0, nc, w32 + (size_t)c0 * 128, 128, sh, lds, info, s));
+      chk(launch_trsm_leaf32(Ab, lda, r0, m, c0, nc, w32 + (size_t)c0 * 128, 128, sh, lds, shadow32, ld32, info,
+                             s));
     } else {
-      chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, info, s));
+      chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
     }
     quant8(r0, m, c0, nc);
   }
@@ -266,7 +271,15 @@ struct Fact {
     begin(use_tc ? CLS_GEMM_TC : CLS_GEMM_SIMT, fl);
     switch (p) {
       case HRP_F64: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F64, lower, s)); break;
-      case HRP_F32: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F32, lower, s)); break;
+      case HRP_F32:
+        // every FP32-level operand is an off-diagonal block of L, finished by a leaf TRSM that
+        // also wrote its FP32 rounding into the shadow
+        if (shadow32)
+          chk(launch_gemm_simt_f32(C, lda, shadow32 + (size_t)k0 * ld32 + r0, ld32, shadow32 + (size_t)k0 * ld32 + c0,
+                                   ld32, m, nd, k, lower, s));
+        else
+          chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F32, lower, s));
+        break;
       case HRP_F16:
         if (use_tc)
           chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s));
@@ -371,6 +384,12 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
     if ((st = ensure(h, &h->w32, &h->w32_cap, (size_t)n * 128 + 128 * 128)) != HRP_OK) return st;
     f.w32 = h->w32;
   }
+  f.shadow32 = nullptr;
+  f.ld32 = n;
+  if (tree_has(t, HRP_F32) && n > 0) {
+    if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)n * n)) != HRP_OK) return st;
+    f.shadow32 = h->shadow32;
+  }
   f.begin(CLS_OTHER, 0.0);
   f.chk(launch_fill_int(d_info, INT_MAX, 1, s));
   f.potrf(0, n, 0);
@@ -458,6 +477,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->shadow);
   cudaFree(h->w32);
   cudaFree(h->shadow8);
+  cudaFree(h->shadow32);
   cudaFree(h->tile_exp);
   cudaFree(h->fact);
   cudaFree(h->work);

@@ -38,17 +38,19 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
                                       cudaStream_t s);
 
 // Leaf TRSM B <- B L^{-T} with B = A[r0.., c0..] (m x nc) and L = A[c0.., c0..] (nc x nc),
-// in FP64 by substitution.  shadow16 (row-major, lds) receives FP16(X) if non-null.
+// in FP64 by substitution.  shadow16 (row-major, lds) receives FP16(X) and shadow32
+// (column-major, ld32, the master's indexing) FP32(X), each if non-null.
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
-                               __half* shadow16, int lds, const int* info, cudaStream_t s);
+                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, cudaStream_t s);
 // Same in FP32 using the precomputed FP32 inverse W (nc x nc lower, ldw) of the block:
 // X = fl32(B) * W^T, result stored in FP64.
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
-                               const float* W, int ldw, __half* shadow16, int lds,
+                               const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
                                const int* info, cudaStream_t s);
 // FP32 substitution variant (no inverse), for blocks whose inverse is not available.
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
-                                     __half* shadow16, int lds, const int* info, cudaStream_t s);
+                                     __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
+                                     cudaStream_t s);
 
 // ---------------- SIMT GEMM (k_gemm_simt.cu) ----------------
 // C[m x n] -= X[m x k] * Y[n x k]^T, all FP64 column-major views of the master, with
@@ -56,6 +58,10 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
 // diagonal block, only entries with row >= col (in C's coordinates) are updated.
 cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const double* Y, int ldy,
                              int m, int n, int k, OpRound rnd, bool lower, cudaStream_t s);
+// FP32 level with operands read from the FP32 shadow of L (column-major views, no rounding
+// on load): C -= X Y^T accumulated in FP32.
+cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, const float* Y, int ldy,
+                                 int m, int n, int k, bool lower, cudaStream_t s);
 
 // ---------------- tcgen05 FP16 GEMM (k_gemm_tc.cu) ----------------
 // C[m x n] (FP64 master, column-major) -= scale * X Y^T with X = S[xr0.., k0..] (m x k) and

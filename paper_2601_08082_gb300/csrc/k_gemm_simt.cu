@@ -21,13 +21,16 @@ __device__ __forceinline__ typename Acc<RND>::T cvt_op(double x) {
   else if constexpr (RND == 1) return __double2float_rn(x);
   else return __half2float(__double2half(x));
 }
+// operands already in FP32 (the FP32 shadow of L): no rounding on load
+template <int RND>
+__device__ __forceinline__ float cvt_op(float x) { return x; }
 
 // TL x TL tile (TL = 64 or 32), 256 threads; thread (tx, ty) = (tid % 16, tid / 16) owns
 // rows tx + 16 i and columns ty + 16 j, i, j < TL / 16.
-template <int RND, int TL>
+template <int RND, int TL, typename TIN = double>
 __global__ void __launch_bounds__(256)
-gemm_simt_kernel(double* __restrict__ C, int ldc, const double* __restrict__ X, int ldx,
-                 const double* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
+gemm_simt_kernel(double* __restrict__ C, int ldc, const TIN* __restrict__ X, int ldx,
+                 const TIN* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
   using T = typename Acc<RND>::T;
   constexpr int BK = Slice<RND>::BK;
   constexpr int BM = TL, BN = TL, R = TL / 16;
@@ -118,6 +121,22 @@ cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const
     case OpRound::F16: if (small) HRP_SIMT(2, 32); else HRP_SIMT(2, 64); break;
   }
 #undef HRP_SIMT
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, const float* Y, int ldy,
+                                 int m, int n, int k, bool lower, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const bool small = (long long)((m + 63) / 64) * ((n + 63) / 64) < sms;
+  const int tl = small ? 32 : 64;
+  dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (small)
+    gemm_simt_kernel<1, 32, float><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
+  else
+    gemm_simt_kernel<1, 64, float><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
   return cudaGetLastError();
 }
 

@@ -234,7 +234,8 @@ potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
 template <typename T>
 __global__ void __launch_bounds__(64)
 trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
-                  __half* __restrict__ S, int lds, const int* __restrict__ info, int rows_per_cta) {
+                  __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32, const int* __restrict__ info,
+                  int rows_per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
   T* Ls = reinterpret_cast<T*>(smem_raw);              // row-major nc x nc: Ls[j * nc + k]
@@ -271,7 +272,10 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   for (int idx = tid; idx < RT * nc; idx += blockDim.x) {
     int t = idx % RT, k = idx / RT;
     int r = row0 + t;
-    if (r < m) A[(size_t)(c0 + k) * ld + (r0 + r)] = (double)Xs[k * RT + t];
+    if (r < m) {
+      A[(size_t)(c0 + k) * ld + (r0 + r)] = (double)Xs[k * RT + t];
+      if (S32 != nullptr) S32[(size_t)(c0 + k) * ld32 + (r0 + r)] = (float)Xs[k * RT + t];
+    }
   }
   if (S != nullptr) {
     for (int idx = tid; idx < RT * nc; idx += blockDim.x) {
@@ -306,7 +310,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
-                  const int* __restrict__ info) {
+                  float* __restrict__ S32, int ld32, const int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
   float* Ws = reinterpret_cast<float*>(smem_raw);          // Ws[k * 132 + j] = W(j, k)
@@ -366,7 +370,10 @@ trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
     const int k = e >> 4, r = e & 15;
     const int gr = row0 + r;
-    if (gr < m) A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[r * kT32WLD + k];
+    if (gr < m) {
+      A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[r * kT32WLD + k];
+      if (S32 != nullptr) S32[(size_t)(c0 + k) * ld32 + (r0 + gr)] = Bs[r * kT32WLD + k];
+    }
   }
   // FP16 shadow (row-major): consecutive columns of one row
   if (S != nullptr) {
@@ -403,7 +410,7 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
 }
 
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
-                               __half* shadow16, int lds, const int* info, cudaStream_t s) {
+                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = nc <= 128 ? 64 : 32;
@@ -416,12 +423,13 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
     attr_done = true;
   }
   int grid = (m + RT - 1) / RT;
-  trsm_subst_kernel<double><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, info, RT);
+  trsm_subst_kernel<double><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
-                                     __half* shadow16, int lds, const int* info, cudaStream_t s) {
+                                     __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
+                                     cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = 64;
@@ -434,12 +442,12 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
     attr_done = true;
   }
   int grid = (m + RT - 1) / RT;
-  trsm_subst_kernel<float><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, info, RT);
+  trsm_subst_kernel<float><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
-                               const float* W, int ldw, __half* shadow16, int lds,
+                               const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
                                const int* info, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 128) return cudaErrorInvalidValue;
@@ -451,7 +459,8 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
     attr_done = true;
   }
   int grid = (m + kT32Rows - 1) / kT32Rows;
-  trsm_inv32_kernel<<<grid, kT32Threads, smem, s>>>(A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, info);
+  trsm_inv32_kernel<<<grid, kT32Threads, smem, s>>>(A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
+                                                     info);
   return cudaGetLastError();
 }
 
