@@ -2,6 +2,8 @@
 // C -= X Y^T on column-major views of the FP64 master.  This is the update
 // "B2 <- B2 - B1 L21^T" of Alg. 2 and "C21 <- C21 - A2 A1^T" of Alg. 3 (alpha = -1,
 // beta = 1 in Alg. 1); with `lower` it is the leaf SYRK of Alg. 3 on a diagonal block.
+#include <cstdint>
+
 #include "hrp_internal.cuh"
 
 namespace hrp {
@@ -100,6 +102,95 @@ gemm_simt_kernel(double* __restrict__ C, int ldc, const TIN* __restrict__ X, int
     }
 }
 
+// FP32 products of the FP32 levels with operands from the FP32 shadow, for large tiles:
+// 128 x 128 outputs per CTA, 256 threads, 8 x 8 per thread (rows 4 tx + i and 64 + 4 tx + i,
+// columns 4 ty + j and 64 + 4 ty + j), K in slices of 16 staged in shared memory (k-major,
+// 16-byte loads and reads) with the next slice prefetched into registers.  The FP64 master
+// update C -= acc is the epilogue; `lower` skips tiles above the diagonal and masks entries
+// above it.
+constexpr int SG_T = 128, SG_BK = 16;
+
+__global__ void __launch_bounds__(256)
+sgemm128_kernel(double* __restrict__ C, int ldc, const float* __restrict__ X, int ldx,
+                const float* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
+  __shared__ __align__(16) float Xs[SG_BK][SG_T];
+  __shared__ __align__(16) float Ys[SG_BK][SG_T];
+  const int m0 = blockIdx.x * SG_T, n0 = blockIdx.y * SG_T;
+  if (lower && m0 + SG_T - 1 < n0) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loader: thread t covers rows 4 (t % 32) .. +3 of slice rows kk = t / 32 and kk + 8
+  const int lr = 4 * (tid & 31), lk = tid >> 5;
+  const bool fullm = m0 + SG_T <= m, fulln = n0 + SG_T <= n;
+  float4 px[2], py[2];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gk = k0 + lk + 8 * h;
+      if (gk < k && fullm) {
+        px[h] = *reinterpret_cast<const float4*>(X + (size_t)gk * ldx + m0 + lr);
+      } else {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (gk < k && m0 + lr + q < m) ? X[(size_t)gk * ldx + m0 + lr + q] : 0.f;
+        px[h] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+      if (gk < k && fulln) {
+        py[h] = *reinterpret_cast<const float4*>(Y + (size_t)gk * ldy + n0 + lr);
+      } else {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (gk < k && n0 + lr + q < n) ? Y[(size_t)gk * ldy + n0 + lr + q] : 0.f;
+        py[h] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  fetch(0);
+  for (int k0 = 0; k0 < k; k0 += SG_BK) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      *reinterpret_cast<float4*>(&Xs[lk + 8 * h][lr]) = px[h];
+      *reinterpret_cast<float4*>(&Ys[lk + 8 * h][lr]) = py[h];
+    }
+    __syncthreads();
+    if (k0 + SG_BK < k) fetch(k0 + SG_BK);
+#pragma unroll
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[kk][4 * tx]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[kk][64 + 4 * tx]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Ys[kk][4 * ty]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Ys[kk][64 + 4 * ty]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int gc = n0 + (j < 4 ? 4 * ty + j : 64 + 4 * ty + (j - 4));
+    if (gc >= n) continue;
+    double cv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int gr = m0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + (i - 4));
+      cv[i] = (gr < m && !(lower && gr < gc)) ? C[(size_t)gc * ldc + gr] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int gr = m0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + (i - 4));
+      if (gr < m && !(lower && gr < gc)) C[(size_t)gc * ldc + gr] = cv[i] - (double)acc[i][j];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const double* Y, int ldy,
@@ -129,6 +220,16 @@ cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, co
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  // large products: 128 x 128 tiles once they cover the SMs (16-byte operand loads need
+  // 16-byte aligned operand columns)
+  const bool vec = (ldx % 4) == 0 && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  if (vec && k >= 64 && (long long)((m + 127) / 128) * ((n + 127) / 128) >= sms / 2) {
+    dim3 g128((m + 127) / 128, (n + 127) / 128);
+    if (g128.y > 65535) return cudaErrorInvalidValue;
+    sgemm128_kernel<<<g128, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
+    return cudaGetLastError();
+  }
   const bool small = (long long)((m + 63) / 64) * ((n + 63) / 64) < sms;
   const int tl = small ? 32 : 64;
   dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);

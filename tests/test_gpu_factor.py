@@ -109,6 +109,21 @@ def test_mixed_tree_matches_emulator(hrp_mod, handle, spec, leaf, n, rho):
     assert dense.backward_error(A, L) <= 5e-5
 
 
+def test_large_fp32_level_matches_emulator(hrp_mod, handle):
+    # n = 4096 with an FP32 tree: the FP32 products of the outer levels (2048^2 x 2048 and
+    # below) are large enough to run on 128 x 128 tiles from the FP32 shadow.  With every
+    # level FP32, the GPU's FP32 accumulation over k = 2048 moves entries by as much as the
+    # FP32 operand rounding the emulator models (both ~1e-10 relative here), so only the
+    # FP32-accumulation bound is asserted, not the "closer to the emulator" ratio.
+    n = 4096
+    A = dominant_spd(n, 2.0, seed_for(0, 77))
+    L, info, _ = _factor(hrp_mod, handle, A, "[F32|F64@128]", 128)
+    assert info == 0
+    L_emu, info_e, _ = otree.emulate_potrf(A, otree.parse("[F32|F64@128]", leaf=128))
+    assert info_e == 0
+    assert np.max(np.abs(L - L_emu)) <= 1e-5 * np.max(np.abs(L_emu))
+
+
 @pytest.mark.parametrize("spec,leaf", [("[F16,F64]", 128), ("[F16,F16,F64]", 64), ("[F16,F16,F16,F64]", 128),
                                        ("[F64,F16,F64]", 64)])
 @pytest.mark.parametrize("n,rho", [(1000, 1.05), (2048, 2.0)])
