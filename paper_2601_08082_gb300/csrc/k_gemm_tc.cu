@@ -11,6 +11,7 @@
 // issues the MMAs (one elected thread), warps 2-5 read the accumulator back with
 // tcgen05.ld and update the master.  Every mbarrier wait is bounded by %globaltimer and
 // reports DEV_ERR_TIMEOUT instead of spinning forever.
+#include <algorithm>
 #include <cstdio>
 
 #include "hrp_internal.cuh"
@@ -225,6 +226,172 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
   }
 }
 
+// Persistent variant for products with more tiles than SMs: each CTA walks the active
+// tiles (column-major over the tile grid, tiles above the diagonal skipped when `lower`)
+// with stride gridDim.x.  The TMEM accumulator is double-buffered (2 x BN columns): the MMA
+// warp fills buffer (t & 1) for tile t while the four epilogue warps drain the other one,
+// so the FP64 read-modify-write of tile t overlaps the MMAs of tile t + 1.  The operand ring
+// (STAGES slots) runs on across tiles.  acc_full[b]: MMAs of the tile in buffer b done
+// (tcgen05.commit); acc_empty[b]: its epilogue has read it (one arrival per epilogue warp).
+// All waits are bounded; on a timeout every role stops after its current tile.
+template <int BN>
+__device__ __forceinline__ bool tile_of(int idx, int gm, int gn, bool lower, int& mt, int& nt) {
+  for (int j = 0; j < gn; ++j) {
+    const int first = lower ? (j * BN) / TC_BM : 0;
+    const int cnt = gm - first;
+    if (cnt <= 0) continue;
+    if (idx < cnt) {
+      mt = first + idx;
+      nt = j;
+      return true;
+    }
+    idx -= cnt;
+  }
+  return false;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                       double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
+                       int ntiles, unsigned* __restrict__ err) {
+  using Lay = TcLayout<BN>;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_STAGES * Lay::a_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * Lay::b_stage);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* acc_full = empty + TC_STAGES;          // [2]
+  uint64_t* acc_empty = acc_full + 2;              // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (k + TC_BK - 1) / TC_BK;
+  const int gm = (m + TC_BM - 1) / TC_BM, gn = (n + BN - 1) / BN;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < TC_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"((uint32_t)(2 * BN)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
+      long long kb_all = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int mt, nt;
+        if (!tile_of<BN>(t, gm, gn, lower != 0, mt, nt)) break;
+        for (int kb = 0; kb < nk; ++kb, ++kb_all) {
+          const int q = (int)(kb_all % TC_STAGES);
+          const uint32_t ph = (uint32_t)((kb_all / TC_STAGES) & 1);
+          if (!mbar_wait(&empty[q], ph ^ 1)) { atomicOr(err, DEV_ERR_TIMEOUT); *abort_flag = 1; break; }
+          mbar_arrive_expect_tx(&full[q], (uint32_t)(Lay::a_stage + Lay::b_stage));
+          tma_load_2d(sA + q * Lay::a_stage, &tmX, kb * TC_BK, mt * TC_BM, &full[q]);
+          tma_load_2d(sB + q * Lay::b_stage, &tmY, kb * TC_BK, nt * BN, &full[q]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
+      long long kb_all = 0;
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        if (!mbar_wait(&acc_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1))) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++kb_all) {
+          const int q = (int)(kb_all % TC_STAGES);
+          const uint32_t ph = (uint32_t)((kb_all / TC_STAGES) & 1);
+          if (!mbar_wait(&full[q], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
+          tc_fence_after();
+          const uint64_t ad = sw128_desc(sA + q * Lay::a_stage);
+          const uint64_t bd = sw128_desc(sB + q * Lay::b_stage);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            mma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[q]);
+        }
+        if (!ok) { *abort_flag = 1; break; }
+        mma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its accessible sub-partition)
+    const int qd = warp & 3;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      int mt, nt;
+      if (!tile_of<BN>(t, gm, gn, lower != 0, mt, nt)) break;
+      const int b = it & 1;
+      const bool ok = mbar_wait(&acc_full[b], (uint32_t)((it >> 1) & 1));
+      if (!ok) { atomicOr(err, DEV_ERR_TIMEOUT); *abort_flag = 1; break; }
+      tc_fence_after();
+      const int m0 = mt * TC_BM, n0 = nt * BN;
+      const int row = m0 + qd * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= n) break;                       // uniform across the warp
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + c0), r);
+        if (row < m) {
+          double* base_p = C + (size_t)(n0 + c0) * ldc + row;
+          double cv[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            cv[j] = (col < n && (!lower || row >= col)) ? __ldcs(base_p + (size_t)j * ldc) : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < n && (!lower || row >= col))
+              __stcs(base_p + (size_t)j * ldc, cv[j] - scale * (double)__uint_as_float(r[j]));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+      if (*abort_flag) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                 : "memory");
+  }
+}
+
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -259,6 +426,26 @@ bool make_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld, 
 }
 
 template <int BN>
+cudaError_t launch_persistent(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n,
+                              int k, bool lower, double scale, long long ntiles, int sms, unsigned* dev_err,
+                              cudaStream_t s) {
+  CUtensorMap mx, my;
+  if (!make_map(&mx, S + (size_t)xr0 * lds + k0, m, k, lds, TC_BM)) return cudaErrorInvalidValue;
+  if (!make_map(&my, S + (size_t)yr0 * lds + k0, n, k, lds, BN)) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_tc_persistent<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcLayout<BN>::bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = (int)std::min<long long>(ntiles, sms);
+  gemm_f16_tc_persistent<BN><<<grid, TC_THREADS, TcLayout<BN>::bytes, s>>>(mx, my, C, ldc, m, n, k, lower ? 1 : 0,
+                                                                          scale, (int)ntiles, dev_err);
+  return cudaGetLastError();
+}
+
+template <int BN>
 cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n, int k,
                       bool lower, double scale, unsigned* dev_err, cudaStream_t s) {
   CUtensorMap mx, my;
@@ -284,7 +471,7 @@ long long active_tiles(int m, int n, bool lower, int bn) {
   long long t = 0;
   for (int j = 0; j < gn; ++j) {
     const int first = (j * bn) / TC_BM;          // first M-tile reaching the diagonal of column tile j
-    t += gm - first;
+    t += gm > first ? gm - first : 0;
   }
   return t;
 }
@@ -311,6 +498,17 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int
   // cover the SMs (tiles of 64 or 32 columns also fit two CTAs per SM, one CTA's epilogue
   // then overlapping the other's MMAs).
   const int bn = pick_bn(m, n, lower);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  // more tiles than SMs: persistent CTAs with the epilogue of one tile under the MMAs of the next
+  if (bn >= 128) {
+    const long long nt = active_tiles(m, n, lower, bn);
+    if (nt > sms) {
+      if (bn == 256)
+        return launch_persistent<256>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, nt, sms, dev_err, s);
+      return launch_persistent<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, nt, sms, dev_err, s);
+    }
+  }
   if (bn == 256) return launch_bn<256>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
   if (bn == 128) return launch_bn<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
   if (bn == 64) return launch_bn<64>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, scale, dev_err, s);
