@@ -36,8 +36,8 @@ METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated back
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (nominal); DFMA-bound kernels report against it
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture
 # (profiles/potrf_leaf_cluster_n2048.md), reported while the kernel source is the one captured
-LEAF_TRAFFIC = {"bytes": 141312 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "sha1": "13416e11383d86225b40891113d38c68edc73602"}
+LEAF_TRAFFIC = {"bytes": 140032 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "sha1": "bcd1b725821b71b5d0289181c19612f75d04edfa"}
 
 
 def leaf_traffic():
