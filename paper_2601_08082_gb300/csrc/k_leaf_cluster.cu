@@ -13,8 +13,10 @@
 //      while the other CTAs apply the update of panel p-1 to their tiles;
 //                                                                      cluster barrier
 //   B  the owners of (I, p), I > p, solve X L_pp^T = A_Ip (TRSM) and store the result
-//      into the shared memory of every CTA that updates a tile with it; D applies the
-//      update of panel p-1 to its other tiles;                         cluster barrier
+//      into the shared memory of every CTA that updates a tile with it;
+//                                                                      cluster barrier
+// D's other tiles get the update of panel p-1 (and D's diagonal tile its FP32 inverse) in
+// phase A of panel p + 1, while the next diagonal owner factors.
 // Finished panel tiles are written into the consumers' shared memory (distributed shared
 // memory stores, double-buffered by panel parity), so no CTA waits on a remote load
 // inside the loop.  The only waits are the hardware cluster barriers, which every thread
@@ -378,14 +380,33 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
           for (int r = 0; r < kCL; ++r)
             if (trsm_ctas & (1u << r)) cluster.map_shared_rank(sm.rin_copy, r)[tid] = sm.rinv[tid];
       }
-    } else if (p > 0) {
-      for (int J = p; J < NT; ++J)
-        for (int I = J; I < NT; ++I)
-          if (owner_of(I, J) == rank) {
-            double* C = sm.own[sm.slot[I][J]];
-            if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
-            else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
-          }
+    } else {
+      // the work D(p-1) left for later: its tiles' update with panel p-2 (still in buffer
+      // `cur`; panel p's tiles only arrive there in phase B) and the FP32 inverse of its
+      // diagonal tile (p-1, p-1)
+      if (p >= 2 && rank == owner_of(p - 1, p - 1)) {
+        for (int J = p; J < NT; ++J)
+          for (int I = J; I < NT; ++I)
+            if (owner_of(I, J) == rank) {
+              double* C = sm.own[sm.slot[I][J]];
+              if (I == J) tile_update_diag(C, sm.pan[cur][I], tid);
+              else tile_update(C, sm.pan[cur][I], sm.pan[cur][J], tid);
+            }
+      }
+      if (W32 && p >= 1 && rank == owner_of(p - 1, p - 1)) {
+        float* F = sm.ownf[sm.slot[p - 1][p - 1]];
+        to_f32(sm.own[sm.slot[p - 1][p - 1]], F, tid);
+        __syncthreads();
+        if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p - 1 >= 4 ? 1 : 0], lane);
+      }
+      if (p > 0)
+        for (int J = p; J < NT; ++J)
+          for (int I = J; I < NT; ++I)
+            if (owner_of(I, J) == rank) {
+              double* C = sm.own[sm.slot[I][J]];
+              if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
+              else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
+            }
     }
     cluster.sync();                                              // S1
     if (*(volatile int*)cluster.map_shared_rank(&sm.fail, D)) { failed = true; break; }
@@ -400,21 +421,13 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
       push_tile(cluster, X, sm.pan[cur][mine], consumers(mine, p, NT), tid);
       if (W32) to_f32(X, sm.ownf[sm.slot[mine][p]], tid);
     }
-    if (rank == D) {
-      if (p > 0)
-        for (int J = p + 1; J < NT; ++J)
-          for (int I = J; I < NT; ++I)
-            if (owner_of(I, J) == rank) {
-              double* C = sm.own[sm.slot[I][J]];
-              if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
-              else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
-            }
-      if (W32) {
-        float* F = sm.ownf[sm.slot[p][p]];
-        to_f32(sm.own[sm.slot[p][p]], F, tid);
-        __syncthreads();
-        if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p >= 4 ? 1 : 0], lane);
-      }
+    // D's other tiles and the FP32 inverse of (p, p) wait for phase A of panel p + 1 (done
+    // there while D(p+1) factors), except after the last panel
+    if (rank == D && W32 && p + 1 == NT) {
+      float* F = sm.ownf[sm.slot[p][p]];
+      to_f32(sm.own[sm.slot[p][p]], F, tid);
+      __syncthreads();
+      if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p >= 4 ? 1 : 0], lane);
     }
     cluster.sync();                                              // S2
   }
