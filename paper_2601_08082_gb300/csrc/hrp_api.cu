@@ -230,7 +230,7 @@ struct Fact {
     begin(CLS_TRSM, (double)m * nc * nc);
     if (p == HRP_F64 || t->trsm_compute == 1) {
       chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
-      quant8(r0, m, c0, nc);
+      quant8(r0, m, c0, nc, p);
       return;
     }
     auto it = leaves.find(c0);
@@ -240,24 +240,22 @@ struct Fact {
     } else {
       chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
     }
-    quant8(r0, m, c0, nc);
+    quant8(r0, m, c0, nc, p);
   }
 
-  // FP8 levels: E4M3 tiles of every finished panel (scale per 128 x 128 tile)
+  // FP8 levels: E4M3 tiles (scale per 128 x 128 tile) of what the F8-level GEMMs of a node
+  // read: the panels of its A21 as the F8-level TRSM finishes them (quant8), and the
+  // off-diagonal tiles of its L11 in one launch once L11 is factored (quant8_lower)
   static constexpr int kG = 8;   // storage upshift: entries are 2^8 s e4m3(x/s)
-  void quant8(int r0, int m, int c0, int nc) {
-    if (!shadow8) return;
-    // only panels some F8-level GEMM reads: the left half (L11 and A21 columns) of the nodes
-    // at an F8 depth (F8 trees have n = 128 * 2^k, so node starts are multiples of the order)
-    bool needed = false;
-    for (int d = 0; d < t->depth && !needed; ++d)
-      if (t->level[d] == HRP_F8E4M3) {
-        const int N = n >> d;
-        needed = N >= 256 && (c0 % N) < N / 2;
-      }
-    if (!needed) return;
+  void quant8(int r0, int m, int c0, int nc, int p) {
+    if (!shadow8 || p != HRP_F8E4M3) return;
     begin(CLS_OTHER, 0.0);
     chk(launch_quant_e4m3(A, lda, r0, m, c0, nc, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
+  }
+  void quant8_lower(int off, int nb) {
+    if (!shadow8 || nb < 256) return;
+    begin(CLS_OTHER, 0.0);
+    chk(launch_quant_e4m3_lower(A, lda, off, nb, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
   }
 
   // C = A[r0:r0+m, c0:c0+nd] -= X Y^T, X = A[r0:r0+m, k0:k0+k], Y = A[c0:c0+nd, k0:k0+k]
@@ -322,6 +320,7 @@ struct Fact {
     }
     int n1 = split(nb), n2 = nb - n1;
     potrf(off, n1, depth + 1);
+    if (p == HRP_F8E4M3) quant8_lower(off, n1);
     trsm(off + n1, n2, off, n1, p);
     syrk(off + n1, n2, off, n1, p);
     potrf(off + n1, n2, depth + 1);

@@ -102,6 +102,9 @@ cudaError_t launch_backward_error(const double* A, int lda, const double* L, int
 // exponent per 128 x 128 tile into tile_exp[(row tile) * ntile_ld + (col tile)].
 cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
                               int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s);
+// every 128 x 128 tile strictly below the diagonal tiles of A[off:off+nb, off:off+nb]
+cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, int lds, int* tile_exp,
+                                    int ntile_ld, int G, unsigned* err, cudaStream_t s);
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 

@@ -335,21 +335,37 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
     sm.fail = 0;
   }
   __syncthreads();
-  // load the owned tiles; rows / columns past n are the identity
+  // load the owned tiles (all loads issued before the first store); rows / columns past n
+  // are the identity
   if (!skip) {
-    for (int J = 0; J < NT; ++J)
-      for (int I = J; I < NT; ++I) {
-        if (owner_of(I, J) != rank) continue;
-        double* T = sm.own[sm.slot[I][J]];
-        for (int e = tid; e < kTS * kTS; e += kCThreads) {
-          const int jj = e >> 4, ii = e & 15;        // column-major walk: coalesced reads
+    // NT <= 8, so this CTA owns at most one tile per block column J: row (rank - J) mod 8
+    double v[kCL][2];
+#pragma unroll
+    for (int J = 0; J < kCL; ++J) {
+      const int I = (rank - J) & 7;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + kCThreads * h;
+        const int jj = e >> 4, ii = e & 15;          // column-major walk: coalesced reads
+        double x = 0.0;
+        if (J < NT && I >= J && I < NT) {
           const int gi = kTS * I + ii, gj = kTS * J + jj;
-          double v;
-          if (gi < n && gj < n) v = (gi >= gj) ? A[(size_t)gj * ld + gi] : 0.0;
-          else v = (gi == gj) ? 1.0 : 0.0;
-          T[ii * kTLD + jj] = v;
+          if (gi < n && gj < n) x = (gi >= gj) ? A[(size_t)gj * ld + gi] : 0.0;
+          else x = (gi == gj) ? 1.0 : 0.0;
         }
+        v[J][h] = x;
       }
+    }
+#pragma unroll
+    for (int J = 0; J < kCL; ++J) {
+      const int I = (rank - J) & 7;
+      if (J < NT && I >= J && I < NT)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = tid + kCThreads * h;
+          sm.own[sm.slot[I][J]][(e & 15) * kTLD + (e >> 4)] = v[J][h];
+        }
+    }
   }
   cluster.sync();
   if (skip) return;

@@ -308,30 +308,33 @@ constexpr int kQT = 128;     // tile edge (rows and columns)
 constexpr int kQLD = 129;    // row stride (doubles) of the staged tile
 constexpr int kQThreads = 1024;
 
-// One CTA per 128 x 128 tile of the panel: the tile is read once from the master
-// (coalesced along rows) into shared memory, its amax gives the power-of-two scale
-// s = 2^sig = 2^ceil(log2(amax / 448)), and the FP16 shadow is written row by row (coalesced
-// along columns).
-__global__ void __launch_bounds__(kQThreads)
-quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, __half* __restrict__ S8,
-                  int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
-  extern __shared__ double tileq[];                  // [128][kQLD]
+// One 128 x 128 tile (rows R0 .. R0 + rows - 1, columns c0 .. c0 + 127) by one CTA: the tile
+// is read once from the master (coalesced along rows, all 16 loads per thread in flight) into
+// shared memory, its amax gives the power-of-two scale s = 2^sig = 2^ceil(log2(amax / 448)),
+// and the FP16 shadow is written row by row (coalesced along columns).
+__device__ __forceinline__ void quant_tile(const double* __restrict__ A, int ld, int R0, int rows, int c0,
+                                           __half* __restrict__ S8, int lds, int* __restrict__ tile_exp,
+                                           int ntile_ld, int G, unsigned* __restrict__ err, double* tileq) {
   __shared__ unsigned long long red[kQThreads / 32];
   __shared__ int s_sig;
-  const int tr = blockIdx.x;                       // row tile within the panel
-  const int R0 = r0 + tr * kQT;
-  const int rows = min(kQT, r0 + m - R0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kPer = kQT * kQT / kQThreads;
+  double v[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int idx = tid + u * kQThreads;
+    const int i = idx & (kQT - 1), j = idx >> 7;
+    v[u] = i < rows ? A[(size_t)(c0 + j) * ld + R0 + i] : 0.0;
+  }
   // amax over finite entries, as the largest |x| bit pattern (non-negative doubles order like
   // their bits)
   unsigned long long abits = 0;
-#pragma unroll 4
-  for (int idx = tid; idx < kQT * kQT; idx += kQThreads) {
-    const int i = idx & (kQT - 1), j = idx >> 7;
-    const double x = i < rows ? A[(size_t)(c0 + j) * ld + R0 + i] : 0.0;
-    tileq[i * kQLD + j] = x;
-    const unsigned long long v = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-    if (v < 0x7ff0000000000000ull && v > abits) abits = v;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int idx = tid + u * kQThreads;
+    tileq[(idx & (kQT - 1)) * kQLD + (idx >> 7)] = v[u];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]) & 0x7fffffffffffffffull;
+    if (b < 0x7ff0000000000000ull && b > abits) abits = b;
   }
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, abits, o);
@@ -363,6 +366,30 @@ quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, _
   }
 }
 
+// The panel rows r0 .. r0 + m - 1, columns c0 .. c0 + 127: one CTA per row tile.
+__global__ void __launch_bounds__(kQThreads)
+quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, __half* __restrict__ S8,
+                  int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  extern __shared__ double tileq[];                  // [128][kQLD]
+  const int R0 = r0 + blockIdx.x * kQT;
+  quant_tile(A, ld, R0, min(kQT, r0 + m - R0), c0, S8, lds, tile_exp, ntile_ld, G, err, tileq);
+}
+
+// Every tile strictly below the diagonal tiles of the block A[off:off+nb, off:off+nb]: CTA e
+// takes tile (I, J), e = I (I - 1) / 2 + J, 0 <= J < I.
+__global__ void __launch_bounds__(kQThreads)
+quant_e4m3_lower_kernel(const double* __restrict__ A, int ld, int off, int nb, __half* __restrict__ S8, int lds,
+                        int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  extern __shared__ double tileq[];                  // [128][kQLD]
+  const int e = blockIdx.x;
+  int I = (int)((1.0f + sqrtf(8.0f * (float)e + 1.0f)) * 0.5f);
+  while (I * (I - 1) / 2 > e) --I;                   // guards against the float rounding
+  while ((I + 1) * I / 2 <= e) ++I;
+  const int J = e - I * (I - 1) / 2;
+  const int R0 = off + I * kQT;
+  quant_tile(A, ld, R0, min(kQT, off + nb - R0), off + J * kQT, S8, lds, tile_exp, ntile_ld, G, err, tileq);
+}
+
 }  // namespace
 
 cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
@@ -377,6 +404,24 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
     attr_done = true;
   }
   quant_e4m3_kernel<<<(m + 127) / 128, kQThreads, smem, s>>>(A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, int lds, int* tile_exp,
+                                    int ntile_ld, int G, unsigned* err, cudaStream_t s) {
+  const int nt = (nb + kQT - 1) / kQT;
+  if (nt < 2) return cudaSuccess;
+  if (off % kQT) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)128 * kQLD * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e =
+        cudaFuncSetAttribute(quant_e4m3_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  quant_e4m3_lower_kernel<<<nt * (nt - 1) / 2, kQThreads, smem, s>>>(A, ld, off, nb, S8, lds, tile_exp, ntile_ld, G,
+                                                                    err);
   return cudaGetLastError();
 }
 

@@ -69,6 +69,34 @@ def test_single_fp64_leaf_on_a_cluster(hrp_mod, handle, n):
     assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-40, 1e40])
+def test_single_fp64_leaf_graded_pivots(hrp_mod, handle, scale):
+    # A = G G^T with rows 2i + 1 = row 2i + eps_i h_i (eps_i from 1e-3 to 1): every odd
+    # pivot is about eps_i^2 under diagonal entries about 1, so the pivot recurrence's
+    # single-precision estimate of d_k cancels and its reciprocal falls back to the seed
+    # from d_k itself (51 of the 128 pivots lose more than 4 bits); scaled by 1e-40 or 1e40
+    # the pivots leave the single-precision range.  Backward error: |L L^T - A| <=
+    # gamma_{n+1} |L| |L^T| <= (n + 1) u max a_ii per entry (Higham, Thm. 10.3), with a
+    # factor 4 for the FP64 residual product and the reciprocals' last-bit errors; and no
+    # more than 8x the plain Cholesky's residual (a reciprocal off in its last 8 bits would
+    # show there first).
+    n = 128
+    rng = np.random.default_rng(seed_for(0, 42))
+    G0 = rng.standard_normal((n, 2 * n)) / np.sqrt(2 * n)
+    G = G0.copy()
+    G[1::2] = G0[0::2] + (10.0 ** rng.uniform(-3, 0, n // 2))[:, None] * G0[1::2]
+    A = (G @ G.T) * scale
+    A = 0.5 * (A + A.T)
+    bound = 4 * (n + 1) * np.finfo(np.float64).eps * np.max(np.diag(A))
+    Lo, info0 = dense.cholesky(A)
+    res0 = np.max(np.abs(Lo @ Lo.T - A))
+    assert info0 == 0 and res0 <= bound
+    L, info, _ = _factor(hrp_mod, handle, A, "[F64]", 128)
+    assert info == 0
+    res = np.max(np.abs(L @ L.T - A))
+    assert res <= bound and res <= 8 * res0
+
+
 @pytest.mark.parametrize("col", [1, 16, 17, 90, 127])
 def test_single_fp64_leaf_reports_failing_column(hrp_mod, handle, col):
     n = 127
