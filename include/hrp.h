@@ -167,6 +167,31 @@ hrp_status hrp_set_timing(hrp_handle* h, int enable);
 int hrp_get_timing(hrp_handle* h, double* out, int n);
 
 /*
+ * Autotuner for the recursion cut-offs of a tree: the base-case sizes b of Alg. 1
+ * (leaf) and Alg. 2 (trsm_leaf), which the paper leaves as parameters (Sec. 3.2).  The
+ * precision list, the inner region and trsm_compute are never changed.
+ * hrp_autotune_candidates (host only, no device work): writes up to `cap` candidate trees
+ *   into out and returns how many there are (-1 for an invalid tree): the given tree
+ *   first, then leaf in {128, 64, 32} with trsm_leaf in {leaf, leaf/2}, without
+ *   duplicates.  A tree with an F8 level admits only leaf = trsm_leaf = 128 (its E4M3
+ *   tiles live on the 128 x 128 grid), so it is its only candidate.
+ * hrp_autotune: factors a seeded SPD matrix of order n (1 <= n <= 65535) drawn on the
+ *   device (off-diagonal entries uniform in [-1, 1), n on the diagonal, the paper's
+ *   synthetic generator of Sec. 4.1) with every candidate: one warm-up, then `reps`
+ *   factorizations timed with CUDA events on `stream`, keeping the median.  A candidate
+ *   counts only if it factors the matrix (info = 0) with a backward error at most
+ *   4 x that of the given tree + 1e-15.  *out receives the fastest, *ms (may be NULL) its
+ *   median milliseconds.  The choice is cached in the handle under (n, precision list,
+ *   inner region, trsm_compute); a later call with that key returns it at once unless
+ *   flags & 1 (re-tune).  Synchronous; allocates 2 n^2 doubles for the call's duration.
+ *   Errors: the given tree's own failure (HRP_ERR_NOT_SPD, HRP_ERR_UNSUPPORTED, ...) is
+ *   returned; other candidates that fail are skipped.
+ */
+int hrp_autotune_candidates(const hrp_tree* tree, hrp_tree* out, int cap);
+hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, int flags, hrp_tree* out,
+                        float* ms, void* stream);
+
+/*
  * Batched factorization of `batch` independent systems (BASELINE's many-systems
  * workload; the paper factors one matrix at a time).  Host arrays: trees[i] (the tree of
  * system i; entries may share one tree; F8 levels are not batched), n[i], dA[i] (device

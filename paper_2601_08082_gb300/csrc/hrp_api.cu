@@ -75,6 +75,8 @@ struct hrp_handle_s {
   float* pio = nullptr;        // device, 12 inputs + 8 logits
   bool policy_set = false;
   int last_choice = -1;
+  // autotuner: tuned tree and its median time by (n, precision list, inner region, trsm_compute)
+  std::map<std::string, std::pair<hrp_tree, float>> tune_cache;
 };
 
 namespace hrp {
@@ -763,6 +765,120 @@ hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda, c
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(h, e, "hrp_backward_error");
   *out = h->h_norms[1] > 0 ? sqrt(h->h_norms[0] / h->h_norms[1]) : sqrt(h->h_norms[0]);
+  return HRP_OK;
+}
+
+int hrp_autotune_candidates(const hrp_tree* tree, hrp_tree* out, int cap) {
+  if (!tree || cap < 0 || (cap > 0 && !out)) return -1;
+  if (validate_tree(nullptr, tree, 1) != HRP_OK) return -1;
+  std::vector<hrp_tree> c;
+  auto add = [&](int leaf, int tl) {
+    hrp_tree t = *tree;
+    t.leaf = leaf;
+    t.trsm_leaf = (tl == leaf) ? 0 : tl;
+    for (const auto& u : c)
+      if (u.leaf == t.leaf && (u.trsm_leaf ? u.trsm_leaf : u.leaf) == (t.trsm_leaf ? t.trsm_leaf : t.leaf)) return;
+    if (validate_tree(nullptr, &t, 1) == HRP_OK) c.push_back(t);
+  };
+  add(tree->leaf, tree->trsm_leaf ? tree->trsm_leaf : tree->leaf);   // the given tree first
+  if (!tree_has(tree, HRP_F8E4M3)) {                                 // F8 trees: 128 / 128 only
+    for (int leaf : {128, 64, 32}) {
+      add(leaf, leaf);
+      add(leaf, leaf / 2);
+    }
+  }
+  for (int i = 0; i < (int)c.size() && i < cap; ++i) out[i] = c[i];
+  return (int)c.size();
+}
+
+hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, int flags, hrp_tree* out, float* ms,
+                        void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (n < 1 || n > 65535) return bad_arg(h, 3, "n must be in [1, 65535]");
+  if (reps < 1) return bad_arg(h, 4, "reps < 1");
+  if (!out) return bad_arg(h, 6, "out is NULL");
+  char key[256];
+  {
+    int o = snprintf(key, sizeof(key), "n=%d;d=%d;in=%d@%d;tc=%d;L=", n, tree->depth, tree->inner, tree->inner_size,
+                     tree->trsm_compute);
+    for (int i = 0; i < tree->depth && o < (int)sizeof(key) - 4; ++i) o += snprintf(key + o, sizeof(key) - o, "%d,", tree->level[i]);
+  }
+  if (!(flags & 1)) {
+    auto it = h->tune_cache.find(key);
+    if (it != h->tune_cache.end()) {
+      *out = it->second.first;
+      if (ms) *ms = it->second.second;
+      return HRP_OK;
+    }
+  }
+  hrp_tree cand[16];
+  const int nc = std::min(hrp_autotune_candidates(tree, cand, 16), 16);
+  if (nc < 1) return set_err(h, HRP_ERR_INVALID_ARG, "no valid candidate tree");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *base = nullptr, *work = nullptr;
+  const size_t bytes = (size_t)n * n * sizeof(double);
+  if (cudaMalloc(&base, bytes) != cudaSuccess || cudaMalloc(&work, bytes) != cudaSuccess) {
+    cudaFree(base);
+    cudaGetLastError();
+    return set_err(h, HRP_ERR_ALLOC, "autotune: cudaMalloc of 2 x %zu bytes failed", bytes);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto fail = [&](hrp_status x) {
+    cudaFree(base);
+    cudaFree(work);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return x;
+  };
+  cudaError_t ce = launch_fill_spd_uniform(base, n, n, 0x2601008082ull + (unsigned long long)n, s);
+  if (ce != cudaSuccess) return fail(cuda_status(h, ce, "autotune generator"));
+  int best = -1;
+  float best_ms = 0.f;
+  double be_ref = -1.0;
+  for (int c = 0; c < nc; ++c) {
+    std::vector<float> t;
+    int info = 0;
+    for (int r = 0; r <= reps; ++r) {                     // r = 0: warm-up (workspace, caches)
+      ce = cudaMemcpyAsync(work, base, bytes, cudaMemcpyDeviceToDevice, s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+      if (ce != cudaSuccess) return fail(cuda_status(h, ce, "autotune"));
+      st = potrf_enqueue(h, &cand[c], n, work, n, h->d_info, s);
+      if (st != HRP_OK) break;
+      ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(&info, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) return fail(cuda_status(h, ce, "autotune"));
+      if ((st = check_dev_err(h, s)) != HRP_OK || info != 0) break;
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (r > 0) t.push_back(x);
+    }
+    if (st == HRP_ERR_CUDA) return fail(st);              // the context may be unusable
+    if (st != HRP_OK || info != 0 || (int)t.size() != reps) {
+      if (c == 0) return fail(st != HRP_OK ? st : set_err(h, HRP_ERR_NOT_SPD, "autotune: the given tree failed"));
+      continue;
+    }
+    double be = 0.0;
+    if ((st = hrp_backward_error(h, n, base, n, work, n, &be, stream)) != HRP_OK) return fail(st);
+    if (c == 0) be_ref = be;
+    else if (!(be <= 4.0 * be_ref + 1e-15)) continue;
+    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+    const float med = t[reps / 2];
+    if (best < 0 || med < best_ms) {
+      best = c;
+      best_ms = med;
+    }
+  }
+  fail(HRP_OK);
+  *out = cand[best];
+  if (ms) *ms = best_ms;
+  h->tune_cache[key] = {cand[best], best_ms};
   return HRP_OK;
 }
 

@@ -84,6 +84,9 @@ int potrs_epochs(int nrhs);
 
 // ---------------- utilities (k_util.cu) ----------------
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s);
+// seeded SPD test matrix: off-diagonal entries uniform in [-1, 1) (symmetric), n on the
+// diagonal (strictly diagonally dominant); n <= 65535
+cudaError_t launch_fill_spd_uniform(double* A, int lda, int n, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_finalize_info(int* info, cudaStream_t s);
 cudaError_t launch_copy_lower(double* dst, int ldd, const double* src, int lds, int n, cudaStream_t s);
 cudaError_t launch_copy_matrix(double* dst, int ldd, const double* src, int lds, int m, int n, cudaStream_t s);

@@ -183,6 +183,41 @@ int grid_for(size_t work, int threads) {
 
 }  // namespace
 
+namespace {
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators", 2014):
+// the finalizer of the state x + (key + 1) * 0x9e3779b97f4a7c15.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// A_ij = A_ji uniform in [-1, 1) from the counter (seed, min(i,j), max(i,j)); A_ii = n.
+__global__ void fill_spd_uniform_kernel(double* __restrict__ A, int lda, int n, unsigned long long seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  double v;
+  if (i == j) {
+    v = (double)n;
+  } else {
+    const unsigned long long lo = (unsigned long long)min(i, j), hi = (unsigned long long)max(i, j);
+    const unsigned long long r = splitmix64(seed ^ splitmix64(hi * 0x100000000ull + lo));
+    v = 2.0 * ((double)(r >> 11) * 0x1.0p-53) - 1.0;
+  }
+  A[(size_t)j * lda + i] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_fill_spd_uniform(double* A, int lda, int n, unsigned long long seed, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (n > 65535) return cudaErrorInvalidValue;
+  fill_spd_uniform_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(A, lda, n, seed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   fill_int_kernel<<<(count + 255) / 256, 256, 0, s>>>(p, v, count);

@@ -32,6 +32,7 @@ EXPORTED = [
     "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched", "hrp_posv_batched",
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
+    "hrp_autotune_candidates", "hrp_autotune",
 ]
 
 
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.hrp_policy_predict.argtypes = [vp, fp, ip]
     L.hrp_policy_tree.argtypes = [c_int, tp]
     L.hrp_last_policy_choice.argtypes = [vp]
+    L.hrp_autotune_candidates.argtypes = [tp, vp, c_int]
+    L.hrp_autotune.argtypes = [vp, tp, c_int, c_int, c_int, tp, fp, vp]
     _lib = L
     return L
 
@@ -310,6 +313,15 @@ class Handle:
         return {"status": st, "info": list(info), "iters": list(iters), "resid": list(resid),
                 "used_fallback": list(fb)}
 
+    def autotune(self, tree: Tree, n: int, reps: int = 3, retune: bool = False, stream=None) -> tuple[Tree, float]:
+        """(fastest valid candidate tree for order n, its median ms); see hrp_autotune."""
+        out = Tree()
+        ms = ctypes.c_float(0.0)
+        st = self._lib.hrp_autotune(self._h, ctypes.byref(tree), n, reps, 1 if retune else 0, ctypes.byref(out),
+                                    ctypes.byref(ms), _stream(stream))
+        self._check(st)
+        return out, float(ms.value)
+
     def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
         n = A.shape[0] if n is None else n
         out = ctypes.c_double(0.0)
@@ -317,6 +329,17 @@ class Handle:
                                           _stream(stream))
         self._check(st)
         return out.value
+
+
+def autotune_candidates(tree: Tree) -> list[Tree]:
+    """The autotuner's candidate trees for `tree` (host only): the given tree first."""
+    L = load()
+    cap = 16
+    arr = (Tree * cap)()
+    cnt = L.hrp_autotune_candidates(ctypes.byref(tree), ctypes.cast(arr, ctypes.c_void_p), cap)
+    if cnt < 0:
+        raise HrpError(1, "invalid tree")
+    return [arr[i] for i in range(min(cnt, cap))]
 
 
 def policy_tree(index: int) -> Tree:

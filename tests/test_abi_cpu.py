@@ -69,3 +69,39 @@ def test_null_handle_is_rejected_without_a_gpu(lib):
     t = hrp.tree_parse("[F64]", 64)
     assert lib.hrp_potrf(None, ctypes.byref(t), 4, None, 4, None, None) == 1
     assert lib.hrp_potrs(None, 4, 1, None, 4, None, 4, None) == 1
+
+
+@pytest.mark.parametrize("spec,leaf,trsm_leaf", [
+    ("[F16,F32|F64@128]", 128, 0), ("[F64]", 64, 0), ("[F32]", 100, 50), ("[F16,F16,F32]", 128, 64)])
+def test_autotune_candidates_keep_the_precisions(lib, spec, leaf, trsm_leaf):
+    # host-only enumeration: the given tree first, then valid cut-offs, no duplicates; the
+    # precision list, inner region and TRSM arithmetic are those of the given tree
+    from paper_2601_08082_gb300 import hrp
+    t = hrp.tree_parse(spec, leaf=leaf, trsm_leaf=trsm_leaf)
+    cands = hrp.autotune_candidates(t)
+    assert (cands[0].leaf, cands[0].trsm_leaf) == (leaf, trsm_leaf)
+    seen = set()
+    for c in cands:
+        tl = c.trsm_leaf or c.leaf
+        assert 1 <= c.leaf <= 128 and 1 <= tl <= c.leaf
+        assert (c.leaf, tl) not in seen
+        seen.add((c.leaf, tl))
+        assert hrp.tree_format(c) == hrp.tree_format(t)
+        assert (c.depth, list(c.level)[:c.depth], c.inner, c.inner_size, c.trsm_compute) == \
+            (t.depth, list(t.level)[:t.depth], t.inner, t.inner_size, t.trsm_compute)
+    assert {(128, 128), (64, 64), (64, 32)} <= seen
+
+
+def test_autotune_candidates_for_an_f8_tree_are_only_the_tree(lib):
+    from paper_2601_08082_gb300 import hrp
+    t = hrp.tree_parse("[F8,F16,F16,F32|F64@128]", leaf=128)
+    cands = hrp.autotune_candidates(t)
+    assert len(cands) == 1 and cands[0].leaf == 128 and (cands[0].trsm_leaf or 128) == 128
+
+
+def test_autotune_rejects_bad_arguments_without_a_gpu(lib):
+    from paper_2601_08082_gb300 import hrp
+    t = hrp.tree_parse("[F64]", leaf=64)
+    t.leaf = 0
+    assert lib.hrp_autotune_candidates(ctypes.byref(t), None, 0) == -1
+    assert lib.hrp_autotune(None, ctypes.byref(t), 64, 1, 0, ctypes.byref(hrp.Tree()), None, None) != 0
