@@ -55,6 +55,7 @@ struct ClusterLeafSmem {
   double sk[kTS];                       // 1 / d_k
   double rinv[kTS];                     // 1 / L_kk = d_k^{-1/2} of the diagonal tile factored last here
   double rin_copy[kTS];                 // rinv of the diagonal tile the TRSM here uses
+  double lt[kTileD];                    // TRSM: unit lower Lt = L diag(rinv) of that tile
   float ownf[kMaxOwn][kTileD];          // FP32 copies of the finished owned tiles
   float winv[2][kTileD];                // FP32 inverses of the (up to 2) diagonal tiles owned
   float gat[kMaxGather][kTileD];        // W phase: gathered FP32 tiles
@@ -244,26 +245,29 @@ __device__ __forceinline__ int potrf16_chain(double* __restrict__ T, ClusterLeaf
 }
 
 // X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
-// threads: thread (i, cp) = (tid / 8, tid % 8) holds A[i][2cp], A[i][2cp + 1]; x_ik is
-// passed along the row's 8 threads by a shuffle.
+// threads, in unit-diagonal form: with L = Lt diag(L_kk) (Lt_jk = L_jk / L_kk, formed here in
+// Lt) and Y = X diag(L_kk), Y Lt^T = A is a substitution without scaling, y_ij = a_ij -
+// sum_{k<j} y_ik Lt_jk, and X = Y diag(rinv) at the end; no multiply sits between one
+// column's broadcast and the next.  Thread (i, cp) = (tid / 8, tid % 8) holds A[i][2cp],
+// A[i][2cp + 1]; y_ik is passed along the row's 8 threads by a shuffle.
 __device__ __forceinline__ void trsm16(double* __restrict__ A, const double* __restrict__ L,
-                                       const double* __restrict__ rinv, int tid) {
+                                       const double* __restrict__ rinv, double* __restrict__ Lt, int tid) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + kCThreads * h, j = e >> 4, k = e & 15;
+    if (k < j) Lt[j * kTLD + k] = L[j * kTLD + k] * rinv[k];
+  }
+  __syncthreads();
   const int i = tid >> 3, cp = tid & 7, lane = tid & 31, j0 = 2 * cp;
   double c0 = A[i * kTLD + j0], c1 = A[i * kTLD + j0 + 1];
 #pragma unroll
   for (int k = 0; k < kTS; ++k) {
-    const int kc = k >> 1;
-    double x = 0.0;
-    if (cp == kc) {
-      if (k & 1) { c1 *= rinv[k]; x = c1; }
-      else { c0 *= rinv[k]; x = c0; }
-    }
-    x = __shfl_sync(0xffffffffu, x, (lane & ~7) | kc);
-    if (j0 > k) c0 = fma(-x, L[j0 * kTLD + k], c0);
-    if (j0 + 1 > k) c1 = fma(-x, L[(j0 + 1) * kTLD + k], c1);
+    const double y = __shfl_sync(0xffffffffu, (k & 1) ? c1 : c0, (lane & ~7) | (k >> 1));
+    if (j0 > k) c0 = fma(-y, Lt[j0 * kTLD + k], c0);
+    if (j0 + 1 > k) c1 = fma(-y, Lt[(j0 + 1) * kTLD + k], c1);
   }
-  A[i * kTLD + j0] = c0;
-  A[i * kTLD + j0 + 1] = c1;
+  A[i * kTLD + j0] = c0 * rinv[j0];
+  A[i * kTLD + j0 + 1] = c1 * rinv[j0 + 1];
 }
 
 // Store the 16 x 16 tile T into slot `dst` of the shared memory of every CTA in `mask`.
@@ -432,7 +436,7 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
       if (owner_of(I, p) == rank) mine = I;
     if (mine >= 0) {
       double* X = sm.own[sm.slot[mine][p]];
-      trsm16(X, sm.pan[cur][p], sm.rin_copy, tid);
+      trsm16(X, sm.pan[cur][p], sm.rin_copy, sm.lt, tid);
       __syncthreads();
       push_tile(cluster, X, sm.pan[cur][mine], consumers(mine, p, NT), tid);
       if (W32) to_f32(X, sm.ownf[sm.slot[mine][p]], tid);
