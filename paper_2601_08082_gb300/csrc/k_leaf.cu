@@ -3,7 +3,11 @@
 #include <climits>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "hrp_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hrp {
 namespace {
@@ -307,26 +311,36 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
+// CPL = output columns per lane: the CTA computes the 16 rows x C = 32 CPL columns
+// jc0 .. jc0 + C - 1 of X (jc0 = blockIdx.y C), so small panels spread over more SMs.
+// When a row tile is split over several CTAs (gridDim.y > 1) they form one cluster
+// (1 x gridDim.y) and meet at a cluster barrier after all of them have staged B and before
+// any writes X in place.  Every CTA reaches it: the only early exit reads `info`, which no
+// kernel writes while this one runs, so all CTAs see the same value.
+template <int CPL>
 __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
                   float* __restrict__ S32, int ld32, const int* __restrict__ info) {
+  constexpr int C = 32 * CPL;
+  constexpr int WLD = C + 4;                               // 16-byte rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
-  float* Ws = reinterpret_cast<float*>(smem_raw);          // Ws[k * 132 + j] = W(j, k)
-  float* Bs = Ws + 128 * kT32WLD;                          // Bs[r * 132 + k] = B(row0 + r, k); later X
+  const int jc0 = blockIdx.y * C;                          // < nc: gridDim.y = ceil(nc / C)
+  float* Ws = reinterpret_cast<float*>(smem_raw);          // Ws[k * WLD + jj] = W(jc0 + jj, k)
+  float* Bs = Ws + 128 * WLD;                              // Bs[r * 132 + k] = B(row0 + r, k); later X
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kT32Rows;
   const bool vecw = (nc == 128) && ((ldw & 3) == 0) && ((reinterpret_cast<uintptr_t>(W) & 15) == 0);
   if (vecw) {
-    for (int e = tid; e < 128 * 32; e += kT32Threads) {
-      const int k = e >> 5, q = e & 31;
-      cp_async16(Ws + k * kT32WLD + 4 * q, W + (size_t)k * ldw + 4 * q);
+    for (int e = tid; e < 128 * (C / 4); e += kT32Threads) {
+      const int k = e / (C / 4), q = e % (C / 4);
+      cp_async16(Ws + k * WLD + 4 * q, W + (size_t)k * ldw + jc0 + 4 * q);
     }
   } else {
-    for (int e = tid; e < 128 * 128; e += kT32Threads) {
-      const int k = e >> 7, j = e & 127;
-      Ws[k * kT32WLD + j] = (j < nc && k < nc) ? W[(size_t)k * ldw + j] : 0.f;
+    for (int e = tid; e < 128 * C; e += kT32Threads) {
+      const int k = e / C, jj = e % C, j = jc0 + jj;
+      Ws[k * WLD + jj] = (j < nc && k < nc) ? W[(size_t)k * ldw + j] : 0.f;
     }
   }
   // B: 8 values per thread, all loads in flight before the conversions
@@ -345,42 +359,56 @@ trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   }
   cp_async_wait_all();
   __syncthreads();
+  if (gridDim.y > 1) cg::this_cluster().sync();             // every slice has read B
+  // warp w: rows 2w, 2w + 1; lane: columns CPL lane .. CPL lane + CPL - 1
   const int ra = 2 * warp, rb = 2 * warp + 1;
-  float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
+  float xa[CPL], xb[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) xa[c] = xb[c] = 0.f;
   const float* Ba = Bs + ra * kT32WLD;
   const float* Bb = Bs + rb * kT32WLD;
 #pragma unroll 8
   for (int k = 0; k < nc; ++k) {
-    const float4 w = *reinterpret_cast<const float4*>(Ws + k * kT32WLD + 4 * lane);
+    float w[CPL];
+    if constexpr (CPL == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(Ws + k * WLD + 4 * lane);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (CPL == 2) {
+      const float2 v = *reinterpret_cast<const float2*>(Ws + k * WLD + 2 * lane);
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = Ws[k * WLD + lane];
+    }
     const float a = Ba[k], b = Bb[k];
-    xa[0] = fmaf(a, w.x, xa[0]);
-    xa[1] = fmaf(a, w.y, xa[1]);
-    xa[2] = fmaf(a, w.z, xa[2]);
-    xa[3] = fmaf(a, w.w, xa[3]);
-    xb[0] = fmaf(b, w.x, xb[0]);
-    xb[1] = fmaf(b, w.y, xb[1]);
-    xb[2] = fmaf(b, w.z, xb[2]);
-    xb[3] = fmaf(b, w.w, xb[3]);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      xa[c] = fmaf(a, w[c], xa[c]);
+      xb[c] = fmaf(b, w[c], xb[c]);
+    }
   }
   __syncthreads();                                         // all reads of B done: reuse Bs for X
-  *reinterpret_cast<float4*>(Bs + ra * kT32WLD + 4 * lane) = make_float4(xa[0], xa[1], xa[2], xa[3]);
-  *reinterpret_cast<float4*>(Bs + rb * kT32WLD + 4 * lane) = make_float4(xb[0], xb[1], xb[2], xb[3]);
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    Bs[ra * kT32WLD + CPL * lane + c] = xa[c];
+    Bs[rb * kT32WLD + CPL * lane + c] = xb[c];
+  }
   __syncthreads();
+  const int ncol = min(C, nc - jc0);
   // master (column-major): 16 consecutive rows of one column per half-warp
-  for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
-    const int k = e >> 4, r = e & 15;
+  for (int e = tid; e < ncol * kT32Rows; e += kT32Threads) {
+    const int jj = e >> 4, r = e & 15;
     const int gr = row0 + r;
     if (gr < m) {
-      A[(size_t)(c0 + k) * ld + (r0 + gr)] = (double)Bs[r * kT32WLD + k];
-      if (S32 != nullptr) S32[(size_t)(c0 + k) * ld32 + (r0 + gr)] = Bs[r * kT32WLD + k];
+      A[(size_t)(c0 + jc0 + jj) * ld + (r0 + gr)] = (double)Bs[r * kT32WLD + jj];
+      if (S32 != nullptr) S32[(size_t)(c0 + jc0 + jj) * ld32 + (r0 + gr)] = Bs[r * kT32WLD + jj];
     }
   }
   // FP16 shadow (row-major): consecutive columns of one row
   if (S != nullptr) {
-    for (int e = tid; e < nc * kT32Rows; e += kT32Threads) {
-      const int r = e / nc, k = e - r * nc;
+    for (int e = tid; e < ncol * kT32Rows; e += kT32Threads) {
+      const int r = e / ncol, jj = e - r * ncol;
       const int gr = row0 + r;
-      if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + k)] = __float2half_rn(Bs[r * kT32WLD + k]);
+      if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + jc0 + jj)] = __float2half_rn(Bs[r * kT32WLD + jj]);
     }
   }
 }
@@ -451,17 +479,57 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const int* info, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 128) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)(128 + kT32Rows) * kT32WLD * 4;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_inv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(trsm_inv32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((128 * 132 + kT32Rows * kT32WLD) * 4));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(trsm_inv32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((128 * 68 + kT32Rows * kT32WLD) * 4));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(trsm_inv32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((128 * 36 + kT32Rows * kT32WLD) * 4));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  int grid = (m + kT32Rows - 1) / kT32Rows;
-  trsm_inv32_kernel<<<grid, kT32Threads, smem, s>>>(A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                                                     info);
-  return cudaGetLastError();
+  // row tiles of 16; panels with fewer row tiles than SMs split their columns over 2 or 4
+  // CTAs (each then stages only its slice of W)
+  const int gx = (m + kT32Rows - 1) / kT32Rows;
+  const int cpl = gx >= sms ? 4 : (2 * gx >= sms ? 2 : 1);
+  const int C = 32 * cpl;
+  const dim3 grid(gx, (nc + C - 1) / C);
+  const size_t smem = (size_t)(128 * (C + 4) + kT32Rows * kT32WLD) * 4;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kT32Threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = grid.y;                         // the slices of one row tile
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = grid.y > 1 ? 1 : 0;
+  cudaError_t e;
+  if (cpl == 4)
+    e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<4>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
+                           info);
+  else if (cpl == 2)
+    e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<2>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
+                           info);
+  else
+    e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<1>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
+                           info);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace hrp
