@@ -36,8 +36,8 @@ METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated back
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (nominal); DFMA-bound kernels report against it
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture
 # (profiles/potrf_leaf_cluster_n2048.md), reported while the kernel source is the one captured
-LEAF_TRAFFIC = {"bytes": 140032 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "sha1": "bcd1b725821b71b5d0289181c19612f75d04edfa"}
+LEAF_TRAFFIC = {"bytes": 151296 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "sha1": "5cc32f5510b8dc07c087d55ad364e2d30c04b431"}
 
 
 def leaf_traffic():
@@ -48,6 +48,14 @@ def leaf_traffic():
     except OSError:
         ok = False
     return LEAF_TRAFFIC["bytes"] if ok else None
+
+
+def tuned_fp64_tree(h, hrp, n):
+    """The plain FP64 tree with the recursion cut-offs hrp_autotune picks at order n (one timed
+    run per candidate), so the comparison is with the fastest FP64 configuration, not a fixed one."""
+    base = hrp.tree_parse(FP64_TREE, leaf=FP64_LEAF)
+    t, ms = h.autotune(base, n, reps=1)
+    return t, {"leaf": t.leaf, "trsm_leaf": t.trsm_leaf or t.leaf, "tuned_at_n": n, "tuner_ms": ms}
 
 
 def peaks():
@@ -319,9 +327,11 @@ def run_fp8posv(args, rank, world):
             tp.append(t)
     fp64 = None
     if args.fp64_steps > 0:
+        # cut-offs tuned at n = 8192 (tuning at n = 32768 would take minutes: ~10 s per run)
+        tree64, tune64 = tuned_fp64_tree(h, hrp, 8192)
         Af.copy_(A)
-        _, t64 = timed(lambda: h.potrf_async(hrp.tree_parse("[F64]", leaf=64), Af, d_info, stream=stream))
-        fp64 = {"ms": t64, "tflops": n ** 3 / 3.0 / (t64 * 1e-3) / 1e12, "tree": "[F64]", "leaf": 64}
+        _, t64 = timed(lambda: h.potrf_async(tree64, Af, d_info, stream=stream))
+        fp64 = {"ms": t64, "tflops": n ** 3 / 3.0 / (t64 * 1e-3) / 1e12, "tree": FP64_TREE, **tune64}
     ms = statistics.median(tf)
     flops = n ** 3 / 3.0
     line = {"metric": METRIC + " (n=32768 FP8 posv)", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
@@ -396,7 +406,7 @@ def main():
 
     h = hrp.Handle(local)
     tree = hrp.tree_parse(TREE, leaf=LEAF)
-    tree64 = hrp.tree_parse(FP64_TREE, leaf=FP64_LEAF)
+    tree64, tune64 = tuned_fp64_tree(h, hrp, N) if args.fp64_steps > 0 else (None, None)
     stream = torch.cuda.current_stream()
 
     bvec = rhs(N, 1, seed_for(1, 100 + rank))
@@ -493,7 +503,7 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             t64.append(a.elapsed_time(b))
-        fp64 = {"ms": min(t64), "tflops": flops / (min(t64) * 1e-3) / 1e12, "tree": FP64_TREE, "leaf": FP64_LEAF}
+        fp64 = {"ms": min(t64), "tflops": flops / (min(t64) * 1e-3) / 1e12, "tree": FP64_TREE, **tune64}
 
     # end to end through the C ABI with host buffers: H2D(A, b) + potrf + potrs + D2H(x)
     e2e = None
