@@ -23,6 +23,31 @@ constexpr unsigned long long kWaitTimeoutNs = 2000ull * 1000ull * 1000ull;
 // Rounding applied to GEMM operands read from the FP64 master.
 enum class OpRound : int { F64 = 0, F32 = 1, F16 = 2 };
 
+// Programmatic dependent launch.  The factorization is a long chain of dependent launches
+// on one stream; a kernel launched by launch_pdl may be scheduled while the previous kernel
+// of the stream still runs.  Every such kernel calls pdl_wait() before its first access to
+// global memory (the wait returns once the previous grid has completed and its writes are
+// visible; it returns at once for a kernel launched without the attribute), then
+// pdl_trigger() to let the next kernel be scheduled in turn.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------- leaf kernels (k_leaf.cu) ----------------
 // Leaf POTRF of the n x n diagonal block at A (ld), n <= 128, computed in FP64
 // (compute64 = true) or FP32; round16: round input and output to FP16 (F16 leaf).

@@ -33,6 +33,8 @@ template <int RND, int TL, typename TIN = double>
 __global__ void __launch_bounds__(256)
 gemm_simt_kernel(double* __restrict__ C, int ldc, const TIN* __restrict__ X, int ldx,
                  const TIN* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
+  pdl_wait();
+  pdl_trigger();
   using T = typename Acc<RND>::T;
   constexpr int BK = Slice<RND>::BK;
   constexpr int BM = TL, BN = TL, R = TL / 16;
@@ -113,6 +115,8 @@ constexpr int SG_T = 128, SG_BK = 16;
 __global__ void __launch_bounds__(256)
 sgemm128_kernel(double* __restrict__ C, int ldc, const float* __restrict__ X, int ldx,
                 const float* __restrict__ Y, int ldy, int m, int n, int k, int lower) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ __align__(16) float Xs[SG_BK][SG_T];
   __shared__ __align__(16) float Ys[SG_BK][SG_T];
   const int m0 = blockIdx.x * SG_T, n0 = blockIdx.y * SG_T;
@@ -205,7 +209,7 @@ cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const
   const int tl = small ? 32 : 64;
   dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-#define HRP_SIMT(R_, T_) gemm_simt_kernel<R_, T_><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower)
+#define HRP_SIMT(R_, T_) (void)launch_pdl(gemm_simt_kernel<R_, T_>, dim3(grid), dim3(256), 0, s, C, ldc, X, ldx, Y, ldy, m, n, k, lower)
   switch (rnd) {
     case OpRound::F64: if (small) HRP_SIMT(0, 32); else HRP_SIMT(0, 64); break;
     case OpRound::F32: if (small) HRP_SIMT(1, 32); else HRP_SIMT(1, 64); break;
@@ -227,7 +231,7 @@ cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, co
   if (vec && k >= 64 && (long long)((m + 127) / 128) * ((n + 127) / 128) >= sms / 2) {
     dim3 g128((m + 127) / 128, (n + 127) / 128);
     if (g128.y > 65535) return cudaErrorInvalidValue;
-    sgemm128_kernel<<<g128, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
+    (void)launch_pdl(sgemm128_kernel, dim3(g128), dim3(256), 0, s, C, ldc, X, ldx, Y, ldy, m, n, k, lower);
     return cudaGetLastError();
   }
   const bool small = (long long)((m + 63) / 64) * ((n + 63) / 64) < sms;
@@ -235,9 +239,9 @@ cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, co
   dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if (small)
-    gemm_simt_kernel<1, 32, float><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
+    (void)launch_pdl(gemm_simt_kernel<1, 32, float>, dim3(grid), dim3(256), 0, s, C, ldc, X, ldx, Y, ldy, m, n, k, lower);
   else
-    gemm_simt_kernel<1, 64, float><<<grid, 256, 0, s>>>(C, ldc, X, ldx, Y, ldy, m, n, k, lower);
+    (void)launch_pdl(gemm_simt_kernel<1, 64, float>, dim3(grid), dim3(256), 0, s, C, ldc, X, ldx, Y, ldy, m, n, k, lower);
   return cudaGetLastError();
 }
 

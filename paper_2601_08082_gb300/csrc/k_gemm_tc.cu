@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(TC_THREADS, BN <= 64 ? 2 : 1)
 gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                    double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
                    unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   using Lay = TcLayout<BN>;
   extern __shared__ unsigned char smem_raw[];
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
@@ -255,6 +257,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                        double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
                        int ntiles, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   using Lay = TcLayout<BN>;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -440,7 +444,7 @@ cudaError_t launch_persistent(double* C, int ldc, const __half* S, int lds, int 
     attr_set = true;
   }
   const int grid = (int)std::min<long long>(ntiles, sms);
-  gemm_f16_tc_persistent<BN><<<grid, TC_THREADS, TcLayout<BN>::bytes, s>>>(mx, my, C, ldc, m, n, k, lower ? 1 : 0,
+  (void)launch_pdl(gemm_f16_tc_persistent<BN>, dim3(grid), dim3(TC_THREADS), TcLayout<BN>::bytes, s, mx, my, C, ldc, m, n, k, lower ? 1 : 0,
                                                                           scale, (int)ntiles, dev_err);
   return cudaGetLastError();
 }
@@ -459,7 +463,7 @@ cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int
     attr_set = true;
   }
   dim3 grid((m + TC_BM - 1) / TC_BM, (n + BN - 1) / BN);
-  gemm_f16_tc_kernel<BN><<<grid, TC_THREADS, TcLayout<BN>::bytes, s>>>(mx, my, C, ldc, m, n, k, lower ? 1 : 0,
+  (void)launch_pdl(gemm_f16_tc_kernel<BN>, dim3(grid), dim3(TC_THREADS), TcLayout<BN>::bytes, s, mx, my, C, ldc, m, n, k, lower ? 1 : 0,
                                                                         scale, dev_err);
   return cudaGetLastError();
 }

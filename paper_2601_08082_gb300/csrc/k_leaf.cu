@@ -124,6 +124,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, 1)
 potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
                   float* __restrict__ W32, int ldw, int* __restrict__ info) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T col[2][128];
   __shared__ int s_fail;
@@ -240,6 +242,8 @@ __global__ void __launch_bounds__(64)
 trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32, const int* __restrict__ info,
                   int rows_per_cta) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (*(volatile const int*)info != INT_MAX) return;
   T* Ls = reinterpret_cast<T*>(smem_raw);              // row-major nc x nc: Ls[j * nc + k]
@@ -322,6 +326,8 @@ __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
                   float* __restrict__ S32, int ld32, const int* __restrict__ info) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int C = 32 * CPL;
   constexpr int WLD = C + 4;                               // 16-byte rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -431,9 +437,9 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
     attr_done = true;
   }
   if (compute64)
-    potrf_leaf_kernel<double><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+    (void)launch_pdl(potrf_leaf_kernel<double>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
   else
-    potrf_leaf_kernel<float><<<1, 256, smem, s>>>(A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+    (void)launch_pdl(potrf_leaf_kernel<float>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
   return cudaGetLastError();
 }
 
@@ -451,7 +457,7 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
     attr_done = true;
   }
   int grid = (m + RT - 1) / RT;
-  trsm_subst_kernel<double><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
+  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
   return cudaGetLastError();
 }
 
@@ -470,7 +476,7 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
     attr_done = true;
   }
   int grid = (m + RT - 1) / RT;
-  trsm_subst_kernel<float><<<grid, 64, smem, s>>>(A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
+  (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
   return cudaGetLastError();
 }
 
@@ -512,13 +518,15 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
   cfg.blockDim = dim3(kT32Threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 1;
-  at[0].val.clusterDim.y = grid.y;                         // the slices of one row tile
-  at[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see launch_pdl
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = 1;
+  at[1].val.clusterDim.y = grid.y;                         // the slices of one row tile
+  at[1].val.clusterDim.z = 1;
   cfg.attrs = at;
-  cfg.numAttrs = grid.y > 1 ? 1 : 0;
+  cfg.numAttrs = grid.y > 1 ? 2 : 1;
   cudaError_t e;
   if (cpl == 4)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<4>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,

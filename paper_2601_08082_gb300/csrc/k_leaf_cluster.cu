@@ -322,6 +322,8 @@ __device__ __forceinline__ unsigned consumers(int I, int p, int NT) {
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kCThreads, 1)
 potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
                           int* __restrict__ info) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ClusterLeafSmem& sm = *reinterpret_cast<ClusterLeafSmem*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
@@ -562,7 +564,7 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  potrf_leaf_cluster_kernel<<<kCL, kCThreads, sizeof(ClusterLeafSmem), s>>>(A, ld, n, col0, W32, ldw, info);
+  (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(ClusterLeafSmem), s, A, ld, n, col0, W32, ldw, info);
   return cudaGetLastError();
 }
 

@@ -9,13 +9,19 @@ namespace hrp {
 namespace {
 
 __global__ void fill_int_kernel(int* p, int v, int count) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) p[i] = v;
 }
 __global__ void finalize_info_kernel(int* info) {
+  pdl_wait();
+  pdl_trigger();
   if (*info == INT_MAX) *info = 0;
 }
 __global__ void copy_lower_kernel(double* dst, int ldd, const double* src, int lds, int n) {
+  pdl_wait();
+  pdl_trigger();
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)n * n;
   for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
@@ -24,6 +30,8 @@ __global__ void copy_lower_kernel(double* dst, int ldd, const double* src, int l
   }
 }
 __global__ void copy_matrix_kernel(double* dst, int ldd, const double* src, int lds, int m, int n) {
+  pdl_wait();
+  pdl_trigger();
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)m * n;
   for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
@@ -32,6 +40,8 @@ __global__ void copy_matrix_kernel(double* dst, int ldd, const double* src, int 
   }
 }
 __global__ void axpy_matrix_kernel(double* X, int ldx, const double* D, int ldd, int n, int nrhs) {
+  pdl_wait();
+  pdl_trigger();
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)n * nrhs;
   for (; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
@@ -55,6 +65,8 @@ __device__ __forceinline__ void tri_index(long long t, int& I, int& J) {
 __global__ void __launch_bounds__(256)
 residual_tile_kernel(const double* __restrict__ A, int lda, const double* __restrict__ X, int ldx,
                      double* __restrict__ R, int ldr, int n, int nrhs) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double As[RT][RT + 1];
   __shared__ double xI[RNRHS][RT];
   __shared__ double xJ[RNRHS][RT];
@@ -92,6 +104,8 @@ residual_tile_kernel(const double* __restrict__ A, int lda, const double* __rest
 }
 
 __global__ void col_norms2_kernel(const double* R, int ldr, const double* B, int ldb, int n, int nrhs, double* out) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   double sr = 0.0, sb = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -220,26 +234,26 @@ cudaError_t launch_fill_spd_uniform(double* A, int lda, int n, unsigned long lon
 
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  fill_int_kernel<<<(count + 255) / 256, 256, 0, s>>>(p, v, count);
+  (void)launch_pdl(fill_int_kernel, dim3((count + 255) / 256), dim3(256), 0, s, p, v, count);
   return cudaGetLastError();
 }
 cudaError_t launch_finalize_info(int* info, cudaStream_t s) {
-  finalize_info_kernel<<<1, 1, 0, s>>>(info);
+  (void)launch_pdl(finalize_info_kernel, dim3(1), dim3(1), 0, s, info);
   return cudaGetLastError();
 }
 cudaError_t launch_copy_lower(double* dst, int ldd, const double* src, int lds, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  copy_lower_kernel<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(dst, ldd, src, lds, n);
+  (void)launch_pdl(copy_lower_kernel, dim3(grid_for((size_t)n * n, 256)), dim3(256), 0, s, dst, ldd, src, lds, n);
   return cudaGetLastError();
 }
 cudaError_t launch_copy_matrix(double* dst, int ldd, const double* src, int lds, int m, int n, cudaStream_t s) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  copy_matrix_kernel<<<grid_for((size_t)m * n, 256), 256, 0, s>>>(dst, ldd, src, lds, m, n);
+  (void)launch_pdl(copy_matrix_kernel, dim3(grid_for((size_t)m * n, 256)), dim3(256), 0, s, dst, ldd, src, lds, m, n);
   return cudaGetLastError();
 }
 cudaError_t launch_axpy_matrix(double* X, int ldx, const double* D, int ldd, int n, int nrhs, cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  axpy_matrix_kernel<<<grid_for((size_t)n * nrhs, 256), 256, 0, s>>>(X, ldx, D, ldd, n, nrhs);
+  (void)launch_pdl(axpy_matrix_kernel, dim3(grid_for((size_t)n * nrhs, 256)), dim3(256), 0, s, X, ldx, D, ldd, n, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_residual(const double* A, int lda, const double* X, int ldx, const double* B, int ldb,
@@ -251,7 +265,7 @@ cudaError_t launch_residual(const double* A, int lda, const double* X, int ldx, 
   const long long tiles = nt * (nt + 1) / 2;
   for (int c0 = 0; c0 < nrhs; c0 += RNRHS) {
     int nc = nrhs - c0 < RNRHS ? nrhs - c0 : RNRHS;
-    residual_tile_kernel<<<(unsigned)tiles, 256, 0, s>>>(A, lda, X + (size_t)c0 * ldx, ldx, R + (size_t)c0 * ldr,
+    (void)launch_pdl(residual_tile_kernel, dim3((unsigned)tiles), dim3(256), 0, s, A, lda, X + (size_t)c0 * ldx, ldx, R + (size_t)c0 * ldr,
                                                          ldr, n, nc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -264,7 +278,7 @@ cudaError_t launch_col_norms2(const double* R, int ldr, const double* B, int ldb
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 2 * nrhs, s);
   if (e != cudaSuccess) return e;
   dim3 grid(grid_for((size_t)n, 256) > 64 ? 64 : grid_for((size_t)n, 256), nrhs);
-  col_norms2_kernel<<<grid, 256, 0, s>>>(R, ldr, B, ldb, n, nrhs, out);
+  (void)launch_pdl(col_norms2_kernel, dim3(grid), dim3(256), 0, s, R, ldr, B, ldb, n, nrhs, out);
   return cudaGetLastError();
 }
 cudaError_t launch_backward_error(const double* A, int lda, const double* L, int ldl, int n, double* out,
@@ -405,6 +419,8 @@ __device__ __forceinline__ void quant_tile(const double* __restrict__ A, int ld,
 __global__ void __launch_bounds__(kQThreads)
 quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, __half* __restrict__ S8,
                   int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double tileq[];                  // [128][kQLD]
   const int R0 = r0 + blockIdx.x * kQT;
   quant_tile(A, ld, R0, min(kQT, r0 + m - R0), c0, S8, lds, tile_exp, ntile_ld, G, err, tileq);
@@ -415,6 +431,8 @@ quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, _
 __global__ void __launch_bounds__(kQThreads)
 quant_e4m3_lower_kernel(const double* __restrict__ A, int ld, int off, int nb, __half* __restrict__ S8, int lds,
                         int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double tileq[];                  // [128][kQLD]
   const int e = blockIdx.x;
   int I = (int)((1.0f + sqrtf(8.0f * (float)e + 1.0f)) * 0.5f);
@@ -438,7 +456,7 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  quant_e4m3_kernel<<<(m + 127) / 128, kQThreads, smem, s>>>(A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
+  (void)launch_pdl(quant_e4m3_kernel, dim3((m + 127) / 128), dim3(kQThreads), smem, s, A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
 }
 
@@ -455,7 +473,7 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  quant_e4m3_lower_kernel<<<nt * (nt - 1) / 2, kQThreads, smem, s>>>(A, ld, off, nb, S8, lds, tile_exp, ntile_ld, G,
+  (void)launch_pdl(quant_e4m3_lower_kernel, dim3(nt * (nt - 1) / 2), dim3(kQThreads), smem, s, A, ld, off, nb, S8, lds, tile_exp, ntile_ld, G,
                                                                     err);
   return cudaGetLastError();
 }
