@@ -36,8 +36,8 @@ METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated back
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (nominal); DFMA-bound kernels report against it
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture
 # (profiles/potrf_leaf_cluster_n2048.md), reported while the kernel source is the one captured
-LEAF_TRAFFIC = {"bytes": 151296 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "sha1": "5cc32f5510b8dc07c087d55ad364e2d30c04b431"}
+LEAF_TRAFFIC = {"bytes": 149376 + 0, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "sha1": "3dac81c8dd589117acc915d2e11f861b282a6c03"}
 
 
 def leaf_traffic():
