@@ -108,6 +108,8 @@ size_t potrs_workspace_bytes(int n);
 int potrs_epochs(int nrhs);
 
 // ---------------- utilities (k_util.cu) ----------------
+// SM count of the current device, queried once per device
+int device_sm_count();
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s);
 // seeded SPD test matrix: off-diagonal entries uniform in [-1, 1) (symmetric), n on the
 // diagonal (strictly diagonally dominant); n <= 65535

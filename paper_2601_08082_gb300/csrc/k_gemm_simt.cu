@@ -203,8 +203,7 @@ cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const
   // 64 x 64 tiles unless that leaves most SMs idle: the operand rounding and the FP64
   // read-modify-write of C run on the FP64 pipe, so the small products of the FP32 levels
   // are spread over 32 x 32 tiles
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const int sms = device_sm_count();
   const bool small = (long long)((m + 63) / 64) * ((n + 63) / 64) < sms;
   const int tl = small ? 32 : 64;
   dim3 grid((m + tl - 1) / tl, (n + tl - 1) / tl);
@@ -222,8 +221,7 @@ cudaError_t launch_gemm_simt(double* C, int ldc, const double* X, int ldx, const
 cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, const float* Y, int ldy,
                                  int m, int n, int k, bool lower, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const int sms = device_sm_count();
   // large products: 128 x 128 tiles once they cover the SMs (16-byte operand loads need
   // 16-byte aligned operand columns)
   const bool vec = (ldx % 4) == 0 && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&

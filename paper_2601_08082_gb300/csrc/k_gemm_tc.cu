@@ -481,8 +481,7 @@ long long active_tiles(int m, int n, bool lower, int bn) {
 }
 
 int pick_bn(int m, int n, bool lower) {
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const int sms = device_sm_count();
   if (n > 128 && active_tiles(m, n, lower, 256) >= sms) return 256;
   if (n > 64 && active_tiles(m, n, lower, 128) >= sms) return 128;
   if (n > 32 && active_tiles(m, n, lower, 64) >= sms) return 64;
@@ -502,8 +501,7 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int
   // cover the SMs (tiles of 64 or 32 columns also fit two CTAs per SM, one CTA's epilogue
   // then overlapping the other's MMAs).
   const int bn = pick_bn(m, n, lower);
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms <= 0) sms = 148;
+  const int sms = device_sm_count();
   // more tiles than SMs: persistent CTAs with the epilogue of one tile under the MMAs of the next
   if (bn >= 128) {
     const long long nt = active_tiles(m, n, lower, bn);

@@ -232,6 +232,18 @@ cudaError_t launch_fill_spd_uniform(double* A, int lda, int n, unsigned long lon
   return cudaGetLastError();
 }
 
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cached[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   (void)launch_pdl(fill_int_kernel, dim3((count + 255) / 256), dim3(256), 0, s, p, v, count);
