@@ -50,6 +50,48 @@ def leaf_traffic():
     return LEAF_TRAFFIC["bytes"] if ok else None
 
 
+class Replicas:
+    """One process per GPU (torchrun): RANK, WORLD_SIZE and LOCAL_RANK come from the
+    environment.  The replicas share no data; the process group (NCCL on the GPUs, gloo in the
+    CPU tests) only brackets the timed region with barriers and combines the per-rank figures:
+    the max of the times, the sum of the work."""
+
+    def __init__(self, backend="nccl", device=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if device is not None else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.dist is not None else None)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.dist is not None else None)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def tuned_fp64_tree(h, hrp, n):
     """The plain FP64 tree with the recursion cut-offs hrp_autotune picks at order n (one timed
     run per candidate), so the comparison is with the fastest FP64 configuration, not a fixed one."""
@@ -186,8 +228,10 @@ def run_batched(args, rank, world):
     import paper_2601_08082_gb300 as hrp
     from synth import rbf_spd, rhs, seed_for, uniforms
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    h = hrp.Handle(0)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    h = hrp.Handle(local)
     batch = args.batch
     u = uniforms(seed_for(3, 0), 7, np.arange(batch * world, dtype=np.uint64))
     sizes = [int(64 + np.floor(x * (2048 - 64 + 1))) for x in u[rank * batch:(rank + 1) * batch]]
@@ -230,6 +274,7 @@ def run_batched(args, rank, world):
     times = []
     for rep in range(args.warmup + args.steps):
         torch.cuda.synchronize()
+        reps.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -238,7 +283,10 @@ def run_batched(args, rank, world):
         torch.cuda.synchronize()
         if rep >= args.warmup:
             times.append(e0.elapsed_time(e1))
-    ms = sum(times) / len(times)
+    # every rank solves its own batch (weak scaling): the job's work over the slowest rank
+    ms = reps.max(sum(times) / len(times))
+    flops_rank = flops
+    flops = reps.sum(flops_rank)
     worst = max(out["resid"])
     # per-matrix loop of the FP64 tree (the comparison named by the workload)
     t64 = hrp.tree_parse("[F64]", leaf=64)
@@ -252,7 +300,7 @@ def run_batched(args, rank, world):
         h.potrs(A, B)
     e1.record()
     torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1)
+    ms64 = reps.max(e0.elapsed_time(e1))
     line = {"metric": METRIC + " (batched)", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 (fp32 acc) / f32 / f64", "data": "synthetic",
@@ -264,6 +312,7 @@ def run_batched(args, rank, world):
             "systems_refactored_with_fallback": int(sum(out["used_fallback"])),
             "max_refinement_rounds": int(max(out["iters"])), "worst_solution_residual": worst,
             "graph_factor_solve_ms": sum(gtimes) / len(gtimes), "graph_systems_failing_mixed_tree": len(failed)}
+    reps.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -283,6 +332,7 @@ def run_fp8posv(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    reps = Replicas("nccl", device=torch.device("cuda", local))
     n, nrhs, rho, spec = args.n3, 16, 2.0, "[F8,F16,F16,F32|F64@128]"
     g = torch.Generator(device="cuda")
     g.manual_seed(2601008082 + 2000 + rank)
@@ -302,6 +352,7 @@ def run_fp8posv(args, rank, world):
 
     def timed(fn):
         torch.cuda.synchronize()
+        reps.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -332,9 +383,11 @@ def run_fp8posv(args, rank, world):
         Af.copy_(A)
         _, t64 = timed(lambda: h.potrf_async(tree64, Af, d_info, stream=stream))
         fp64 = {"ms": t64, "tflops": n ** 3 / 3.0 / (t64 * 1e-3) / 1e12, "tree": FP64_TREE, **tune64}
-    ms = statistics.median(tf)
+    # every rank factors its own matrix (weak scaling): the job's work over the slowest rank
+    ms = reps.max(statistics.median(tf))
     flops = n ** 3 / 3.0
-    line = {"metric": METRIC + " (n=32768 FP8 posv)", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+    line = {"metric": METRIC + " (n=32768 FP8 posv)", "value": world * flops / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "e4m3 (in f16 storage) / f16 (fp32 acc) / f32 / f64", "data": "synthetic (device generator)",
@@ -347,6 +400,7 @@ def run_fp8posv(args, rank, world):
                      "tflops_incl_refinement": flops / (statistics.median(tp) * 1e-3) / 1e12},
             "fp64_tree": fp64, "speedup_vs_fp64_tree": (fp64["ms"] / ms) if fp64 else None,
             "clocks": clk.summary()}
+    reps.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -385,14 +439,10 @@ def main():
     from synth import dominant_spd, rhs, seed_for
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas("nccl", device=torch.device("cuda", local))
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
     # inputs: one matrix per rho, generated on the host (same bits as the oracle sees)
@@ -436,11 +486,7 @@ def main():
             launches += step(s)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reps.max(e0.elapsed_time(e1))
     infos = d_info.cpu().tolist()
     assert all(i == 0 for i in infos), infos
     value = world * args.steps * flops / (ms * 1e-3) / 1e12
@@ -552,8 +598,7 @@ def main():
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
     h.close()
     return 0
 
