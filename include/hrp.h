@@ -46,7 +46,7 @@ typedef enum {
   HRP_ERR_ALLOC = 4,           /* device or host allocation failed */
   HRP_ERR_CUDA = 5,            /* a CUDA call failed; hrp_last_error() has the text */
   HRP_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired (no trap, context usable) */
-  HRP_ERR_UNSUPPORTED = 7,     /* valid request this build does not implement */
+  HRP_ERR_UNSUPPORTED = 7,     /* valid request the library does not implement */
   HRP_ERR_RANGE = 8            /* input outside the range an FP16 tree handles without alpha > 1 */
 } hrp_status;
 
@@ -192,8 +192,8 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
                         float* ms, void* stream);
 
 /*
- * Batched factorization of `batch` independent systems (BASELINE's many-systems
- * workload; the paper factors one matrix at a time).  Host arrays: trees[i] (the tree of
+ * Batched factorization of `batch` independent systems (a many-systems workload; the
+ * paper factors one matrix at a time).  Host arrays: trees[i] (the tree of
  * system i; entries may share one tree; F8 levels are not batched), n[i], dA[i] (device
  * pointer), lda[i].  d_info: DEVICE array of batch ints, info of each system as in
  * hrp_potrf.  Each system runs the recursion of Alg. 1-3 on one stream of an internal
@@ -210,7 +210,7 @@ hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* con
                              int nrhs, double* const* dB, const int* ldb, void* stream);
 
 /*
- * Learned precision policy (not in the paper; BASELINE's learned part).  A small network
+ * Learned precision policy (not in the paper; an extension of it).  A small network
  * (MLP 12 -> 64 -> 64 -> 8, ReLU, FP32) maps cheap matrix features to one of eight
  * candidate trees (hrp_policy_tree); hrp_posv with tree == NULL uses it, and falls back
  * to the conservative tree (index 0, "[F32|F64@128]") when the chosen factorization fails.

@@ -1,6 +1,6 @@
 """Rounding to the reduced precisions used by the precision tree, and block scaling.
 
-Sec. 3.3 assigns FP16 (and, in this build's large configuration, FP8 E4M3) to
+Sec. 3.3 assigns FP16 (and, in the large FP8 configuration, FP8 E4M3) to
 the off-diagonal GEMM operands; Sec. 3.4 rescales each operand block into the
 format's range before the low-precision product and scales the result back.
 

@@ -1,6 +1,6 @@
 """Oracle for the learned precision policy: matrix features, Lanczos, and the MLP.
 
-Not in the paper (a BASELINE extension): a small network predicts the precision tree
+Not in the paper (an extension of it): a small network predicts the precision tree
 from cheap matrix features.  Definitions written here in float64 numpy:
 
 * Features of a symmetric A (lower triangle read as symmetric), in this order:

@@ -331,7 +331,7 @@ struct Fact {
 
 hrp_status cuda_status(hrp_handle* h, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return HRP_OK;
-  if (e == cudaErrorNotSupported) return set_err(h, HRP_ERR_UNSUPPORTED, "%s: precision not supported by this build", where);
+  if (e == cudaErrorNotSupported) return set_err(h, HRP_ERR_UNSUPPORTED, "%s: precision not supported by this library", where);
   return set_err(h, HRP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 

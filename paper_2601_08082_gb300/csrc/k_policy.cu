@@ -1,6 +1,6 @@
 // Learned precision policy: matrix features, Lanczos, and the MLP 12 -> 64 -> 64 -> 8
 // (forward, softmax cross-entropy gradient, Adam step), all in FP32 except the FP64
-// matrix passes.  Not in the paper: a BASELINE extension that predicts the precision tree.
+// matrix passes.  Not in the paper: an extension that predicts the precision tree.
 //
 // Features (same order and definitions as the oracle): log2 n; min / mean / fraction > 1
 // of the row dominance ratios r_i = a_ii / sum_{j!=i} |a_ij|; log10 ||A||_F; log10 of
