@@ -110,6 +110,14 @@ int potrs_epochs(int nrhs);
 // ---------------- utilities (k_util.cu) ----------------
 // SM count of the current device, queried once per device
 int device_sm_count();
+// Function attributes (the opt-in shared memory size) belong to the current device.  A launch
+// site keeps a mask of the devices it has configured; dev_bit() is the current device's bit
+// (0 for devices >= 64, which are then configured on every call).
+inline unsigned long long dev_bit() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 0ull;
+  return 1ull << d;
+}
 cudaError_t launch_fill_int(int* p, int v, int count, cudaStream_t s);
 // seeded SPD test matrix: off-diagonal entries uniform in [-1, 1) (symmetric), n on the
 // diagonal (strictly diagonally dominant); n <= 65535

@@ -436,12 +436,13 @@ cudaError_t launch_persistent(double* C, int ldc, const __half* S, int lds, int 
   CUtensorMap mx, my;
   if (!make_map(&mx, S + (size_t)xr0 * lds + k0, m, k, lds, TC_BM)) return cudaErrorInvalidValue;
   if (!make_map(&my, S + (size_t)yr0 * lds + k0, n, k, lds, BN)) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(gemm_f16_tc_persistent<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TcLayout<BN>::bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_mask |= attr_bit;
   }
   const int grid = (int)std::min<long long>(ntiles, sms);
   (void)launch_pdl(gemm_f16_tc_persistent<BN>, dim3(grid), dim3(TC_THREADS), TcLayout<BN>::bytes, s, mx, my, C, ldc, m, n, k, lower ? 1 : 0,
@@ -455,12 +456,13 @@ cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int
   CUtensorMap mx, my;
   if (!make_map(&mx, S + (size_t)xr0 * lds + k0, m, k, lds, TC_BM)) return cudaErrorInvalidValue;
   if (!make_map(&my, S + (size_t)yr0 * lds + k0, n, k, lds, BN)) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(gemm_f16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TcLayout<BN>::bytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_mask |= attr_bit;
   }
   dim3 grid((m + TC_BM - 1) / TC_BM, (n + BN - 1) / BN);
   (void)launch_pdl(gemm_f16_tc_kernel<BN>, dim3(grid), dim3(TC_THREADS), TcLayout<BN>::bytes, s, mx, my, C, ldc, m, n, k, lower ? 1 : 0,

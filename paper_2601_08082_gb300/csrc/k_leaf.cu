@@ -427,14 +427,15 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
   if (n > 128) return cudaErrorInvalidValue;
   if (compute64 && !round16 && n > 32) return launch_potrf_leaf_cluster(A, ld, n, col0, W32, ldw, info, s);
   const size_t smem = W32 ? (size_t)2 * 128 * kInvLD * 4 : 0;
-  static bool attr_done = false;     // one opt-in to the largest footprint (n = 128, with W)
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;     // one opt-in to the largest footprint (n = 128, with W)
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     const int maxb = (int)((size_t)2 * 128 * kInvLD * 4);
     cudaError_t e = cudaFuncSetAttribute(potrf_leaf_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(potrf_leaf_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   if (compute64)
     (void)launch_pdl(potrf_leaf_kernel<double>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
@@ -449,12 +450,13 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = nc <= 128 ? 64 : 32;
   size_t smem = ((size_t)nc * nc + (size_t)RT * nc) * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(((size_t)144 * 144 + (size_t)32 * 144) * sizeof(double)));
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
   (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
@@ -468,12 +470,13 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = 64;
   size_t smem = ((size_t)nc * nc + (size_t)RT * nc) * sizeof(float);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(((size_t)144 * 144 + (size_t)64 * 144) * sizeof(float)));
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
   (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
@@ -486,8 +489,9 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 128) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(trsm_inv32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -499,7 +503,7 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
       e = cudaFuncSetAttribute(trsm_inv32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)((128 * 36 + kT32Rows * kT32WLD) * 4));
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   // row tiles of 16; panels with fewer row tiles than SMs split their columns over 2 or 4
   // CTAs (each then stages only its slice of W)

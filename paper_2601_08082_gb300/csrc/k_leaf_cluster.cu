@@ -557,12 +557,13 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
                                       cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 128) return cudaErrorInvalidValue;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(potrf_leaf_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(ClusterLeafSmem));
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(ClusterLeafSmem), s, A, ld, n, col0, W32, ldw, info);
   return cudaGetLastError();

@@ -191,13 +191,14 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
                     int epoch, unsigned* err, cudaStream_t s) {
   const int nb = (n + PB - 1) / PB;
   const size_t smem = 2 * sizeof(T) * PB * (PB + 1);
-  static bool attr_done = false;
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
   cudaError_t e;
-  if (!attr_done) {
+  if (!(attr_mask & attr_bit)) {
     if ((e = cudaFuncSetAttribute(potrs_diag_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   potrs_diag_inverse_kernel<T><<<nb, PT, smem, s>>>(L, ldl, n, W);
   e = cudaGetLastError();

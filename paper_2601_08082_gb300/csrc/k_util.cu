@@ -462,11 +462,12 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if ((r0 % 128) || (c0 % 128) || nc != 128) return cudaErrorInvalidValue;
   const size_t smem = (size_t)128 * kQLD * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(quant_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   (void)launch_pdl(quant_e4m3_kernel, dim3((m + 127) / 128), dim3(kQThreads), smem, s, A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
@@ -478,12 +479,13 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
   if (nt < 2) return cudaSuccess;
   if (off % kQT) return cudaErrorInvalidValue;
   const size_t smem = (size_t)128 * kQLD * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static unsigned long long attr_mask = 0;
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask & attr_bit)) {
     cudaError_t e =
         cudaFuncSetAttribute(quant_e4m3_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    attr_mask |= attr_bit;
   }
   (void)launch_pdl(quant_e4m3_lower_kernel, dim3(nt * (nt - 1) / 2), dim3(kQThreads), smem, s, A, ld, off, nb, S8, lds, tile_exp, ntile_ld, G,
                                                                     err);
