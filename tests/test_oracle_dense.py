@@ -80,6 +80,31 @@ def test_exact_rational_small(n):
         np.testing.assert_allclose(Lh, Lexp, rtol=1e-14, atol=1e-15 * np.abs(Lexp).max())
 
 
+def test_exhaustive_small_integer_matrices():
+    # every 2 x 2 with a21 in -3..3 and a_ii = |a21| + t (t = 1..3), and every 3 x 3 with the
+    # three off-diagonal entries in -3..3 and a_ii = 1 + sum_{j!=i} |a_ij|: the factor against
+    # exact rational LDL^T
+    cases = []
+    for a21 in range(-3, 4):
+        for t1 in range(1, 4):
+            for t2 in range(1, 4):
+                cases.append(np.array([[abs(a21) + t1, a21], [a21, abs(a21) + t2]], dtype=np.int64))
+    for a21 in range(-3, 4):
+        for a31 in range(-3, 4):
+            for a32 in range(-3, 4):
+                A = np.array([[0, a21, a31], [a21, 0, a32], [a31, a32, 0]], dtype=np.int64)
+                np.fill_diagonal(A, np.abs(A).sum(axis=1) + 1)
+                cases.append(A)
+    assert len(cases) == 63 + 343
+    for A in cases:
+        n = A.shape[0]
+        Lu, D = _rational_ldl(A)
+        Lexp = np.array([[float(Lu[i][j]) * np.sqrt(float(D[j])) for j in range(n)] for i in range(n)])
+        Lh, info = dense.cholesky(A.astype(float))
+        assert info == 0
+        np.testing.assert_allclose(Lh, Lexp, rtol=4e-16 * n, atol=4e-16 * n * np.abs(Lexp).max())
+
+
 @pytest.mark.parametrize("n", [1, 17, 64, 129, 300])
 def test_recovers_known_factor(n):
     L = known_factor(n, seed_for(90, n))
