@@ -111,59 +111,83 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling (200 ms) during the timed region."""
+    """nvidia-smi sampling during the timed region.  The sampler is started and its first
+    sample awaited before the region opens (nvidia-smi takes a few hundred milliseconds to
+    start), and one sample after the region closes is awaited before it stops, so that the
+    samples inside the region and the two that bracket it are always on record.  All waits
+    are bounded; without nvidia-smi the summary has no samples."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, period_ms: int = 200, cmd=None, start_timeout_s: float = 5.0):
         self.device = device
+        self.period = period_ms / 1e3
+        self.cmd = cmd or ["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                           "--format=csv,noheader,nounits", "-lms", str(period_ms)]
+        self.start_timeout = start_timeout_s
         self.proc = None
-        self.lines = []
+        self.lines = []                  # (monotonic time of arrival, line)
+        self.t0 = self.t1 = None
+
+    def _wait_for(self, pred, timeout):
+        end = time.monotonic() + timeout
+        while not pred() and time.monotonic() < end:
+            if self.proc is not None and self.proc.poll() is not None:
+                break
+            time.sleep(0.01)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self._wait_for(lambda: len(self.lines) > 0, self.start_timeout)
         except Exception:
             self.proc = None
+        self.t0 = time.monotonic()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def __exit__(self, *a):
+        self.t1 = time.monotonic()
         if self.proc:
+            self._wait_for(lambda: any(t > self.t1 for t, _ in self.lines), 4 * self.period + 1.0)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _parse(line):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 8:
+            return None
+        try:
+            return float(parts[0]), float(parts[1]), parts[4:8]
+        except ValueError:
+            return None
+
     def summary(self):
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        rows = [(t, r) for t, ln in self.lines for r in [self._parse(ln)] if r is not None]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "in_region": 0}
+        t0 = self.t0 if self.t0 is not None else rows[0][0]
+        t1 = self.t1 if self.t1 is not None else rows[-1][0]
+        inside = [r for t, r in rows if t0 <= t <= t1]
+        before = [r for t, r in rows if t < t0][-1:]
+        after = [r for t, r in rows if t > t1][:1]
+        use = before + inside + after
+        sm = [r[0] for r in use]
+        reasons = {nm for r in use for nm, v in zip(names, r[2]) if v.lower().startswith("active")}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in use), "reasons": sorted(reasons),
+                "samples": len(use), "in_region": len(inside)}
 
 
 def cpu_oracle_sample(n_s: int = 3072, rho: float = 2.0, mats=None, budget_s: float = 10.0):
@@ -410,7 +434,7 @@ def run_fp8posv(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hrp", choices=["hrp", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)

@@ -1,0 +1,76 @@
+"""Host logic of bench.py on the CPU: the clock sampler against a fake nvidia-smi (the
+samples inside the timed region and the two that bracket it are kept, throttle reasons are
+collected, every wait is bounded), and the roofline denominators read from the measured
+peaks file."""
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _fake_smi(rows, period_s=0.03, delay_s=0.0):
+    """A stand-in for nvidia-smi --query-gpu ... -lms: prints one CSV row every period_s."""
+    script = ("import sys, time\n"
+              f"time.sleep({delay_s})\n"
+              f"rows = {rows!r}\n"
+              "i = 0\n"
+              "while True:\n"
+              "    print(rows[min(i, len(rows) - 1)], flush=True)\n"
+              "    i += 1\n"
+              f"    time.sleep({period_s})\n")
+    return [sys.executable, "-c", script]
+
+
+NORMAL = "2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+CAPPED = "1890, 2070, 1395.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+THERMAL = "1500, 2070, 1100.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active"
+
+
+def test_samples_inside_and_around_the_region():
+    with bench.Clocks(0, period_ms=30, cmd=_fake_smi([NORMAL], delay_s=0.2)) as clk:
+        assert clk.lines, "the first sample is awaited before the region opens"
+        time.sleep(0.2)
+    s = clk.summary()
+    assert s["in_region"] >= 3 and s["samples"] >= s["in_region"] + 1
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == []
+
+
+def test_throttle_reasons_are_collected():
+    rows = [NORMAL] * 3 + [CAPPED] * 3 + [THERMAL] * 100
+    with bench.Clocks(0, period_ms=30, cmd=_fake_smi(rows)) as clk:
+        time.sleep(0.4)
+    s = clk.summary()
+    assert "sw_power_cap" in s["reasons"] and "hw_thermal_slowdown" in s["reasons"]
+    assert s["sm_mhz"] < 2070.0
+
+
+def test_short_region_keeps_the_bracketing_samples():
+    # a region shorter than the sampling period still has the sample before and after it
+    with bench.Clocks(0, period_ms=200, cmd=_fake_smi([NORMAL], period_s=0.2)) as clk:
+        pass
+    s = clk.summary()
+    assert s["samples"] >= 2 and s["sm_mhz"] == 2070.0
+
+
+def test_missing_or_silent_sampler_does_not_hang():
+    t = time.monotonic()
+    with bench.Clocks(0, cmd=["/nonexistent/nvidia-smi"]) as clk:
+        pass
+    assert clk.summary()["samples"] == 0
+    with bench.Clocks(0, cmd=[sys.executable, "-c", "pass"], start_timeout_s=1.0) as clk:
+        pass
+    assert clk.summary()["samples"] == 0
+    assert time.monotonic() - t < 10.0
+
+
+def test_peaks_come_from_the_measured_file_when_present():
+    p = bench.peaks()
+    assert set(p) >= {"hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "src"}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert p["src"] == "measured" and p["hbm_gbs"] > 1000 and p["bf16_tflops"] > 100
+    else:
+        assert p["src"] == "fallback"
