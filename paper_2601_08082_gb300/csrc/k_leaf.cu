@@ -296,12 +296,13 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
 
 // ---------------------------------------------------------------------------------------
 // Leaf TRSM in FP32 through the inverse of the diagonal block: X = fl32(B) W^T with
-// W = fl32(L)^{-1} precomputed by the leaf POTRF.  One CTA owns 16 full rows of the
-// panel (so reading B and writing X in place never race): 256 threads, warp w the rows
-// 2w and 2w + 1, lane c the columns 4c .. 4c + 3; per k one 16-byte load of W(4c.., k) and
-// one broadcast of B(row, k) per row feed 8 FMAs.  Small CTAs (about 76 KB of shared
-// memory, two per SM) keep many rows in flight: the kernel is bound by the latency of its
-// dependent FMA chains, not by bandwidth.
+// W = fl32(L)^{-1} precomputed by the leaf POTRF.  A tile of 16 rows is computed by 256
+// threads: warp w the rows 2w and 2w + 1, each lane CPL consecutive columns; per k one load
+// of W (16 bytes for CPL = 4) and one broadcast of B(row, k) per row feed 2 CPL FMAs.  With
+// CPL = 4 one CTA owns the tile's 128 columns (about 76 KB of shared memory, two CTAs per
+// SM); panels with fewer tiles than SMs use CPL = 2 or 1 and split the columns over a cluster
+// of 2 or 4 CTAs.  The kernel is bound by the latency of its dependent FMA chains and of
+// staging W, not by bandwidth.
 // ---------------------------------------------------------------------------------------
 constexpr int kT32Rows = 16;
 constexpr int kT32Threads = 256;
