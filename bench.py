@@ -50,6 +50,15 @@ def leaf_traffic():
     return LEAF_TRAFFIC["bytes"] if ok else None
 
 
+def forward_error_colmajor(Lm, L64):
+    """||L_hat - L||_F / ||L||_F for two factors held column-major as (n, ld) tensors, storage
+    row c = matrix column c: the factors' lower triangles are the storage's upper triangles
+    (the strict lower part of the storage holds the untouched input)."""
+    import torch
+    ref = torch.triu(L64)
+    return float(torch.linalg.norm(torch.triu(Lm) - ref) / torch.linalg.norm(ref))
+
+
 class Replicas:
     """One process per GPU (torchrun): RANK, WORLD_SIZE and LOCAL_RANK come from the
     environment.  The replicas share no data; the process group (NCCL on the GPUs, gloo in the
@@ -574,6 +583,23 @@ def main():
             torch.cuda.synchronize()
             t64.append(a.elapsed_time(b))
         fp64 = {"ms": min(t64), "tflops": flops / (min(t64) * 1e-3) / 1e12, "tree": FP64_TREE, **tune64}
+        # forward error of the mixed factor against the FP64 tree's on the same matrix, and the
+        # solve alone (POTRS, 1 RHS); reported when they can be taken, never failing the line
+        try:
+            i = (args.fp64_steps - 1) % len(RHOS)          # tmp holds the FP64 factor of A0[i]
+            fp64["forward_error_mixed"] = forward_error_colmajor(copies[i], tmp)
+            fp64["forward_error_rho"] = RHOS[i]
+            Bx = hrp.colmajor(bvec).cuda()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.potrs(copies[i], Bx, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp64["potrs_ms"] = a.elapsed_time(b)
+        except Exception as exc:                           # pragma: no cover (GPU only)
+            fp64["extra_error"] = repr(exc)
 
     # end to end through the C ABI with host buffers: H2D(A, b) + potrf + potrs + D2H(x)
     e2e = None

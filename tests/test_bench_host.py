@@ -74,3 +74,16 @@ def test_peaks_come_from_the_measured_file_when_present():
         assert p["src"] == "measured" and p["hbm_gbs"] > 1000 and p["bf16_tflops"] > 100
     else:
         assert p["src"] == "fallback"
+
+
+def test_forward_error_of_column_major_factors_ignores_the_upper_input():
+    import numpy as np
+    import paper_2601_08082_gb300.hrp as hrp
+    rng = np.random.default_rng(3)
+    n = 9
+    L = np.tril(rng.standard_normal((n, n))) + 3 * np.eye(n)
+    D = np.tril(rng.standard_normal((n, n))) * 1e-3
+    M1 = L + np.triu(rng.standard_normal((n, n)), 1)        # strict upper: untouched input
+    M2 = (L + D) + np.triu(rng.standard_normal((n, n)), 1)  # different garbage there
+    fe = bench.forward_error_colmajor(hrp.colmajor(M2), hrp.colmajor(M1))
+    assert abs(fe - np.linalg.norm(D) / np.linalg.norm(L)) <= 1e-12
