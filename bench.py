@@ -50,6 +50,21 @@ def leaf_traffic():
     return LEAF_TRAFFIC["bytes"] if ok else None
 
 
+def lpt_partition(costs, world):
+    """Longest processing time first: the items, by decreasing cost (ties by index), each go
+    to the rank with the least load so far (ties by rank).  Returns each rank's item indices in
+    increasing order.  Graham's bound: the largest load is at most 4/3 of the optimum."""
+    import heapq
+    loads = [(0.0, r) for r in range(world)]
+    heapq.heapify(loads)
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda j: (-costs[j], j)):
+        load, r = heapq.heappop(loads)
+        parts[r].append(i)
+        heapq.heappush(loads, (load + costs[i], r))
+    return [sorted(p) for p in parts]
+
+
 def forward_error_colmajor(Lm, L64):
     """||L_hat - L||_F / ||L||_F for two factors held column-major as (n, ld) tensors, storage
     row c = matrix column c: the factors' lower triangles are the storage's upper triangles
@@ -266,15 +281,19 @@ def run_batched(args, rank, world):
     reps = Replicas("nccl", device=torch.device("cuda", local))
     h = hrp.Handle(local)
     batch = args.batch
+    # the job's batch * world systems, shared among the ranks by LPT on n^3 (each rank then
+    # holds about `batch` systems and the same share of the work)
     u = uniforms(seed_for(3, 0), 7, np.arange(batch * world, dtype=np.uint64))
-    sizes = [int(64 + np.floor(x * (2048 - 64 + 1))) for x in u[rank * batch:(rank + 1) * batch]]
-    mats = [rbf_spd(n, seed_for(3, 1 + rank * batch + i)) for i, n in enumerate(sizes)]
+    all_sizes = [int(64 + np.floor(x * (2048 - 64 + 1))) for x in u]
+    mine = lpt_partition([float(n) ** 3 for n in all_sizes], world)[rank]
+    sizes = [all_sizes[g] for g in mine]
+    mats = [rbf_spd(all_sizes[g], seed_for(3, 1 + g)) for g in mine]
     A0 = [hrp.colmajor(A).cuda() for A in mats]
-    B0 = [hrp.colmajor(rhs(n, 4, seed_for(3, 10000 + rank * batch + i))).cuda() for i, n in enumerate(sizes)]
+    B0 = [hrp.colmajor(rhs(all_sizes[g], 4, seed_for(3, 10000 + g))).cuda() for g in mine]
     As = [A.clone() for A in A0]
     Bs = [B.clone() for B in B0]
     tree = hrp.tree_parse(args.batch_tree, leaf=128)
-    d_info = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    d_info = torch.zeros(len(mine), dtype=torch.int32, device="cuda")
     h.potrf_batched(tree, As, d_info)
     h.potrs_batched(As, Bs)
     torch.cuda.synchronize()
@@ -316,7 +335,8 @@ def run_batched(args, rank, world):
         torch.cuda.synchronize()
         if rep >= args.warmup:
             times.append(e0.elapsed_time(e1))
-    # every rank solves its own batch (weak scaling): the job's work over the slowest rank
+    # every rank solves its LPT share (weak scaling: batch systems per rank on average): the
+    # job's work over the slowest rank
     ms = reps.max(sum(times) / len(times))
     flops_rank = flops
     flops = reps.sum(flops_rank)
@@ -337,9 +357,11 @@ def run_batched(args, rank, world):
     line = {"metric": METRIC + " (batched)", "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 (fp32 acc) / f32 / f64", "data": "synthetic",
-            "config": {"workload": f"{batch} RBF systems n~U[64,2048], 4 RHS, tree {args.batch_tree}, batched posv "
+            "config": {"workload": f"{batch * world} RBF systems n~U[64,2048] over {world} rank(s) by LPT on n^3, "
+                                   f"4 RHS, tree {args.batch_tree}, batched posv "
                                    "with FP32/FP64 fallback and FP64 refinement",
-                       "batch": batch, "sum_n3_over_3": flops, "tree": args.batch_tree},
+                       "batch": batch * world, "systems_rank0": len(mine), "sum_n3_over_3": flops,
+                       "tree": args.batch_tree},
             "fp64_loop": {"ms": ms64, "tflops": flops / (ms64 * 1e-3) / 1e12},
             "speedup_vs_fp64_loop": ms64 / ms, "status": out["status"],
             "systems_refactored_with_fallback": int(sum(out["used_fallback"])),

@@ -87,3 +87,22 @@ def test_forward_error_of_column_major_factors_ignores_the_upper_input():
     M2 = (L + D) + np.triu(rng.standard_normal((n, n)), 1)  # different garbage there
     fe = bench.forward_error_colmajor(hrp.colmajor(M2), hrp.colmajor(M1))
     assert abs(fe - np.linalg.norm(D) / np.linalg.norm(L)) <= 1e-12
+
+
+def test_lpt_partition_covers_every_system_once_and_balances_the_work():
+    import numpy as np
+    rng = np.random.default_rng(7)
+    n = rng.integers(64, 2049, size=2048)
+    costs = [float(x) ** 3 for x in n]
+    for world in (1, 2, 4, 8):
+        parts = bench.lpt_partition(costs, world)
+        assert len(parts) == world
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(costs)))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        # Graham: LPT <= 4/3 OPT, and OPT >= max(mean load, largest item)
+        opt_lb = max(sum(costs) / world, max(costs))
+        assert max(loads) <= 4.0 / 3.0 * opt_lb
+        assert max(loads) - min(loads) <= max(costs)      # list scheduling: within one item
+    assert bench.lpt_partition([5.0, 5.0, 5.0], 2) == [[0, 2], [1]]   # ties by index, then rank
+    assert bench.lpt_partition([], 3) == [[], [], []]
