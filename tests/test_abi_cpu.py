@@ -105,3 +105,27 @@ def test_autotune_rejects_bad_arguments_without_a_gpu(lib):
     t.leaf = 0
     assert lib.hrp_autotune_candidates(ctypes.byref(t), None, 0) == -1
     assert lib.hrp_autotune(None, ctypes.byref(t), 64, 1, 0, ctypes.byref(hrp.Tree()), None, None) != 0
+
+
+def _prototypes():
+    """name -> number of parameters, from the prototypes in include/hrp.h."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(hrp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        args = m.group(2).strip()
+        depth, n = 0, (0 if args in ("", "void") else 1)
+        for ch in args:
+            depth += ch == "("
+            depth -= ch == ")"
+            n += ch == "," and depth == 0
+        out[m.group(1)] = n
+    return out
+
+
+def test_binding_declares_every_prototype_with_its_arity(lib):
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    for name, nargs in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, f"{name}: no argtypes in the binding"
+        assert len(argtypes) == nargs, (name, len(argtypes), nargs)
