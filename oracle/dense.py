@@ -40,13 +40,20 @@ def cholesky(A: np.ndarray, dtype=np.float64) -> tuple[np.ndarray, int]:
 
 
 def trsm_rlt(B: np.ndarray, L: np.ndarray, dtype=np.float64) -> np.ndarray:
-    """X = B L^{-T} for lower-triangular L, by column substitution in ``dtype``."""
+    """X = B L^{-T} for lower-triangular L, by column substitution in ``dtype``.
+
+    Each row is an independent substitution x_j = (b_j - sum_{k<j} x_k l_jk) / l_jj; the
+    sum of a row is reduced along that row alone, so a row's result does not depend on
+    which other rows are solved in the same call (a matrix-vector product would let the
+    library's blocking, and with it the rounding order, vary with the number of rows).
+    """
     B = np.asarray(B).astype(dtype)
     L = np.tril(np.asarray(L)).astype(dtype)
     m, n = B.shape
     X = np.zeros((m, n), dtype=dtype)
     for j in range(n):
-        X[:, j] = (B[:, j] - X[:, :j] @ L[j, :j]) / L[j, j]
+        s = np.sum(X[:, :j] * L[j, :j], axis=1, dtype=dtype) if j else np.zeros(m, dtype=dtype)
+        X[:, j] = (B[:, j] - s) / L[j, j]
     return X.astype(np.float64)
 
 

@@ -77,12 +77,12 @@ def test_level_flop_shares_closed_form():
 # independent left-looking formulation with per-term precision
 # ---------------------------------------------------------------------------------------
 def _leaves_and_nodes(n, t):
-    """Leaf ranges, and for each internal node its (depth, order, split index)."""
+    """Leaf ranges with their depth, and for each internal node its (depth, order, split index)."""
     leaves, nodes = [], []
 
     def walk(off, m, depth):
         if m <= t.leaf:
-            leaves.append((off, m))
+            leaves.append((off, m, depth))
             return
         m1 = tree.split(m)
         nodes.append((off, m, depth, off + m1))
@@ -116,16 +116,30 @@ def _round(p, X, M=None, r0=0, c0=0, sb=128):
     return q * s
 
 
-def left_looking_reference(A, t):
+def _leaf_potrf_at(p, S):
+    """Diagonal leaf of precision p (the tree's reading of a leaf POTRF at that level)."""
+    if p == "F64":
+        return dense.cholesky(S)
+    if p == "F32":
+        return dense.cholesky(lowprec.round_f32(S), np.float32)
+    L, info = dense.cholesky(lowprec.round_f16(S), np.float32)
+    return lowprec.round_f16(L), info
+
+
+def left_looking_reference(A, t, leaf_compute="F64"):
+    """Left-looking block Cholesky over the tree's leaves, every update term l_ik l_jk
+    rounded at the precision of the shallower separating node.  leaf_compute="F64" runs
+    every leaf in FP64; None runs each diagonal leaf at its own node's precision and each
+    off-diagonal leaf solve in FP32 when its separating node is not F64."""
     n = A.shape[0]
     leaves, nodes = _leaves_and_nodes(n, t)
     L = np.zeros((n, n))
-    for J, (j0, nj) in enumerate(leaves):
+    for J, (j0, nj, dj) in enumerate(leaves):
         for I in range(J, len(leaves)):
-            i0, ni = leaves[I]
+            i0, ni, _ = leaves[I]
             S = np.array(np.tril(A)[i0:i0 + ni, j0:j0 + nj]) if I == J else np.array(A[i0:i0 + ni, j0:j0 + nj])
             for K in range(J):
-                k0, nk = leaves[K]
+                k0, nk, _ = leaves[K]
                 njk = _separating_node(nodes, k0, j0)
                 if I == J:
                     node = njk
@@ -137,12 +151,37 @@ def left_looking_reference(A, t):
                 Xj = _round(p, L[j0:j0 + nj, k0:k0 + nk], L, j0, k0)
                 S -= Xi @ Xj.T
             if I == J:
-                Lj, info = dense.cholesky(S)
+                p = "F64" if leaf_compute == "F64" else tree.node_prec(t, dj, nj)
+                Lj, info = _leaf_potrf_at(p, S)
                 assert info == 0
                 L[j0:j0 + nj, j0:j0 + nj] = Lj
             else:
-                L[i0:i0 + ni, j0:j0 + nj] = dense.trsm_rlt(S, L[j0:j0 + nj, j0:j0 + nj])
+                nij = _separating_node(nodes, j0, i0)
+                p = tree.node_prec(t, nij[0], nij[1])
+                dt = np.float64 if (p == "F64" or leaf_compute == "F64") else np.float32
+                L[i0:i0 + ni, j0:j0 + nj] = dense.trsm_rlt(S, L[j0:j0 + nj, j0:j0 + nj], dt)
     return L
+
+
+def _leaf_solves_are_per_leaf(n, t):
+    """True when every leaf TRSM of Alg. 2 covers the columns of exactly one POTRF leaf:
+    a node's A21 has more rows than the TRSM base case, or its A11 is itself one leaf.
+    (Otherwise one FP32 substitution spans several leaves, which the per-leaf left-looking
+    order does not model.)"""
+    ok = True
+
+    def walk(m):
+        nonlocal ok
+        if m <= t.leaf:
+            return
+        m1 = tree.split(m)
+        if not (m - m1 > t.tleaf() or m1 <= t.leaf):
+            ok = False
+        walk(m1)
+        walk(m - m1)
+
+    walk(n)
+    return ok
 
 
 @pytest.mark.parametrize("spec,n,leaf", [
@@ -208,3 +247,131 @@ def test_fp8_level_uses_tile_scales():
     # E4M3 keeps 3 mantissa bits: the error is far above FP16's but bounded
     assert 1e-5 < be < 5e-2
     assert any(c[0] == "F8" for c in em.gemm_calls)
+
+
+# ---------------------------------------------------------------------------------------
+# FP32 (and FP16) leaves: the emulator's reduced-precision leaf POTRF and leaf TRSM
+# ---------------------------------------------------------------------------------------
+FP32_LEAF_CASES = [
+    ("[F32]", 384, 64),
+    ("[F16,F32]", 384, 64),
+    ("[F16,F16,F32|F64@64]", 640, 64),
+    ("[F16,F16,F16,F32|F64@128]", 1024, 128),
+    ("[F16]", 384, 64),
+]
+
+
+@pytest.mark.parametrize("spec,n,leaf", FP32_LEAF_CASES)
+def test_emulator_reduced_precision_leaves_match_left_looking(spec, n, leaf):
+    """With every leaf at its tree precision, the independent left-looking order must
+    reproduce the emulator (both take each leaf's input from float64 sums of the same
+    rounded terms, so only their float64 order differs), and both must sit far from the
+    same tree with FP64 leaves (the FP32 leaf arithmetic is really there)."""
+    t = tree.parse(spec, leaf=leaf)
+    assert _leaf_solves_are_per_leaf(n, t)
+    A = dominant_spd(n, 1.05, seed_for(1, n))
+    L_emu, info, _ = tree.emulate_potrf(A, t)
+    assert info == 0
+    L_ref = left_looking_reference(A, t, leaf_compute=None)
+    L_f64leaves, _, _ = tree.emulate_potrf(A, t, leaf_compute="F64")
+    d_ref = np.linalg.norm(L_emu - L_ref)
+    d_leaf = np.linalg.norm(L_emu - L_f64leaves)
+    assert d_leaf > 1e-9 * np.linalg.norm(L_ref)
+    assert d_ref <= 1e-4 * d_leaf, (d_ref, d_leaf)
+
+
+def test_a_leaf_computed_in_fp64_is_detected():
+    """Plausible mistake: an F32 diagonal leaf (or an FP32 leaf solve) evaluated in
+    float64.  The left-looking FP32-leaf reference must reject both."""
+    t = tree.parse("[F16,F32]", leaf=64)
+    n = 384
+    A = dominant_spd(n, 1.05, seed_for(1, n))
+    L_ref = left_looking_reference(A, t, leaf_compute=None)
+
+    class LeafF64(tree.Emulator):
+        def _leaf_potrf(self, off, nb, p):
+            super()._leaf_potrf(off, nb, "F64" if p == "F32" else p)
+
+    class SolveF64(tree.Emulator):
+        def _leaf_trsm(self, r0, m, c0, nc, p):
+            B = self.M[r0:r0 + m, c0:c0 + nc]
+            self.M[r0:r0 + m, c0:c0 + nc] = dense.trsm_rlt(B, self.M[c0:c0 + nc, c0:c0 + nc])
+
+    L_ok, _, _ = tree.emulate_potrf(A, t)
+    d_ok = np.linalg.norm(L_ok - L_ref)
+    for cls in (LeafF64, SolveF64):
+        em = cls(A, t)
+        em.potrf(0, em.n, 0)
+        d_bad = np.linalg.norm(np.tril(em.M) - L_ref)
+        assert d_bad > 1e3 * d_ok, (cls.__name__, d_bad, d_ok)
+
+
+def _f32_exact(x):
+    return np.array_equal(np.asarray(x, np.float64), np.asarray(x, np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 64, 128])
+def test_fp32_cholesky_is_single_precision_arithmetic(n):
+    """dense.cholesky(., float32), the emulator's F32 leaf: every entry of L is a float32
+    value; the entrywise backward error meets Higham's bound for Cholesky in floating point
+    (Thm. 10.3: |A - L L^T| <= gamma_{n+1} |L| |L^T|, u = 2^-24); and on a generic matrix
+    it is not the float64 factor rounded once (most entries differ from that rounding,
+    since a float32 sum accumulates several roundings)."""
+    A = dominant_spd(n, 1.05, seed_for(1, 500 + n), shift=1.0)
+    A32 = lowprec.round_f32(A)
+    L, info = dense.cholesky(A, np.float32)
+    assert info == 0 and _f32_exact(L)
+    u = 2.0 ** -24
+    g = (n + 1) * u / (1 - (n + 1) * u)
+    R = np.abs(np.tril(A32) - np.tril(L @ L.T))
+    assert np.all(R <= g * np.tril(np.abs(L) @ np.abs(L).T) + 1e-300)
+    if n >= 64:
+        L64r = lowprec.round_f32(dense.cholesky(A32)[0])
+        low = np.tril_indices(n)
+        assert np.mean(L[low] != L64r[low]) > 0.1
+
+
+def test_fp32_cholesky_recovers_an_exact_factor():
+    """L with power-of-two diagonal and small integer entries: A = L L^T and every
+    intermediate of the column formula are integers below 2^24 (or exact quotients by a
+    power of two), so single-precision arithmetic returns L exactly."""
+    n = 48
+    rng = np.random.default_rng(seed_for(1, 600))
+    L = np.tril(rng.integers(-3, 4, (n, n)).astype(np.float64), -1)
+    np.fill_diagonal(L, 2.0 ** rng.integers(0, 3, n))
+    A = L @ L.T
+    assert np.max(np.abs(A)) < 2 ** 24
+    L32, info = dense.cholesky(A, np.float32)
+    assert info == 0 and np.array_equal(L32, L)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 16), (70, 64), (300, 128)])
+def test_fp32_trsm_is_single_precision_arithmetic(m, n):
+    """dense.trsm_rlt(., float32), the emulator's FP32 leaf solve X = B L^{-T}: float32
+    entries; each row meets the triangular-solve backward bound (Higham Thm. 8.5:
+    |b - x L^T| <= gamma_n |x| |L^T| with u = 2^-24); not the float64 solve rounded once;
+    and a row's result does not depend on the other rows solved with it."""
+    rng = np.random.default_rng(seed_for(1, 700 + n))
+    L = lowprec.round_f32(np.tril(rng.standard_normal((n, n))) / np.sqrt(n) + 2.0 * np.eye(n))
+    B = lowprec.round_f32(rng.standard_normal((m, n)))
+    X = dense.trsm_rlt(B, L, np.float32)
+    assert _f32_exact(X)
+    u = 2.0 ** -24
+    g = n * u / (1 - n * u)
+    assert np.all(np.abs(B - X @ L.T) <= g * (np.abs(X) @ np.abs(L).T) + 1e-300)
+    if m * n >= 4000:
+        X64r = lowprec.round_f32(dense.trsm_rlt(B, L))
+        assert np.mean(X != X64r) > 0.1
+    if m > 3:
+        assert np.array_equal(dense.trsm_rlt(B[2:m - 1], L, np.float32), X[2:m - 1])
+
+
+def test_fp32_trsm_recovers_an_exact_solution():
+    n, m = 40, 30
+    rng = np.random.default_rng(seed_for(1, 800))
+    L = np.tril(rng.integers(-2, 3, (n, n)).astype(np.float64), -1)
+    np.fill_diagonal(L, 2.0 ** rng.integers(0, 3, n))
+    X = rng.integers(-4, 5, (m, n)).astype(np.float64)
+    B = X @ L.T
+    assert np.max(np.abs(B)) < 2 ** 24
+    assert np.array_equal(dense.trsm_rlt(B, L, np.float32), X)
