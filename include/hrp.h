@@ -195,7 +195,10 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
  * Batched factorization of `batch` independent systems (a many-systems workload; the
  * paper factors one matrix at a time).  Host arrays: trees[i] (the tree of
  * system i; entries may share one tree; F8 levels are not batched), n[i], dA[i] (device
- * pointer), lda[i].  d_info: DEVICE array of batch ints, info of each system as in
+ * pointer), lda[i].  trees == NULL, or trees[i] == NULL: the learned policy chooses that
+ * system's tree (hrp_policy_predict on its features, F8 levels taken in FP16; the
+ * fallback tree when no policy is loaded); the feature pass synchronizes `stream`, so
+ * such a call cannot be captured in a graph.  d_info: DEVICE array of batch ints, info of each system as in
  * hrp_potrf.  Each system runs the recursion of Alg. 1-3 on one stream of an internal
  * pool forked from `stream` (longest systems first) and joined back into it; the call only
  * enqueues work (capturable into one CUDA graph once the workspace for these sizes exists).
@@ -227,8 +230,14 @@ hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* con
  *   gradient of the mean softmax cross-entropy and *d_loss the loss; Adam with
  *   beta = (0.9, 0.999), eps 1e-8, bias-corrected at step `step` (1-based).  Asynchronous.
  * hrp_policy_set: install trained parameters (host arrays) and the input standardization
- *   (mean[12], scale[12]); hrp_policy_predict: index of the predicted tree for host
- *   feat[12]; hrp_last_policy_choice: the index hrp_posv chose last (-1 if a tree was given).
+ *   (mean[12], scale[12]).
+ * hrp_policy_load: the same from a file written by train_policy.py (JSON, format
+ *   "hrp-policy-v1": "trees" must be this library's 8 candidate trees in order, "params"
+ *   5512 numbers, "mean" and "scale" 12 each); HRP_ERR_INVALID_ARG (with hrp_last_error)
+ *   when the file is missing or does not match.
+ * hrp_policy_predict: the predicted tree for host feat[12] into *out and its index into
+ *   *index (either may be NULL, not both); HRP_ERR_INVALID_ARG when no policy is loaded.
+ * hrp_last_policy_choice: the index hrp_posv chose last (-1 if a tree was given).
  */
 hrp_status hrp_policy_features(hrp_handle* h, int n, const double* dA, int lda, int lanczos_steps, float* feat,
                                void* stream);
@@ -240,14 +249,16 @@ hrp_status hrp_mlp_adam(hrp_handle* h, float* d_params, const float* d_grad, flo
                         float lr, void* stream);
 int hrp_mlp_param_count(void);
 hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean, const float* scale);
-hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index);
+hrp_status hrp_policy_load(hrp_handle* h, const char* path);
+hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, hrp_tree* out, int* index);
 hrp_status hrp_policy_tree(int index, hrp_tree* out);
 int hrp_last_policy_choice(const hrp_handle* h);
 
 /*
  * Batched hrp_posv: for each system i (host arrays as in hrp_potrf_batched, plus dB[i],
- * ldb[i], dX[i], ldx[i]; 1 <= nrhs <= 16): factor a copy of A_i with trees[i] (dA[i] is not
- * modified), refactor with "[F32|F64@128]" where that fails (used_fallback[i] = 1), solve,
+ * ldb[i], dX[i], ldx[i]; 1 <= nrhs <= 16): factor a copy of A_i with trees[i] (NULL: the
+ * policy's choice, as above; dA[i] is not modified), refactor with "[F32|F64@128]" where
+ * that fails or needs alpha > 1 (used_fallback[i] = 1), solve,
  * and refine in FP64 until ||b - A x||_2 / ||b||_2 <= tol per column or max_iter.  All
  * systems advance together, one round of refinement at a time, on the internal stream
  * pool.  info, iters, resid, used_fallback: host arrays of batch entries (may be NULL).
@@ -260,6 +271,27 @@ hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees, int bat
 
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);
+
+/*
+ * Device-side status.  Kernels record failures that only the device sees in the handle's
+ * status word: a bounded wait that expired (POTRS sweeps; the tcgen05 GEMM pipeline) and
+ * an operand outside the FP16 / E4M3 range.  Synchronous calls read and clear it before
+ * they return; asynchronous calls (hrp_potrf_async, hrp_potrs, the batched calls) leave it
+ * for the next synchronous call or for hrp_check.
+ * hrp_check: synchronizes `stream`, reads and clears the word; returns HRP_ERR_TIMEOUT,
+ *   HRP_ERR_RANGE or HRP_OK.
+ * hrp_set_wait_limit: the limit of the bounded waits in the handle's solves (POTRS
+ *   sweeps), 1 us .. 2 s (the default).  A sweep whose wait expires writes NaN into the
+ *   rows it could not solve and publishes them, so dependent rows come out NaN too.
+ * hrp_wait_selftest: one device thread waits, through the sweeps' bounded-wait routine,
+ *   on a device flag that nothing sets, for `microseconds` (1 .. 2e6); the wait expires,
+ *   the kernel records the timeout and returns, and the call reports HRP_ERR_TIMEOUT with
+ *   *waited_us (host, may be NULL) the time the device waited.  The context stays usable.
+ *   Synchronous.
+ */
+hrp_status hrp_check(hrp_handle* h, void* stream);
+hrp_status hrp_set_wait_limit(hrp_handle* h, long long microseconds);
+hrp_status hrp_wait_selftest(hrp_handle* h, long long microseconds, double* waited_us, void* stream);
 
 /*
  * hrp_potrs_noalloc: the same solve as hrp_potrs (B <- A^{-1} B from the factor in the
@@ -278,7 +310,10 @@ long long hrp_last_launch_count(const hrp_handle* h);
  *     before any stream capture.  Later calls only enqueue work on `stream`.
  *   - All calls share the one array: calls that overlap on the GPU (different streams,
  *     no ordering between them) race and must not be issued.
- *   - A bounded device wait that expires is recorded in the array, not reported here.
+ *   - The call only enqueues work, so it cannot return a device-side failure: a bounded
+ *     device wait that expires inside a sweep (it gives up after 2 s) leaves NaN in the
+ *     rows of dB it could not solve and in every row that depends on them.  Check the
+ *     result for NaN where that matters.
  */
 hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
                              void* stream);

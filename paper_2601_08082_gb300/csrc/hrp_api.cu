@@ -37,7 +37,9 @@ struct hrp_handle_s {
   int* d_ticket = nullptr;
   int* d_flags = nullptr;
   size_t flags_cap = 0;
-  int epoch = 1;
+  int* d_epoch = nullptr;      // POTRS epoch counter (advanced on the device by every solve)
+  int* d_probe = nullptr;      // a flag nothing sets (hrp_wait_selftest) and the time waited
+  unsigned long long wait_ns = hrp::kWaitTimeoutNs;   // limit of the solves' bounded waits
   __half* shadow = nullptr;
   size_t shadow_cap = 0;       // elements
   float* w32 = nullptr;
@@ -223,7 +225,7 @@ struct Fact {
       leaves[off] = nb;
     }
     begin(CLS_POTRF, (double)nb * nb * nb / 3.0);
-    chk(launch_potrf_leaf(A + (size_t)off * lda + off, lda, nb, off, p == HRP_F64, p == HRP_F16, W, 128, info, s));
+    chk(launch_potrf_leaf(A + (size_t)off * lda + off, lda, nb, off, p == HRP_F64, p == HRP_F16, W, 128, info, h->d_err, s));
   }
 
   void leaf_trsm(int r0, int m, int c0, int nc, int p) {
@@ -231,16 +233,16 @@ struct Fact {
     __half* sh = shadow;
     begin(CLS_TRSM, (double)m * nc * nc);
     if (p == HRP_F64 || t->trsm_compute == 1) {
-      chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
+      chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, h->d_err, s));
       quant8(r0, m, c0, nc, p);
       return;
     }
     auto it = leaves.find(c0);
     if (w32 && it != leaves.end() && it->second == nc) {
       chk(launch_trsm_leaf32(Ab, lda, r0, m, c0, nc, w32 + (size_t)c0 * 128, 128, sh, lds, shadow32, ld32, info,
-                             s));
+                             h->d_err, s));
     } else {
-      chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, s));
+      chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, h->d_err, s));
     }
     quant8(r0, m, c0, nc, p);
   }
@@ -418,10 +420,37 @@ hrp_status check_dev_err(hrp_handle* h, cudaStream_t s) {
     cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s);
     return set_err(h, HRP_ERR_RANGE, "an E4M3 tile fell outside the exact FP16 storage window");
   }
+  if (e & DEV_ERR_RANGE16) {
+    cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s);
+    return set_err(h, HRP_ERR_RANGE,
+                   "an FP16 operand exceeds 65504: the Sec. 3.4 scale alpha would be > 1 (use an F32 tree)");
+  }
   return HRP_OK;
 }
 
 }  // namespace
+
+// The learned policy's tree for the system (n, dA, lda): its features, the network's choice
+// (index 0, the fallback tree, when no policy is loaded), with F8 levels taken in FP16 when
+// n is not 128 * 2^k or when no_f8 (the batched calls do not run F8 levels).  Synchronous.
+hrp_status policy_choose(hrp_handle* h, int n, const double* dA, int lda, bool no_f8, hrp_tree* out, int* idx,
+                         void* stream) {
+  int k = 0;
+  if (h->policy_set) {
+    float feat[12];
+    hrp_status fs = hrp_policy_features(h, n, dA, lda, kPolicyLanczosSteps, feat, stream);
+    if (fs != HRP_OK) return fs;
+    if ((fs = hrp_policy_predict(h, feat, nullptr, &k)) != HRP_OK) return fs;
+  }
+  hrp_policy_tree(k, out);
+  const bool pow2 = n >= 128 && n % 128 == 0 && (((n / 128) & (n / 128 - 1)) == 0);
+  if (no_f8 || !pow2)
+    for (int i = 0; i < out->depth; ++i)
+      if (out->level[i] == HRP_F8E4M3) out->level[i] = HRP_F16;
+  if (idx) *idx = k;
+  return HRP_OK;
+}
+
 }  // namespace hrp
 
 using namespace hrp;
@@ -457,9 +486,13 @@ hrp_status hrp_create(hrp_handle** out, int device) {
   bool ok = cudaMalloc(&h->d_info, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_err, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&h->d_ticket, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_epoch, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_probe, 4 * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&h->d_norms, sizeof(double) * 128) == cudaSuccess &&
             cudaMallocHost(&h->h_norms, sizeof(double) * 128) == cudaSuccess;
-  if (!ok || cudaMemset(h->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+  if (!ok || cudaMemset(h->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->d_epoch, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_probe, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     hrp_destroy(h);
     return HRP_ERR_ALLOC;
   }
@@ -474,6 +507,8 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->d_info);
   cudaFree(h->d_err);
   cudaFree(h->d_ticket);
+  cudaFree(h->d_epoch);
+  cudaFree(h->d_probe);
   cudaFree(h->d_flags);
   cudaFree(h->shadow);
   cudaFree(h->w32);
@@ -605,26 +640,19 @@ hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int
 static hrp_status potrs_impl(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
                              bool fp32, cudaStream_t s) {
   hrp_status st;
-  size_t nb = (size_t)(n + 63) / 64;
   int* old_flags = h->d_flags;
   size_t old_cap = h->flags_cap;
-  if ((st = ensure(h, &h->d_flags, &h->flags_cap, nb)) != HRP_OK) return st;
+  if ((st = ensure(h, &h->d_flags, &h->flags_cap, potrs_flag_count(n))) != HRP_OK) return st;
   if (h->d_flags != old_flags || h->flags_cap != old_cap) {
-    // fresh flags must not hold a value equal to a future epoch
+    // fresh flags must not hold a value equal to a future epoch (epochs are >= 1)
     cudaError_t me = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->flags_cap, s);
     if (me != cudaSuccess) return cuda_status(h, me, "hrp_potrs");
-    h->epoch = 1;
   }
-  int ne = potrs_epochs(nrhs);
-  if (h->epoch > INT_MAX - 1024) {
-    cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->flags_cap, s);
-    h->epoch = 1;
-  }
-  int ep = h->epoch;
-  h->epoch += ne;
   if ((st = ensure(h, &h->pwork, &h->pwork_cap, potrs_workspace_bytes(n))) != HRP_OK) return st;
-  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->pwork, h->d_ticket, h->d_flags, ep, h->d_err, s);
-  h->launches += 1 + 2 * ne;
+  cudaError_t e =
+      launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->pwork, h->d_ticket, h->d_flags, h->d_epoch, h->d_err, s,
+                   h->wait_ns);
+  h->launches += 2 + potrs_epochs(nrhs);
   return cuda_status(h, e, "hrp_potrs");
 }
 
@@ -652,18 +680,8 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
   if (!tree && n > 0 && dA && lda >= n) {
     // no tree given: the learned policy picks one (the fallback tree if none is loaded)
     int idx = 0;
-    if (h->policy_set) {
-      float feat[12];
-      hrp_status fs = hrp_policy_features(h, n, dA, lda, kPolicyLanczosSteps, feat, stream);
-      if (fs != HRP_OK) return fs;
-      if ((fs = hrp_policy_predict(h, feat, &idx)) != HRP_OK) return fs;
-    }
-    // F8 trees need n = 128 * 2^k; otherwise take the same depth in FP16
-    hrp_policy_tree(idx, &chosen);
-    const bool pow2 = n >= 128 && n % 128 == 0 && (((n / 128) & (n / 128 - 1)) == 0);
-    if (!pow2)
-      for (int i = 0; i < chosen.depth; ++i)
-        if (chosen.level[i] == HRP_F8E4M3) chosen.level[i] = HRP_F16;
+    hrp_status fs = policy_choose(h, n, dA, lda, false, &chosen, &idx, stream);
+    if (fs != HRP_OK) return fs;
     h->last_choice = idx;
     tree = &chosen;
   }
@@ -706,6 +724,10 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
     e = cudaMemcpyAsync(&hinfo, h->d_info, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+    // an operand outside the FP16 (or E4M3 storage) range: the tree cannot factor this
+    // matrix without alpha > 1, so the fallback tree takes over
+    if ((st = check_dev_err(h, s)) == HRP_ERR_RANGE && attempt == 0) continue;
+    if (st != HRP_OK) return st;
     if (hinfo) continue;
     // X0 = POTRS(B) in FP32
     if ((e = launch_copy_matrix(dX, ldx, dB, ldb, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
@@ -726,6 +748,8 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
         double rb = h->h_norms[nrhs + c] > 0 ? sqrt(h->h_norms[c] / h->h_norms[nrhs + c]) : sqrt(h->h_norms[c]);
         if (!(rb <= worst)) worst = rb;   // NaN propagates
       }
+      // a solve whose bounded wait expired leaves NaN rows: report it, do not refine on
+      if (worst != worst && (st = check_dev_err(h, s)) != HRP_OK) return st;
       if (worst <= tol || it >= max_iter) break;
       if (!(worst < prev)) { diverged = true; break; }   // no decrease: this factor will not get there
       prev = worst;
@@ -901,6 +925,40 @@ int hrp_get_timing(hrp_handle* h, double* out, int n) {
 
 long long hrp_last_launch_count(const hrp_handle* h) { return h ? h->launches : 0; }
 
+hrp_status hrp_check(hrp_handle* h, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  return check_dev_err(h, static_cast<cudaStream_t>(stream));
+}
+
+hrp_status hrp_set_wait_limit(hrp_handle* h, long long microseconds) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (microseconds < 1 || microseconds > 2000000) return bad_arg(h, 2, "limit must be in [1, 2000000] us");
+  h->wait_ns = (unsigned long long)microseconds * 1000ull;
+  return HRP_OK;
+}
+
+hrp_status hrp_wait_selftest(hrp_handle* h, long long microseconds, double* waited_us, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (microseconds < 1 || microseconds > 2000000) return bad_arg(h, 2, "limit must be in [1, 2000000] us");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hrp_status st = check_dev_err(h, s);           // report what earlier calls left first
+  if (st != HRP_OK) return st;
+  // d_probe[0] (an int that stays 0) is the flag; d_probe[1] receives the time waited
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(h->d_probe) + 1;
+  cudaError_t e = cudaMemsetAsync(h->d_probe, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = launch_wait_probe(h->d_probe, (unsigned long long)microseconds * 1000ull, h->d_err, out, s);
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, out, sizeof(ns), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_wait_selftest");
+  if (waited_us) *waited_us = ns * 1e-3;
+  return check_dev_err(h, s);
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
@@ -933,7 +991,7 @@ hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<Sys
     w.shadow = need_factor_ws ? take((size_t)ni * w.lds * sizeof(__half)) : 0;
     w.w32 = need_factor_ws ? take(((size_t)ni * 128 + 128 * 128) * sizeof(float)) : 0;
     w.pinv = take(potrs_workspace_bytes(ni));
-    w.flags = take(sizeof(int) * (size_t)((ni + 63) / 64 + 1));
+    w.flags = take(sizeof(int) * (potrs_flag_count(ni) + 1));   // flags, then the epoch counter
     w.ticket = take(sizeof(int));
     w.fact = nrhs_ir ? take(sizeof(double) * (size_t)ni * ni) : 0;
     w.res = nrhs_ir ? take(sizeof(double) * (size_t)ni * nrhs_ir + sizeof(double) * 2 * nrhs_ir) : 0;
@@ -943,8 +1001,8 @@ hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<Sys
   hrp_status st = ensure(h, &h->bwork, &h->bwork_cap, off);
   if (st != HRP_OK) return st;
   if (h->bwork != old || h->bwork_cap != old_cap) {
+    // zero flags and epoch counters (and everything else) of the fresh workspace
     if (cudaMemset(h->bwork, 0, h->bwork_cap) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "batch workspace");
-    h->epoch = std::max(h->epoch, 1);
   }
   while ((int)h->bstreams.size() < kBatchStreams) {
     cudaStream_t st2;
@@ -990,6 +1048,31 @@ hrp_status join(hrp_handle* h, cudaStream_t s) {
   return HRP_OK;
 }
 
+hrp_status check_batch_args(hrp_handle* h, int batch, const int* n, double* const* dA, const int* lda);
+
+// The tree of every system: trees[i], or the learned policy's choice where trees (the
+// array) or trees[i] is NULL (F8 levels taken in FP16: the batched calls do not run them).
+hrp_status batch_trees(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n, double* const* dA,
+                       const int* lda, std::vector<hrp_tree>& chosen, std::vector<const hrp_tree*>& out,
+                       void* stream) {
+  chosen.assign(batch, hrp_tree{});
+  out.assign(batch, nullptr);
+  for (int i = 0; i < batch; ++i) {
+    if (trees && trees[i]) {
+      out[i] = trees[i];
+      continue;
+    }
+    if (n[i] > 0) {
+      hrp_status st = policy_choose(h, n[i], dA[i], lda[i], true, &chosen[i], nullptr, stream);
+      if (st != HRP_OK) return st;
+    } else {
+      hrp_policy_tree(0, &chosen[i]);
+    }
+    out[i] = &chosen[i];
+  }
+  return HRP_OK;
+}
+
 hrp_status check_batch_args(hrp_handle* h, int batch, const int* n, double* const* dA, const int* lda) {
   if (batch < 0) return bad_arg(h, 3, "batch < 0");
   if (batch > 0 && (!n || !dA || !lda)) return bad_arg(h, 4, "NULL array");
@@ -1006,14 +1089,17 @@ hrp_status check_batch_args(hrp_handle* h, int batch, const int* n, double* cons
 
 extern "C" {
 
-hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n, double* const* dA,
-                             const int* lda, int* d_info, void* stream) {
+hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees_in, int batch, const int* n,
+                             double* const* dA, const int* lda, int* d_info, void* stream) {
   if (!h) return HRP_ERR_INVALID_ARG;
   h->last_arg = 0;
-  if (batch > 0 && !trees) return bad_arg(h, 2, "trees is NULL");
   hrp_status st = check_batch_args(h, batch, n, dA, lda);
   if (st != HRP_OK) return st;
   if (batch > 0 && !d_info) return bad_arg(h, 7, "d_info is NULL");
+  std::vector<hrp_tree> chosen;
+  std::vector<const hrp_tree*> tv;
+  if ((st = batch_trees(h, trees_in, batch, n, dA, lda, chosen, tv, stream)) != HRP_OK) return st;
+  const hrp_tree* const* trees = tv.data();
   for (int i = 0; i < batch; ++i) {
     if ((st = validate_tree(h, trees[i], 2)) != HRP_OK) return st;
     if (tree_has(trees[i], HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "F8 levels are not batched");
@@ -1077,19 +1163,16 @@ hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* con
   if (batch == 0 || nrhs == 0) return HRP_OK;
   std::vector<int> which = lpt_assign(batch, n, kBatchStreams);
   if ((st = fork(h, s)) != HRP_OK) return st;
-  if (h->epoch > INT_MAX - 4096) h->epoch = 1;        // flags of every system are reset below
-  const int ep = h->epoch;
-  h->epoch += potrs_epochs(nrhs);
   cudaError_t err = cudaSuccess;
   long long launches = 0;
   for (int i = 0; i < batch; ++i) {
     if (n[i] == 0) continue;
     cudaStream_t si = h->bstreams[which[i]];
     int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
-    if (ep == 1) cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n[i] + 63) / 64 + 1), si);
     cudaError_t e = launch_potrs(dL[i], ldl[i], dB[i], ldb[i], n[i], nrhs, false, h->bwork + ws[i].pinv,
-                                 reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si);
-    launches += 1 + 2 * potrs_epochs(nrhs);
+                                 reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags,
+                                 flags + potrs_flag_count(n[i]), h->d_err, si, h->wait_ns);
+    launches += 2 + potrs_epochs(nrhs);
     if (e != cudaSuccess && err == cudaSuccess) err = e;
   }
   if ((st = join(h, s)) != HRP_OK) return st;
@@ -1116,6 +1199,50 @@ const char* kPolicyTrees[8] = {
     "[F8,F16,F32|F64@128]",
     "[F8,F16,F16,F16,F32|F64@128]",
 };
+
+// The array following "key": in a JSON text (the policy file's flat layout: one array of
+// numbers, or of strings without escapes, per key).  False if the key or the array is missing
+// or malformed.
+size_t json_array_start(const std::string& t, const char* key) {
+  const std::string k = std::string("\"") + key + "\"";
+  size_t p = t.find(k);
+  if (p == std::string::npos) return std::string::npos;
+  p = t.find_first_not_of(" \t\r\n", p + k.size());
+  if (p == std::string::npos || t[p] != ':') return std::string::npos;
+  p = t.find_first_not_of(" \t\r\n", p + 1);
+  if (p == std::string::npos || t[p] != '[') return std::string::npos;
+  return p + 1;
+}
+bool json_numbers(const std::string& t, const char* key, std::vector<float>& out) {
+  size_t p = json_array_start(t, key);
+  if (p == std::string::npos) return false;
+  out.clear();
+  const char* c = t.c_str() + p;
+  while (true) {
+    while (*c == ' ' || *c == ',' || *c == '\n' || *c == '\r' || *c == '\t') ++c;
+    if (*c == ']') return true;
+    char* end = nullptr;
+    const double v = strtod(c, &end);
+    if (end == c) return false;
+    out.push_back((float)v);
+    c = end;
+  }
+}
+bool json_strings(const std::string& t, const char* key, std::vector<std::string>& out) {
+  size_t p = json_array_start(t, key);
+  if (p == std::string::npos) return false;
+  out.clear();
+  while (true) {
+    p = t.find_first_not_of(" ,\t\r\n", p);
+    if (p == std::string::npos) return false;
+    if (t[p] == ']') return true;
+    if (t[p] != '"') return false;
+    const size_t q = t.find('"', p + 1);
+    if (q == std::string::npos) return false;
+    out.push_back(t.substr(p + 1, q - p - 1));
+    p = q + 1;
+  }
+}
 
 // number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count)
 int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
@@ -1290,9 +1417,10 @@ hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean,
   return HRP_OK;
 }
 
-hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index) {
+hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, hrp_tree* out, int* index) {
   if (!h) return HRP_ERR_INVALID_ARG;
-  if (!feat || !index) return bad_arg(h, 2, "NULL argument");
+  if (!feat) return bad_arg(h, 2, "feat is NULL");
+  if (!out && !index) return bad_arg(h, 3, "out and index are both NULL");
   if (!h->policy_set) return set_err(h, HRP_ERR_INVALID_ARG, "no policy loaded (hrp_policy_set)");
   cudaSetDevice(h->device);
   float z[8];
@@ -1303,13 +1431,49 @@ hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, int* index) {
   int best = 0;
   for (int i = 1; i < 8; ++i)
     if (z[i] > z[best]) best = i;
-  *index = best;
+  if (index) *index = best;
+  if (out) return hrp_policy_tree(best, out);
   return HRP_OK;
 }
 
 hrp_status hrp_policy_tree(int index, hrp_tree* out) {
   if (index < 0 || index >= 8 || !out) return HRP_ERR_INVALID_ARG;
   return hrp_tree_parse(kPolicyTrees[index], 128, out);
+}
+
+hrp_status hrp_policy_load(hrp_handle* h, const char* path) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (!path) return bad_arg(h, 2, "path is NULL");
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_err(h, HRP_ERR_INVALID_ARG, "cannot open %s", path);
+  std::string text;
+  char buf[65536];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  fclose(f);
+  if (text.find("\"hrp-policy-v1\"") == std::string::npos)
+    return set_err(h, HRP_ERR_INVALID_ARG, "%s: not an hrp-policy-v1 file", path);
+  // the candidate trees the weights were trained for must be this library's, in order
+  std::vector<std::string> trees;
+  if (!json_strings(text, "trees", trees) || trees.size() != 8)
+    return set_err(h, HRP_ERR_INVALID_ARG, "%s: \"trees\" must list 8 trees", path);
+  for (int i = 0; i < 8; ++i) {
+    hrp_tree a, b;
+    if (hrp_tree_parse(trees[i].c_str(), 128, &a) != HRP_OK || hrp_tree_parse(kPolicyTrees[i], 128, &b) != HRP_OK ||
+        memcmp(&a, &b, sizeof(a)) != 0)
+      return set_err(h, HRP_ERR_INVALID_ARG, "%s: tree %d is %s, this library's is %s", path, i, trees[i].c_str(),
+                     kPolicyTrees[i]);
+  }
+  std::vector<float> params, mean, scale;
+  if (!json_numbers(text, "params", params) || (int)params.size() != policy_nparam())
+    return set_err(h, HRP_ERR_INVALID_ARG, "%s: \"params\" must hold %d numbers", path, policy_nparam());
+  if (!json_numbers(text, "mean", mean) || mean.size() != 12 || !json_numbers(text, "scale", scale) ||
+      scale.size() != 12)
+    return set_err(h, HRP_ERR_INVALID_ARG, "%s: \"mean\" and \"scale\" must hold 12 numbers each", path);
+  for (float v : scale)
+    if (!(v > 0.f)) return set_err(h, HRP_ERR_INVALID_ARG, "%s: a scale is not positive", path);
+  return hrp_policy_set(h, params.data(), mean.data(), scale.data());
 }
 
 int hrp_last_policy_choice(const hrp_handle* h) { return h ? h->last_choice : -1; }
@@ -1319,17 +1483,20 @@ int hrp_last_policy_choice(const hrp_handle* h) { return h ? h->last_choice : -1
 // ---------------------------------------------------------------------------------------
 // Batched solve with FP64 iterative refinement (the many-systems counterpart of hrp_posv).
 // ---------------------------------------------------------------------------------------
-extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n,
+extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees_in, int batch, const int* n,
                                        double* const* dA, const int* lda, int nrhs, double* const* dB, const int* ldb,
                                        double* const* dX, const int* ldx, int max_iter, double tol, int* info,
                                        int* iters, double* resid, int* used_fallback, void* stream) {
   if (!h) return HRP_ERR_INVALID_ARG;
   h->last_arg = 0;
-  if (batch > 0 && !trees) return bad_arg(h, 2, "trees is NULL");
   hrp_status st = check_batch_args(h, batch, n, dA, lda);
   if (st != HRP_OK) return st;
   if (nrhs < 1 || nrhs > 16) return bad_arg(h, 7, "nrhs must be in [1, 16]");
   if (batch > 0 && (!dB || !ldb || !dX || !ldx)) return bad_arg(h, 8, "NULL B or X arrays");
+  std::vector<hrp_tree> chosen;
+  std::vector<const hrp_tree*> tv;
+  if ((st = batch_trees(h, trees_in, batch, n, dA, lda, chosen, tv, stream)) != HRP_OK) return st;
+  const hrp_tree* const* trees = tv.data();
   for (int i = 0; i < batch; ++i) {
     if ((st = validate_tree(h, trees[i], 2)) != HRP_OK) return st;
     if (tree_has(trees[i], HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "F8 levels are not batched");
@@ -1385,6 +1552,15 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
     if ((st = join(h, s)) != HRP_OK) break;
     note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
     note(cudaStreamSynchronize(s));
+    if (err != cudaSuccess) break;
+    st = check_dev_err(h, s);
+    if (st == HRP_ERR_RANGE && pass == 0) {
+      // some FP16 operand needs alpha > 1: the systems with FP16 levels take the fallback tree
+      st = HRP_OK;
+      for (int i = 0; i < batch; ++i)
+        if (n[i] > 0 && tree_has(trees[i], HRP_F16)) hinfo[i] = -1;
+    }
+    if (st != HRP_OK) break;
     bool any = false;
     for (int i = 0; i < batch; ++i) any |= hinfo[i] != 0;
     if (!any) break;
@@ -1393,23 +1569,22 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
   // X0 = POTRS(B) in FP32, then rounds of refinement over the systems not yet converged
   for (int it = 0; st == HRP_OK && err == cudaSuccess; ++it) {
     if ((st = fork(h, s)) != HRP_OK) break;
-    if (h->epoch > INT_MAX - 4096) h->epoch = 1;
-    const int ep = h->epoch;
-    h->epoch += potrs_epochs(nrhs);
     for (int i = 0; i < batch; ++i) {
       if (n[i] == 0 || hinfo[i] != 0 || done[i]) continue;
       cudaStream_t si = h->bstreams[which[i]];
       int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
-      if (ep == 1) note(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n[i] + 63) / 64 + 1), si));
+      int* ctr = flags + potrs_flag_count(n[i]);
       double* R = res_of(i);
       if (fresh[i]) {
         fresh[i] = 0;
         note(launch_copy_matrix(dX[i], ldx[i], dB[i], ldb[i], n[i], nrhs, si));
         note(launch_potrs(fact_of(i), n[i], dX[i], ldx[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
-                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si));
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ctr, h->d_err, si,
+                          h->wait_ns));
       } else {
         note(launch_potrs(fact_of(i), n[i], R, n[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
-                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ep, h->d_err, si));
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ctr, h->d_err, si,
+                          h->wait_ns));
         note(launch_axpy_matrix(dX[i], ldx[i], R, n[i], n[i], nrhs, si));
         ++its[i];
       }
@@ -1419,6 +1594,7 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
     if ((st = join(h, s)) != HRP_OK) break;
     note(cudaStreamSynchronize(s));
     if (err != cudaSuccess) break;
+    if ((st = check_dev_err(h, s)) != HRP_OK) break;       // a solve's bounded wait expired
     bool all = true;
     for (int i = 0; i < batch; ++i) {
       if (n[i] == 0 || hinfo[i] != 0 || done[i]) continue;
@@ -1472,6 +1648,7 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
       if ((st = join(h, s)) != HRP_OK) break;
       note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
       note(cudaStreamSynchronize(s));
+      if (err == cudaSuccess && (st = check_dev_err(h, s)) != HRP_OK) break;
       restart.clear();
     }
     if (all) break;

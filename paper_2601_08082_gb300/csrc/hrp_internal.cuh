@@ -15,7 +15,11 @@ enum : unsigned {
   DEV_ERR_TIMEOUT = 1u,     // a bounded wait expired
   DEV_ERR_BOUNDS = 2u,      // a checked index fell outside its buffer
   DEV_ERR_RANGE = 4u,       // an E4M3 tile fell outside the exact FP16 storage window
+  DEV_ERR_RANGE16 = 8u,     // an FP16 operand exceeded 65504 (Sec. 3.4 would need alpha > 1)
 };
+
+// Largest finite FP16 value, R_max of the Sec. 3.4 scaling rule alpha = max(1, amax / R_max)
+constexpr float kF16Max = 65504.0f;
 
 // Bounded device waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitTimeoutNs = 2000ull * 1000ull * 1000ull;
@@ -54,8 +58,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // If W32 != nullptr also writes the FP32 inverse of the (FP32-rounded) factor,
 // column-major n x n with leading dimension ldw.  info: device int, atomicMin of the
 // 1-based global column (col0 + k + 1) of the first failing pivot (INT_MAX = none).
+// err: device status word; an F16 leaf whose input or factor exceeds kF16Max sets
+// DEV_ERR_RANGE16.
 cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64, bool round16,
-                              float* W32, int ldw, int* info, cudaStream_t s);
+                              float* W32, int ldw, int* info, unsigned* err, cudaStream_t s);
 
 // The same FP64 leaf POTRF (no FP16 rounding) on a cluster of 8 CTAs holding 16 x 16
 // tiles in shared memory (k_leaf_cluster.cu); launch_potrf_leaf uses it for n > 32.
@@ -64,18 +70,21 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
 
 // Leaf TRSM B <- B L^{-T} with B = A[r0.., c0..] (m x nc) and L = A[c0.., c0..] (nc x nc),
 // in FP64 by substitution.  shadow16 (row-major, lds) receives FP16(X) and shadow32
-// (column-major, ld32, the master's indexing) FP32(X), each if non-null.
+// (column-major, ld32, the master's indexing) FP32(X), each if non-null.  An entry of X
+// beyond kF16Max written to shadow16 sets DEV_ERR_RANGE16 in err (the FP16 operand would
+// need the Sec. 3.4 scale alpha > 1).
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
-                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, cudaStream_t s);
+                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, unsigned* err,
+                               cudaStream_t s);
 // Same in FP32 using the precomputed FP32 inverse W (nc x nc lower, ldw) of the block:
 // X = fl32(B) * W^T, result stored in FP64.
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
-                               const int* info, cudaStream_t s);
+                               const int* info, unsigned* err, cudaStream_t s);
 // FP32 substitution variant (no inverse), for blocks whose inverse is not available.
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
                                      __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
-                                     cudaStream_t s);
+                                     unsigned* err, cudaStream_t s);
 
 // ---------------- SIMT GEMM (k_gemm_simt.cu) ----------------
 // C[m x n] -= X[m x k] * Y[n x k]^T, all FP64 column-major views of the master, with
@@ -100,11 +109,21 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds,
 // ---------------- POTRS (k_potrs.cu) ----------------
 // B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 or (fp32)
 // in FP32 on FP32-rounded L and B.  ticket: device int scratch; flags: device ints, one per
-// 64-row block; consumes potrs_epochs(nrhs) consecutive epoch values starting at `epoch`.
-// work: device scratch of potrs_workspace_bytes(n) (inverses of the 64 x 64 diagonal blocks).
+// 64-row block (potrs_flag_count(n), zero before first use); epoch_ctr: a device int (zero
+// before first use) that the solve's first kernel advances by potrs_epochs(nrhs), clearing
+// the flags when it would overflow.  work: device scratch of potrs_workspace_bytes(n)
+// (inverses of the 64 x 64 diagonal blocks).  A bounded wait that expires sets
+// DEV_ERR_TIMEOUT in dev_err and leaves NaN in the unsolved rows of B.
 cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32, void* work,
-                         int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s);
+                         int* ticket, int* flags, int* epoch_ctr, unsigned* dev_err, cudaStream_t s,
+                         unsigned long long wait_limit_ns = kWaitTimeoutNs);
+// One thread waits, through the sweeps' bounded wait, on *flag reaching 1 (the caller sees
+// that nothing sets it): after wait_limit_ns it sets DEV_ERR_TIMEOUT and writes the time it
+// waited (ns) to *waited_ns (device).
+cudaError_t launch_wait_probe(const int* flag, unsigned long long wait_limit_ns, unsigned* dev_err,
+                              unsigned long long* waited_ns, cudaStream_t s);
 size_t potrs_workspace_bytes(int n);
+size_t potrs_flag_count(int n);
 int potrs_epochs(int nrhs);
 
 // ---------------- utilities (k_util.cu) ----------------

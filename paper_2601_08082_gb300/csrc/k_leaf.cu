@@ -123,7 +123,7 @@ __device__ void trtri32_blocked(const float* __restrict__ Lf, float* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(256, 1)
 potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
-                  float* __restrict__ W32, int ldw, int* __restrict__ info) {
+                  float* __restrict__ W32, int ldw, int* __restrict__ info, unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -133,15 +133,20 @@ potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ti = tid & 15, tj = tid >> 4;
   T reg[8][8];
+  bool over16 = false;                               // an F16 value beyond kF16Max
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int i = ti + 16 * a, j = tj + 16 * b;
       double v = (i < n && j < n && i >= j) ? A[(size_t)j * ld + i] : 0.0;
-      if (round16) v = round_to_f16(v);
+      if (round16) {
+        over16 |= fabs(v) > (double)kF16Max;
+        v = round_to_f16(v);
+      }
       reg[a][b] = (T)v;
     }
+  if (round16 && __any_sync(0xffffffffu, over16) && lane == 0) atomicOr(err, DEV_ERR_RANGE16);
   if (tid == 0) s_fail = 0;
   __syncthreads();
 
@@ -204,10 +209,14 @@ potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
       const int i = ti + 16 * a, j = tj + 16 * b;
       if (i < n && j < n && i >= j) {
         double v = (double)reg[a][b];
-        if (round16) v = round_to_f16(v);              // F16 leaf: the stored factor is FP16
+        if (round16) {                                 // F16 leaf: the stored factor is FP16
+          over16 |= fabs(v) > (double)kF16Max;
+          v = round_to_f16(v);
+        }
         A[(size_t)j * ld + i] = v;
       }
     }
+  if (round16 && __any_sync(0xffffffffu, over16) && lane == 0) atomicOr(err, DEV_ERR_RANGE16);
   if (W32 == nullptr) return;
   __syncthreads();
 
@@ -241,7 +250,7 @@ template <typename T>
 __global__ void __launch_bounds__(64)
 trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32, const int* __restrict__ info,
-                  int rows_per_cta) {
+                  unsigned* __restrict__ err, int rows_per_cta) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -286,11 +295,17 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
     }
   }
   if (S != nullptr) {
+    bool over16 = false;
     for (int idx = tid; idx < RT * nc; idx += blockDim.x) {
       int k = idx % nc, t = idx / nc;
       int r = row0 + t;
-      if (r < m) S[(size_t)(r0 + r) * lds + (c0 + k)] = __double2half((double)Xs[k * RT + t]);
+      if (r < m) {
+        const double v = (double)Xs[k * RT + t];
+        over16 |= fabs(v) > (double)kF16Max;
+        S[(size_t)(r0 + r) * lds + (c0 + k)] = __double2half(v);
+      }
     }
+    if (__any_sync(0xffffffffu, over16) && (tid & 31) == 0) atomicOr(err, DEV_ERR_RANGE16);
   }
 }
 
@@ -326,7 +341,7 @@ template <int CPL>
 __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
-                  float* __restrict__ S32, int ld32, const int* __restrict__ info) {
+                  float* __restrict__ S32, int ld32, const int* __restrict__ info, unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   constexpr int C = 32 * CPL;
@@ -412,18 +427,24 @@ trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   }
   // FP16 shadow (row-major): consecutive columns of one row
   if (S != nullptr) {
+    bool over16 = false;
     for (int e = tid; e < ncol * kT32Rows; e += kT32Threads) {
       const int r = e / ncol, jj = e - r * ncol;
       const int gr = row0 + r;
-      if (gr < m) S[(size_t)(r0 + gr) * lds + (c0 + jc0 + jj)] = __float2half_rn(Bs[r * kT32WLD + jj]);
+      if (gr < m) {
+        const float v = Bs[r * kT32WLD + jj];
+        over16 |= fabsf(v) > kF16Max;
+        S[(size_t)(r0 + gr) * lds + (c0 + jc0 + jj)] = __float2half_rn(v);
+      }
     }
+    if (__any_sync(0xffffffffu, over16) && lane == 0) atomicOr(err, DEV_ERR_RANGE16);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64, bool round16,
-                              float* W32, int ldw, int* info, cudaStream_t s) {
+                              float* W32, int ldw, int* info, unsigned* err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (n > 128) return cudaErrorInvalidValue;
   if (compute64 && !round16 && n > 32) return launch_potrf_leaf_cluster(A, ld, n, col0, W32, ldw, info, s);
@@ -439,14 +460,15 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
     attr_mask |= attr_bit;
   }
   if (compute64)
-    (void)launch_pdl(potrf_leaf_kernel<double>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+    (void)launch_pdl(potrf_leaf_kernel<double>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info, err);
   else
-    (void)launch_pdl(potrf_leaf_kernel<float>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info);
+    (void)launch_pdl(potrf_leaf_kernel<float>, dim3(1), dim3(256), smem, s, A, ld, n, col0, round16 ? 1 : 0, W32, ldw, info, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
-                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, cudaStream_t s) {
+                               __half* shadow16, int lds, float* shadow32, int ld32, const int* info, unsigned* err,
+                               cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = nc <= 128 ? 64 : 32;
@@ -460,13 +482,13 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
     attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
-  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
+  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, err, RT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
                                      __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
-                                     cudaStream_t s) {
+                                     unsigned* err, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = 64;
@@ -480,13 +502,13 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
     attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
-  (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, RT);
+  (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, err, RT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
-                               const int* info, cudaStream_t s) {
+                               const int* info, unsigned* err, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 128) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
@@ -530,13 +552,13 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
   cudaError_t e;
   if (cpl == 4)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<4>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info);
+                           info, err);
   else if (cpl == 2)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<2>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info);
+                           info, err);
   else
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<1>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info);
+                           info, err);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -11,8 +11,16 @@
 //      flight; at the end y_r = W_r (b_r - sum_j L_rj y_j) is a small matrix product, so
 //      no division sits on the dependency chain between blocks.
 //   3. backward sweep, the same with L^T: x_r = W_r^T (y_r - sum_{j>r} L_jr^T x_j).
-// All waits are bounded by %globaltimer: on expiry the CTA records DEV_ERR_TIMEOUT and
-// stops instead of spinning forever.
+// Epochs: a block's ready flag holds the epoch of the sweep that solved it, so flags never
+// need clearing between sweeps.  The epochs come from a device counter that the first
+// kernel of every solve advances in stream order (and that clears the flags before the
+// counter would overflow), so a solve captured in a CUDA graph takes fresh epochs on every
+// replay.
+// All waits are bounded by %globaltimer: on expiry the CTA records DEV_ERR_TIMEOUT, writes
+// NaN into its own block of the solution and still publishes it, so blocks downstream turn
+// NaN as well instead of waiting in turn; no flag is left unpublished.
+#include <climits>
+
 #include "hrp_internal.cuh"
 
 namespace hrp {
@@ -35,7 +43,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ bool wait_flag(const int* flags, int j, int epoch) {
+// true once flags[j] == epoch; false when limit_ns of %globaltimer have passed first
+__device__ bool wait_flag(const int* flags, int j, int epoch, unsigned long long limit_ns) {
   if (ld_acquire(flags + j) == epoch) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
@@ -43,9 +52,38 @@ __device__ bool wait_flag(const int* flags, int j, int epoch) {
       if (ld_acquire(flags + j) == epoch) return true;
       __nanosleep(64);
     }
-    if (gtimer() - t0 > kWaitTimeoutNs) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
 }
+
+// One thread waits through wait_flag on *flag reaching 1, which nothing writes: the wait
+// must expire after limit_ns, record DEV_ERR_TIMEOUT and return.  out[0] = the time waited.
+__global__ void wait_probe_kernel(const int* flag, unsigned long long limit_ns, unsigned* err,
+                                  unsigned long long* out) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long t0 = gtimer();
+  if (!wait_flag(flag, 0, 1, limit_ns)) atomicOr(err, DEV_ERR_TIMEOUT);
+  out[0] = gtimer() - t0;
+}
+
+// ---- 0. epochs of this solve: epochs ctr + 1 .. ctr + ne, flags cleared on wrap-around ----
+__global__ void __launch_bounds__(256) potrs_epoch_kernel(int* __restrict__ ctr, int* __restrict__ flags, int nflags,
+                                                          int ne) {
+  __shared__ int s_base;
+  if (threadIdx.x == 0) {
+    int base = ctr[0] + 1;
+    if (base < 1 || base > INT_MAX - ne) base = -1;        // wrap: clear the flags first
+    s_base = base;
+  }
+  __syncthreads();
+  if (s_base < 0)
+    for (int i = threadIdx.x; i < nflags; i += blockDim.x) flags[i] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) ctr[0] = (s_base < 0 ? 1 : s_base) + ne - 1;
+}
+
+// epoch q (0-based) of the solve whose epochs end at ctr[0]
+__device__ __forceinline__ int solve_epoch(const int* ctr, int ne, int q) { return *(volatile const int*)ctr - ne + 1 + q; }
 
 // ---- 1. W_r = L_rr^{-1} for every 64-row diagonal block (one CTA each) ----
 template <typename T>
@@ -90,14 +128,15 @@ potrs_diag_inverse_kernel(const double* __restrict__ L, int ldl, int n, T* __res
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(PT)
 potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ W, double* __restrict__ B, int ldb,
-                   int n, int nrhs, int* __restrict__ ticket, int* __restrict__ flags, int epoch,
-                   unsigned* __restrict__ err) {
+                   int n, int nrhs, int* __restrict__ ticket, int* __restrict__ flags, const int* __restrict__ ctr,
+                   int ne, int q, unsigned* __restrict__ err, unsigned long long limit_ns) {
   __shared__ T yS[MAX_RHS][PB];          // solved block of another CTA; later the reduced rhs
   __shared__ T part[4][MAX_RHS][PB];     // per-chunk partial sums
   __shared__ int s_r, s_abort;
   T (*accS)[PB] = yS;
   const int tid = threadIdx.x;
   const int nb = (n + PB - 1) / PB;
+  const int epoch = solve_epoch(ctr, ne, q);
   if (tid == 0) {
     const int t = atomicAdd(ticket, 1);
     s_r = FWD ? t : nb - 1 - t;
@@ -131,12 +170,23 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
       if (FWD) lv[q] = (kk < jrows && i < rows) ? (T)L[(size_t)(J0 + kk) * ldl + R0 + i] : (T)0;
       else lv[q] = (kk < jrows && i < rows) ? (T)L[(size_t)(R0 + i) * ldl + J0 + kk] : (T)0;
     }
-    if (tid == 0 && !wait_flag(flags, j, epoch)) {
+    if (tid == 0 && !wait_flag(flags, j, epoch, limit_ns)) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       s_abort = 1;
     }
     __syncthreads();
-    if (s_abort) return;
+    if (s_abort) {
+      // this block cannot be solved: NaN marks it (and, through the products, every block
+      // that depends on it); publishing it spares those blocks a wait of their own
+      for (int idx = tid; idx < nrhs * PB; idx += PT) {
+        const int ii = idx % PB, c = idx / PB;
+        if (ii < rows) B[(size_t)c * ldb + R0 + ii] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release(flags + r, epoch);
+      return;
+    }
     for (int idx = tid; idx < nrhs * PB; idx += PT) {
       const int kk = idx % PB, c = idx / PB;
       yS[c][kk] = (kk < jrows) ? (T)__ldcg(B + (size_t)c * ldb + J0 + kk) : (T)0;
@@ -188,8 +238,9 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
 
 template <typename T>
 cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrhs, T* W, int* ticket, int* flags,
-                    int epoch, unsigned* err, cudaStream_t s) {
+                    int* ctr, unsigned* err, unsigned long long limit_ns, cudaStream_t s) {
   const int nb = (n + PB - 1) / PB;
+  const int ne = potrs_epochs(nrhs);
   const size_t smem = 2 * sizeof(T) * PB * (PB + 1);
   static unsigned long long attr_mask = 0;
   const unsigned long long attr_bit = dev_bit();
@@ -200,6 +251,8 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
       return e;
     attr_mask |= attr_bit;
   }
+  potrs_epoch_kernel<<<1, 256, 0, s>>>(ctr, flags, nb, ne);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   potrs_diag_inverse_kernel<T><<<nb, PT, smem, s>>>(L, ldl, n, W);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -207,12 +260,12 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
     const int nc = nrhs - c0 < MAX_RHS ? nrhs - c0 : MAX_RHS;
     double* Bc = B + (size_t)c0 * ldb;
     for (int pass = 0; pass < 2; ++pass) {
-      const int ep = epoch + 2 * (c0 / MAX_RHS) + pass;
+      const int q = 2 * (c0 / MAX_RHS) + pass;
       if ((e = cudaMemsetAsync(ticket, 0, sizeof(int), s)) != cudaSuccess) return e;
       if (pass == 0)
-        potrs_sweep_kernel<T, true><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ep, err);
+        potrs_sweep_kernel<T, true><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ctr, ne, q, err, limit_ns);
       else
-        potrs_sweep_kernel<T, false><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ep, err);
+        potrs_sweep_kernel<T, false><<<nb, PT, 0, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, flags, ctr, ne, q, err, limit_ns);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
@@ -224,12 +277,25 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
 size_t potrs_workspace_bytes(int n) { return (size_t)((n + PB - 1) / PB) * PB * PB * sizeof(double); }
 
 cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32, void* work,
-                         int* ticket, int* flags, int epoch, unsigned* dev_err, cudaStream_t s) {
+                         int* ticket, int* flags, int* epoch_ctr, unsigned* dev_err, cudaStream_t s,
+                         unsigned long long wait_limit_ns) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  if (fp32) return potrs_t<float>(L, ldl, B, ldb, n, nrhs, static_cast<float*>(work), ticket, flags, epoch, dev_err, s);
-  return potrs_t<double>(L, ldl, B, ldb, n, nrhs, static_cast<double*>(work), ticket, flags, epoch, dev_err, s);
+  if (fp32)
+    return potrs_t<float>(L, ldl, B, ldb, n, nrhs, static_cast<float*>(work), ticket, flags, epoch_ctr, dev_err,
+                          wait_limit_ns, s);
+  return potrs_t<double>(L, ldl, B, ldb, n, nrhs, static_cast<double*>(work), ticket, flags, epoch_ctr, dev_err,
+                         wait_limit_ns, s);
 }
 
-int potrs_epochs(int nrhs) { return 2 * ((nrhs + MAX_RHS - 1) / MAX_RHS); }
+cudaError_t launch_wait_probe(const int* flag, unsigned long long limit_ns, unsigned* dev_err,
+                              unsigned long long* waited_ns, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(flag, limit_ns, dev_err, waited_ns);
+  return cudaGetLastError();
+}
+
+// two sweeps per chunk of MAX_RHS columns (written without forming nrhs + MAX_RHS - 1)
+int potrs_epochs(int nrhs) { return 2 * (nrhs / MAX_RHS + (nrhs % MAX_RHS != 0)); }
+
+size_t potrs_flag_count(int n) { return (size_t)((n + PB - 1) / PB); }
 
 }  // namespace hrp

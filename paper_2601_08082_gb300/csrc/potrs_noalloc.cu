@@ -10,8 +10,11 @@
 // process exits.
 //
 // Scratch layout (kScratchBytes, fixed): inverses of the 64 x 64 diagonal blocks
-// (n_max x 64 doubles), one ready flag per 64-row block, the sweep ticket, an error word.
-#include <climits>
+// (n_max x 64 doubles), one ready flag per 64-row block, the sweep ticket, the epoch
+// counter of the sweeps (advanced on the device by every call) and an error word.
+// A bounded wait inside a sweep that expires leaves NaN in the rows of B it could not
+// solve (and, through the products, in every row that depends on them): that NaN is
+// how a caller of this entry point sees the failure.
 #include <mutex>
 
 #include "hrp_internal.cuh"
@@ -24,7 +27,8 @@ constexpr int kNoAllocBlocks = (kNoAllocMaxN + 63) / 64;             // 128 row 
 constexpr size_t kInvBytes = (size_t)kNoAllocBlocks * 64 * 64 * sizeof(double);   // 4 MiB
 constexpr size_t kFlagsOffset = kInvBytes;
 constexpr size_t kTicketOffset = kFlagsOffset + sizeof(int) * kNoAllocBlocks;
-constexpr size_t kErrOffset = kTicketOffset + sizeof(int);
+constexpr size_t kEpochOffset = kTicketOffset + sizeof(int);
+constexpr size_t kErrOffset = kEpochOffset + sizeof(int);
 constexpr size_t kScratchBytes = (kErrOffset + sizeof(unsigned) + 255) / 256 * 256;
 
 static __device__ __align__(256) unsigned char g_potrs_scratch[kScratchBytes];
@@ -32,7 +36,6 @@ static __device__ __align__(256) unsigned char g_potrs_scratch[kScratchBytes];
 struct DeviceScratch {
   bool ready = false;
   unsigned char* base = nullptr;   // device address of g_potrs_scratch on this device
-  int epoch = 1;
 };
 constexpr int kMaxDevices = 64;
 DeviceScratch g_dev[kMaxDevices];
@@ -55,33 +58,25 @@ extern "C" hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int l
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HRP_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int ep;
   unsigned char* base;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceScratch& d = g_dev[dev];
     if (!d.ready) {
       // once per device, with that device current: the device address of the array (its
-      // host-side name is only a stand-in) and zeroed flags (no flag may equal an epoch)
+      // host-side name is only a stand-in), then zeroed flags, ticket, epoch counter and
+      // error word (no flag may equal an epoch, and epochs start at 1)
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_potrs_scratch) != cudaSuccess) return HRP_ERR_CUDA;
       if (cudaMemset(static_cast<unsigned char*>(p) + kFlagsOffset, 0, kScratchBytes - kFlagsOffset) != cudaSuccess)
         return HRP_ERR_CUDA;
       d.base = static_cast<unsigned char*>(p);
-      d.epoch = 1;
       d.ready = true;
     }
-    if (d.epoch > INT_MAX - 4096) {
-      if (cudaMemsetAsync(d.base + kFlagsOffset, 0, sizeof(int) * kNoAllocBlocks, s) != cudaSuccess)
-        return HRP_ERR_CUDA;
-      d.epoch = 1;
-    }
-    ep = d.epoch;
-    d.epoch += potrs_epochs(nrhs);
     base = d.base;
   }
   cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, false, base, reinterpret_cast<int*>(base + kTicketOffset),
-                               reinterpret_cast<int*>(base + kFlagsOffset), ep,
+                               reinterpret_cast<int*>(base + kFlagsOffset), reinterpret_cast<int*>(base + kEpochOffset),
                                reinterpret_cast<unsigned*>(base + kErrOffset), s);
   return e == cudaSuccess ? HRP_OK : HRP_ERR_CUDA;
 }

@@ -32,7 +32,8 @@ EXPORTED = [
     "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched", "hrp_posv_batched",
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
-    "hrp_autotune_candidates", "hrp_autotune",
+    "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
+    "hrp_wait_selftest",
 ]
 
 
@@ -92,7 +93,11 @@ def load(path: str = LIB_PATH):
     L.hrp_mlp_adam.argtypes = [vp, vp, vp, vp, vp, c_int, ctypes.c_float, vp]
     L.hrp_mlp_param_count.argtypes = []
     L.hrp_policy_set.argtypes = [vp, fp, fp, fp]
-    L.hrp_policy_predict.argtypes = [vp, fp, ip]
+    L.hrp_policy_predict.argtypes = [vp, fp, tp, ip]
+    L.hrp_policy_load.argtypes = [vp, ctypes.c_char_p]
+    L.hrp_check.argtypes = [vp, vp]
+    L.hrp_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    L.hrp_wait_selftest.argtypes = [vp, ctypes.c_longlong, dp, vp]
     L.hrp_policy_tree.argtypes = [c_int, tp]
     L.hrp_last_policy_choice.argtypes = [vp]
     L.hrp_autotune_candidates.argtypes = [tp, vp, c_int]
@@ -216,17 +221,25 @@ class Handle:
                 "used_fallback": fb.value}
 
     # batched: lists of column-major CUDA tensors; trees: one Tree or a list of Trees
-    def potrf_batched(self, trees, As, d_info, stream=None) -> None:
-        batch = len(As)
+    @staticmethod
+    def _tree_array(trees, batch):
+        """trees: one Tree, a list (None entries: the policy chooses) or None (policy for all)."""
+        if trees is None:
+            return None, ctypes.c_void_p(0)
         if isinstance(trees, Tree):
             trees = [trees] * batch
         keep = list(trees)
-        tptr = (ctypes.POINTER(Tree) * batch)(*[ctypes.pointer(t) for t in keep])
+        arr = (ctypes.POINTER(Tree) * batch)(*[ctypes.pointer(t) if t is not None else ctypes.POINTER(Tree)()
+                                               for t in keep])
+        return (keep, arr), ctypes.cast(arr, ctypes.c_void_p)
+
+    def potrf_batched(self, trees, As, d_info, stream=None) -> None:
+        batch = len(As)
+        keep, tptr = self._tree_array(trees, batch)
         n = (ctypes.c_int * batch)(*[A.shape[0] for A in As])
         lda = (ctypes.c_int * batch)(*[A.shape[1] for A in As])
         ptrs = (ctypes.c_void_p * batch)(*[A.data_ptr() for A in As])
-        st = self._lib.hrp_potrf_batched(self._h, ctypes.cast(tptr, ctypes.c_void_p), batch, n, ptrs, lda,
-                                         _ptr(d_info), _stream(stream))
+        st = self._lib.hrp_potrf_batched(self._h, tptr, batch, n, ptrs, lda, _ptr(d_info), _stream(stream))
         self._check(st)
 
     def potrs_batched(self, Ls, Bs, stream=None) -> None:
@@ -284,27 +297,44 @@ class Handle:
         self._check(self._lib.hrp_policy_set(self._h, pp, mp, sp))
 
     def policy_predict(self, feat) -> int:
+        return self.policy_predict_tree(feat)[1]
+
+    def policy_predict_tree(self, feat) -> tuple[Tree, int]:
         f = np.ascontiguousarray(feat, dtype=np.float32)
         idx = ctypes.c_int(-1)
+        t = Tree()
         self._check(self._lib.hrp_policy_predict(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                                 ctypes.byref(idx)))
-        return idx.value
+                                                 ctypes.byref(t), ctypes.byref(idx)))
+        return t, idx.value
+
+    def policy_load(self, path: str) -> None:
+        self._check(self._lib.hrp_policy_load(self._h, os.fsencode(path)))
+
+    def check(self, stream=None) -> int:
+        """hrp_check: status of the device-side failures since the last synchronous call."""
+        return self._lib.hrp_check(self._h, _stream(stream))
+
+    def set_wait_limit(self, microseconds: int) -> None:
+        self._check(self._lib.hrp_set_wait_limit(self._h, int(microseconds)))
+
+    def wait_selftest(self, microseconds: int, stream=None) -> tuple[int, float]:
+        """(status, microseconds the device waited) of a bounded wait on a flag nothing sets."""
+        w = ctypes.c_double(0.0)
+        st = self._lib.hrp_wait_selftest(self._h, int(microseconds), ctypes.byref(w), _stream(stream))
+        return st, w.value
 
     def last_policy_choice(self) -> int:
         return self._lib.hrp_last_policy_choice(self._h)
 
     def posv_batched(self, trees, As, Bs, Xs, max_iter: int = 30, tol: float = 1e-12, stream=None) -> dict:
         batch = len(As)
-        if isinstance(trees, Tree):
-            trees = [trees] * batch
-        keep = list(trees)
-        tptr = (ctypes.POINTER(Tree) * batch)(*[ctypes.pointer(t) for t in keep])
+        keep, tptr = self._tree_array(trees, batch)
         arr_i = lambda v: (ctypes.c_int * batch)(*v)
         arr_p = lambda ts: (ctypes.c_void_p * batch)(*[t.data_ptr() for t in ts])
         info, iters, fb = arr_i([0] * batch), arr_i([0] * batch), arr_i([0] * batch)
         resid = (ctypes.c_double * batch)()
         nrhs = Bs[0].shape[0] if batch else 1
-        st = self._lib.hrp_posv_batched(self._h, ctypes.cast(tptr, ctypes.c_void_p), batch,
+        st = self._lib.hrp_posv_batched(self._h, tptr, batch,
                                         arr_i([A.shape[0] for A in As]), arr_p(As), arr_i([A.shape[1] for A in As]),
                                         nrhs, arr_p(Bs), arr_i([B.shape[1] for B in Bs]), arr_p(Xs),
                                         arr_i([X.shape[1] for X in Xs]), max_iter, tol, info, iters, resid, fb,

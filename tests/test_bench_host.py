@@ -6,6 +6,8 @@ import os
 import sys
 import time
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
@@ -106,3 +108,25 @@ def test_lpt_partition_covers_every_system_once_and_balances_the_work():
         assert max(loads) - min(loads) <= max(costs)      # list scheduling: within one item
     assert bench.lpt_partition([5.0, 5.0, 5.0], 2) == [[0, 2], [1]]   # ties by index, then rank
     assert bench.lpt_partition([], 3) == [[], [], []]
+
+
+@pytest.mark.parametrize("warmup", [0, 1, 3, 5, 7])
+def test_accuracy_entries_name_the_matrix_each_step_factored(warmup):
+    # step s factors copies[s] = A0[s % 3]; the accuracy entry of a step must carry that
+    # matrix's rho whatever the number of warm-up steps
+    nsteps = warmup + 24
+    seen = bench.accuracy_steps(warmup, nsteps, 3)
+    assert [s for s, _ in seen] == [warmup, warmup + 1, warmup + 2]
+    assert all(k == s % 3 for s, k in seen)
+    assert sorted(k for _, k in seen) == [0, 1, 2]
+    assert bench.accuracy_steps(warmup, warmup + 1, 3) == [(warmup, warmup % 3)]
+
+
+def test_leaf_traffic_is_keyed_to_the_kernel_code(tmp_path):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n\ncudaError_t launch_k() { return 0; }\n")
+    a = bench.device_code_sha1(str(src), "cudaError_t launch_k(")
+    src.write_text("__global__ void k() {}\n\ncudaError_t launch_k() { return 1; /* host change */ }\n")
+    assert bench.device_code_sha1(str(src), "cudaError_t launch_k(") == a
+    src.write_text("__global__ void k() { int x; }\n\ncudaError_t launch_k() { return 1; }\n")
+    assert bench.device_code_sha1(str(src), "cudaError_t launch_k(") != a
