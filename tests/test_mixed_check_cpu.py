@@ -1,20 +1,17 @@
-"""The mixed-tree parity check (tests/mixed_check.py) rejects a mis-levelled factor and
-accepts a factor that differs from the emulator only by FP32 accumulation.
+"""The mixed-tree parity check (tests/mixed_check.py) rejects mis-levelled factors and
+accepts factors that differ from the emulator only by FP32 arithmetic.
 
 No GPU: the "correct" candidate is the emulator with every reduced-precision GEMM
 accumulated in float32, 16 exact products at a time, each partial sum truncated toward
-zero (a pessimistic stand-in for the tensor cores' FP32 accumulator); the wrong
-candidates are planted on the CPU.
+zero (a pessimistic stand-in for the tensor cores' FP32 accumulator); the wrong ones
+are the same model run on a mis-levelled tree, or with operands rounded at the wrong level.
 """
 import numpy as np
 import pytest
 
-from mixed_check import fp32_effect_ratio, level_alternatives, mislevel_ratio
+from mixed_check import check_mixed_factor, level_alternatives, mislevel_projections
 from oracle import dense, tree as otree
 from synth import dominant_spd, seed_for
-
-MISLEVEL_BOUND = 0.3      # the GPU test's bound on mislevel_ratio
-FP32_EFFECT_RANGE = (0.5, 2.0)
 
 
 class Acc32(otree.Emulator):
@@ -40,52 +37,58 @@ class Acc32(otree.Emulator):
             D -= prod
 
 
-def _acc32(A, spec, leaf):
-    em = Acc32(A, otree.parse(spec, leaf=leaf))
+def _acc32(A, spec, leaf, cls=Acc32):
+    em = cls(A, otree.parse(spec, leaf=leaf))
     em.potrf(0, em.n, 0)
     return np.tril(em.M)
 
 
 def test_level_alternatives():
-    assert level_alternatives("[F16,F32|F64@128]") == ["[F32,F32|F64@128]", "[F16,F16|F64@128]"]
-    assert level_alternatives("[F8,F64]") == ["[F16,F64]", "[F8,F32]"]
+    assert level_alternatives("[F16,F32|F64@128]") == [
+        ("[F32,F32|F64@128]", True), ("[F16,F16|F64@128]", True), ("[F16,F64|F64@128]", False),
+        ("[F16,F32|F32@128]", False)]
+    assert level_alternatives("[F8,F64]") == [("[F16,F64]", True), ("[F8,F32]", False)]
 
 
-@pytest.mark.parametrize("spec,leaf", [("[F16,F16,F32|F64@128]", 128), ("[F16,F32|F64@64]", 64),
-                                       ("[F16,F32,F64]", 128)])
-def test_fp32_accumulation_passes_and_a_mislevelled_tree_fails(spec, leaf):
+SPECS = [("[F16,F16,F32|F64@128]", 128), ("[F16,F32|F64@64]", 64), ("[F16,F32,F64]", 128),
+         ("[F16,F16,F16,F16,F32|F64@128]", 128)]
+
+
+@pytest.mark.parametrize("spec,leaf", SPECS)
+def test_fp32_accumulation_passes_and_mislevelled_trees_fail(spec, leaf):
     n = 1000
     A = dominant_spd(n, 1.05, seed_for(1, n))
-    r_ok, _, _ = mislevel_ratio(_acc32(A, spec, leaf), A, spec, leaf)
-    assert r_ok <= MISLEVEL_BOUND, r_ok
-    for alt in level_alternatives(spec):
-        L_alt, info, _ = otree.emulate_potrf(A, otree.parse(alt, leaf=leaf))
-        r_bad, d_bad, _ = mislevel_ratio(L_alt, A, spec, leaf)
-        if d_bad > 0:
-            assert r_bad >= 1.0 > MISLEVEL_BOUND
+    check_mixed_factor(_acc32(A, spec, leaf), A, spec, leaf)
+    L_emu, _, _ = otree.emulate_potrf(A, otree.parse(spec, leaf=leaf))
+    for alt, low in level_alternatives(spec):
+        if not low:
+            continue
+        L_bad = _acc32(A, alt, leaf)
+        rows, gn = mislevel_projections(L_bad, A, spec, leaf, L_emu=L_emu)
+        if not any(a == alt for a, _, _, _ in rows):
+            continue                                   # level not reached at this n
+        with pytest.raises(AssertionError):
+            check_mixed_factor(L_bad, A, spec, leaf, L_emu=L_emu)
 
 
 def test_operands_rounded_at_the_wrong_level_fail():
-    """A GEMM of a deeper F32 node fed FP16 operands (the shallower level's rounding)."""
+    """The GEMMs of the F32 nodes fed FP16 operands (a shallower level's rounding)."""
     spec, leaf, n = "[F16,F32|F64@128]", 128, 1000
     A = dominant_spd(n, 1.05, seed_for(1, n))
 
-    class Wrong(otree.Emulator):
+    class Wrong(Acc32):
         def _gemm(self, p, r0, m, c0, nd, k0, k, lower=False):
             super()._gemm("F16" if p == "F32" else p, r0, m, c0, nd, k0, k, lower)
 
-    em = Wrong(A, otree.parse(spec, leaf=leaf))
-    em.potrf(0, em.n, 0)
-    r, _, _ = mislevel_ratio(np.tril(em.M), A, spec, leaf)
-    assert r > MISLEVEL_BOUND
+    with pytest.raises(AssertionError):
+        check_mixed_factor(_acc32(A, spec, leaf, Wrong), A, spec, leaf)
 
 
 @pytest.mark.parametrize("spec", ["[F32]", "[F32,F32,F32,F64]"])
-def test_fp32_levels_run_in_fp64_fail_the_effect_bound(spec):
+def test_fp32_levels_run_in_fp64_fail(spec):
     n = 1000
     A = dominant_spd(n, 2.0, seed_for(1, n))
-    L_emu, _, _ = otree.emulate_potrf(A, otree.parse(spec, leaf=128))
-    lo, hi = FP32_EFFECT_RANGE
-    assert lo <= fp32_effect_ratio(_acc32(A, spec, 128), A, L_emu) <= hi
+    check_mixed_factor(_acc32(A, spec, 128), A, spec, 128)
     L64, _ = dense.cholesky(A)
-    assert fp32_effect_ratio(L64, A, L_emu) < lo
+    with pytest.raises(AssertionError):
+        check_mixed_factor(L64, A, spec, 128)
