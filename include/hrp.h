@@ -167,6 +167,17 @@ hrp_status hrp_set_timing(hrp_handle* h, int enable);
 int hrp_get_timing(hrp_handle* h, double* out, int n);
 
 /*
+ * Lookahead (on by default): after a node's A11 is factored, the rows of its A21 that the
+ * next diagonal block needs, and that block's share of the SYRK, run on the handle's
+ * critical stream (highest priority); the remaining TRSM rows and SYRK blocks run on a side
+ * stream of that recursion depth and are awaited only when the recursion reaches them, so
+ * they overlap the leaf factorizations.  The arithmetic of every entry is unchanged.  The
+ * streams fork from and join into the call's stream (capturable in a CUDA graph).
+ * hrp_set_lookahead(h, 0) keeps every launch on the call's stream.
+ */
+hrp_status hrp_set_lookahead(hrp_handle* h, int enable);
+
+/*
  * Autotuner for the recursion cut-offs of a tree: the base-case sizes b of Alg. 1
  * (leaf) and Alg. 2 (trsm_leaf), which the paper leaves as parameters (Sec. 3.2).  The
  * precision list, the inner region and trsm_compute are never changed.

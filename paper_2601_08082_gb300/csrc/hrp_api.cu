@@ -79,6 +79,11 @@ struct hrp_handle_s {
   int last_choice = -1;
   // autotuner: tuned tree and its median time by (n, precision list, inner region, trsm_compute)
   std::map<std::string, std::pair<hrp_tree, float>> tune_cache;
+  // lookahead: the critical stream (highest priority), side streams by recursion depth, and
+  // a pool of events for the dependencies between them
+  bool lookahead = true;
+  std::vector<cudaStream_t> lstreams;
+  std::vector<cudaEvent_t> levents;
 };
 
 namespace hrp {
@@ -177,6 +182,14 @@ struct Fact {
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
   cudaError_t err = cudaSuccess;
   long long launches = 0;
+  // lookahead (see potrf): s is the stream of the next launch, main_s the critical stream;
+  // side[d] takes the off-critical TRSM/SYRK work of nodes at depth d
+  bool la = false;
+  cudaStream_t main_s = nullptr;
+  const std::vector<cudaStream_t>* side = nullptr;
+  size_t ev_used = 0;
+  std::map<cudaStream_t, bool> waited;   // the stream's next kernel follows a cross-stream wait
+  int side_ctas = 0;
   // timing mode: an event pair around every launch, tagged with its class and flops
   struct Rec { int cls; size_t ev; double flops; };
   std::vector<Rec> recs;
@@ -197,6 +210,11 @@ struct Fact {
     cur_cls = cls;
     cur_flops = flops;
     began = false;
+    LaunchCtx& lc = launch_ctx();
+    auto w = waited.find(s);
+    lc.pdl = !(w != waited.end() && w->second);
+    if (w != waited.end()) w->second = false;
+    lc.max_ctas = (la && s != main_s) ? side_ctas : 0;
     if (h->timing) {
       cudaEvent_t e = event(ev_next);
       began = e && cudaEventRecord(e, s) == cudaSuccess;
@@ -299,35 +317,88 @@ struct Fact {
     }
   }
 
-  // Alg. 2: B = A[r0:r0+m, c0:c0+nc] <- B L^{-T}, L = A[c0:c0+nc, c0:c0+nc]
-  void trsm(int r0, int m, int c0, int nc, int p) {
-    if (std::min(m, nc) <= tleaf()) {
+  // Alg. 2: B = A[r0:r0+m, c0:c0+nc] <- B L^{-T}, L = A[c0:c0+nc, c0:c0+nc].  The rows of B
+  // are independent; when B is a slice of a taller block (lookahead), mdec is that block's
+  // height, so the slice follows the block's own recursion (same base cases, same GEMMs).
+  void trsm(int r0, int m, int c0, int nc, int p, int mdec = -1) {
+    if (mdec < 0) mdec = m;
+    if (std::min(mdec, nc) <= tleaf()) {
       leaf_trsm(r0, m, c0, nc, p);
       return;
     }
     int n1 = split(nc);
-    trsm(r0, m, c0, n1, p);
+    trsm(r0, m, c0, n1, p, mdec);
     gemm(p, r0, m, c0 + n1, nc - n1, c0, n1, false);   // B2 -= B1 L21^T
-    trsm(r0, m, c0 + n1, nc - n1, p);
+    trsm(r0, m, c0 + n1, nc - n1, p, mdec);
   }
 
   // Alg. 3 flattened: C = A[c0:c0+nc, c0:c0+nc] (lower) -= X X^T, X = A[c0:c0+nc, a0:a0+k]
   void syrk(int c0, int nc, int a0, int k, int p) { gemm(p, c0, nc, c0, nc, a0, k, true); }
 
-  // Alg. 1
-  void potrf(int off, int nb, int depth) {
+  // ---- cross-stream dependencies (lookahead) ----
+  cudaEvent_t record(cudaStream_t on) {
+    while (h->levents.size() <= ev_used) {
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        if (err == cudaSuccess) err = cudaErrorMemoryAllocation;
+        return nullptr;
+      }
+      h->levents.push_back(e);
+    }
+    cudaEvent_t e = h->levents[ev_used++];
+    cudaError_t r = cudaEventRecord(e, on);
+    if (r != cudaSuccess && err == cudaSuccess) err = r;
+    return e;
+  }
+  void wait(cudaStream_t on, cudaEvent_t e) {
+    if (!e) return;
+    cudaError_t r = cudaStreamWaitEvent(on, e, 0);
+    if (r != cudaSuccess && err == cudaSuccess) err = r;
+    waited[on] = true;
+  }
+
+  // Alg. 1.  `rest`: when non-null, the event after which everything of this node outside
+  // its A11 block is up to date (A11 itself is up to date now, on the critical stream).
+  //
+  // Lookahead: the next node, Alg. 1 on A22, starts with its own A11 block, A22[0:m1, 0:m1]
+  // (m1 = split(n2)), which needs only the top m1 rows of A21 solved (Alg. 2) and their share
+  // of the SYRK (Alg. 3).  Those stay on the critical stream; the other rows of the TRSM and
+  // the rest of the SYRK (A22's off-diagonal block and its trailing block) go to the side
+  // stream of this depth, and A22's Alg. 1 waits for them only after its own A11.  Every
+  // entry still receives the same updates with the same inner dimension and precision.
+  void potrf(int off, int nb, int depth, cudaEvent_t rest = nullptr) {
     if (nb <= 0) return;
     int p = node_prec(t, depth, nb);
     if (nb <= t->leaf) {
+      wait(s, rest);
       leaf_potrf(off, nb, p);
       return;
     }
     int n1 = split(nb), n2 = nb - n1;
     potrf(off, n1, depth + 1);
+    wait(s, rest);
     if (p == HRP_F8E4M3) quant8_lower(off, n1);
-    trsm(off + n1, n2, off, n1, p);
-    syrk(off + n1, n2, off, n1, p);
-    potrf(off + n1, n2, depth + 1);
+    const int m1 = n2 > t->leaf ? split(n2) : n2;
+    if (!la || m1 >= n2 || depth + 1 >= (int)side->size()) {
+      trsm(off + n1, n2, off, n1, p);
+      syrk(off + n1, n2, off, n1, p);
+      potrf(off + n1, n2, depth + 1);
+      return;
+    }
+    cudaStream_t ss = (*side)[depth + 1];
+    const int r0 = off + n1, rb = off + n1 + m1, mb = n2 - m1;
+    wait(ss, record(s));                         // L11 (and its FP32 inverses) are final
+    trsm(r0, m1, off, n1, p, n2);                // top rows of A21: critical
+    cudaEvent_t top = record(s);
+    syrk(r0, m1, off, n1, p);                    // A22[0:m1, 0:m1] -= A21_top A21_top^T
+    s = ss;                                      // side: the rest of Alg. 2 and Alg. 3
+    trsm(rb, mb, off, n1, p, n2);
+    wait(ss, top);
+    gemm(p, rb, mb, r0, m1, off, n1, false);     // A22[m1:, 0:m1] -= A21_bot A21_top^T
+    syrk(rb, mb, off, n1, p);                    // A22[m1:, m1:] (lower) -= A21_bot A21_bot^T
+    cudaEvent_t done = record(ss);
+    s = main_s;
+    potrf(off + n1, n2, depth + 1, done);
   }
 };
 
@@ -346,6 +417,31 @@ void collect_timing(hrp_handle* h, const Fact& f) {
     h->cls_flops[r.cls] += r.flops;
   }
   cudaGetLastError();   // a failed elapsed-time query must not leak into the next launch check
+}
+
+// The lookahead streams of the handle: [0] with the highest priority (the critical path),
+// [1..] side streams by recursion depth, deeper ones at higher priority than shallower ones
+// (their work is needed sooner), all below [0].
+hrp_status lookahead_streams(hrp_handle* h) {
+  constexpr int kStreams = 12;
+  if ((int)h->lstreams.size() >= kStreams) return HRP_OK;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
+  while ((int)h->lstreams.size() < kStreams) {
+    const int i = (int)h->lstreams.size();
+    // numerically lower is higher priority: [0] = greatest; side depth d from least upwards
+    int prio = greatest;
+    if (i > 0) prio = std::max(greatest + 1, least - (i - 1) / 2);
+    if (greatest == least) prio = least;
+    cudaStream_t st;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess)
+      return set_err(h, HRP_ERR_CUDA, "lookahead stream");
+    h->lstreams.push_back(st);
+  }
+  return HRP_OK;
 }
 
 hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s) {
@@ -393,11 +489,28 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
     if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)n * n)) != HRP_OK) return st;
     f.shadow32 = h->shadow32;
   }
+  // lookahead needs a node whose A22 splits again (n2 > leaf)
+  f.la = h->lookahead && n > 2 * t->leaf + 128;
+  if (f.la && (st = lookahead_streams(h)) != HRP_OK) return st;
+  if (f.la) {
+    f.side = &h->lstreams;                 // [0] is the critical stream, [d] the side stream of depth d
+    f.main_s = h->lstreams[0];
+    f.side_ctas = std::max(1, device_sm_count() - 16);
+    f.wait(f.main_s, f.record(s));          // fork from the caller's stream
+    f.s = f.main_s;
+  } else {
+    f.main_s = s;
+  }
   f.begin(CLS_OTHER, 0.0);
-  f.chk(launch_fill_int(d_info, INT_MAX, 1, s));
+  f.chk(launch_fill_int(d_info, INT_MAX, 1, f.s));
   f.potrf(0, n, 0);
   f.begin(CLS_OTHER, 0.0);
-  f.chk(launch_finalize_info(d_info, s));
+  f.chk(launch_finalize_info(d_info, f.s));
+  if (f.la) {
+    f.wait(s, f.record(f.main_s));          // join: every side stream was joined into it
+    f.s = s;
+  }
+  launch_ctx() = LaunchCtx{};
   h->launches = f.launches;
   if (h->timing && f.err == cudaSuccess) {
     cudaError_t e = cudaStreamSynchronize(s);
@@ -523,6 +636,8 @@ hrp_status hrp_destroy(hrp_handle* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->bevents) cudaEventDestroy(e);
   for (cudaStream_t st : h->bstreams) cudaStreamDestroy(st);
+  for (cudaStream_t st : h->lstreams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : h->levents) cudaEventDestroy(e);
   cudaFree(h->bwork);
   cudaFree(h->fwork);
   cudaFree(h->policy);
@@ -909,6 +1024,12 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
 hrp_status hrp_set_timing(hrp_handle* h, int enable) {
   if (!h) return HRP_ERR_INVALID_ARG;
   h->timing = enable != 0;
+  return HRP_OK;
+}
+
+hrp_status hrp_set_lookahead(hrp_handle* h, int enable) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->lookahead = enable != 0;
   return HRP_OK;
 }
 

@@ -36,6 +36,21 @@ enum class OpRound : int { F64 = 0, F32 = 1, F16 = 2 };
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Launch settings the scheduler sets for the next launches of the calling host thread:
+//   pdl: launch with programmatic stream serialization.  Cleared for the first kernel after
+//        the stream waited on another stream's event, so that no kernel overlaps the
+//        predecessor it may depend on across streams.
+//   max_ctas: upper bound on the CTAs of a persistent kernel (0 = one per SM), so that work
+//        on a side stream leaves SMs to the critical path.
+struct LaunchCtx {
+  bool pdl = true;
+  int max_ctas = 0;
+};
+inline LaunchCtx& launch_ctx() {
+  thread_local LaunchCtx c;
+  return c;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args&&... args) {
@@ -48,7 +63,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = launch_ctx().pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 

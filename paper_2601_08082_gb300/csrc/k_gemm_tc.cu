@@ -444,7 +444,8 @@ cudaError_t launch_persistent(double* C, int ldc, const __half* S, int lds, int 
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  const int grid = (int)std::min<long long>(ntiles, sms);
+  const int cap = launch_ctx().max_ctas > 0 ? std::min(sms, launch_ctx().max_ctas) : sms;
+  const int grid = (int)std::min<long long>(ntiles, cap);
   (void)launch_pdl(gemm_f16_tc_persistent<BN>, dim3(grid), dim3(TC_THREADS), TcLayout<BN>::bytes, s, mx, my, C, ldc, m, n, k, lower ? 1 : 0,
                                                                           scale, (int)ntiles, dev_err);
   return cudaGetLastError();

@@ -541,14 +541,21 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see launch_pdl
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  at[1].id = cudaLaunchAttributeClusterDimension;
-  at[1].val.clusterDim.x = 1;
-  at[1].val.clusterDim.y = grid.y;                         // the slices of one row tile
-  at[1].val.clusterDim.z = 1;
+  int na = 0;
+  if (launch_ctx().pdl) {                                  // see launch_pdl
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (grid.y > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = 1;
+    at[na].val.clusterDim.y = grid.y;                      // the slices of one row tile
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = grid.y > 1 ? 2 : 1;
+  cfg.numAttrs = na;
   cudaError_t e;
   if (cpl == 4)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<4>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,

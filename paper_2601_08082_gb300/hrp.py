@@ -33,7 +33,7 @@ EXPORTED = [
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
-    "hrp_wait_selftest",
+    "hrp_wait_selftest", "hrp_set_lookahead",
 ]
 
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.hrp_posv.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp, c_int, c_int, c_double, ip, dp, ip, ip, vp]
     L.hrp_backward_error.argtypes = [vp, c_int, vp, c_int, vp, c_int, dp, vp]
     L.hrp_set_timing.argtypes = [vp, c_int]
+    L.hrp_set_lookahead.argtypes = [vp, c_int]
     L.hrp_get_timing.argtypes = [vp, dp, c_int]
     L.hrp_last_launch_count.argtypes = [vp]
     L.hrp_last_launch_count.restype = ctypes.c_longlong
@@ -182,6 +183,9 @@ class Handle:
 
     def launch_count(self) -> int:
         return self._lib.hrp_last_launch_count(self._h)
+
+    def set_lookahead(self, enable: bool) -> None:
+        self._check(self._lib.hrp_set_lookahead(self._h, 1 if enable else 0))
 
     # hrp_potrf: A is a column-major (n, lda) float64 CUDA tensor, overwritten with L
     def potrf(self, tree: Tree, A, n: int | None = None, stream=None, raise_not_spd: bool = False) -> int:
