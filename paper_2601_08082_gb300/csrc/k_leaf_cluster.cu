@@ -88,14 +88,34 @@ __device__ __forceinline__ int pivot_class(double d) {
   return (ex > 1023 - 120 && ex < 1023 + 120) ? 2 : 1;
 }
 
-// 1/d from the single-precision reciprocal x0 and one third-order step of Householder's
-// iteration for 1/x - d = 0: with e = 1 - d x0, 1/d = x0 / (1 - e) = x0 (1 + e + e^2 + O(e^3)).
-// The seed (rounding of d plus the approximation, |e| < 2^-21) leaves a truncation error
-// below 2^-63; three dependent FP64 operations after the seed.  pivot_class(d) == 2.
+// d truncated to single precision and a single-precision value widened to double, both by
+// integer operations on the IEEE-754 bit fields (d, f positive and normal with |log2| < 120:
+// pivot_class == 2).  On this GPU a conversion instruction costs about as much as a
+// dependent DFMA on the FP64 pipe; these take a few integer operations instead.
+__device__ __forceinline__ float trunc_to_float(double d) {
+  const long long b = __double_as_longlong(d);
+  const int hi = (int)(b >> 32);
+  const unsigned lo = (unsigned)b;
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;                    // rebias the exponent
+  const unsigned m = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);    // top 23 mantissa bits
+  return __int_as_float((e << 23) | (int)m);
+}
+__device__ __forceinline__ double widen_float(float f) {
+  const unsigned u = __float_as_uint(f);
+  const long long e = (long long)(((u >> 23) & 0xff) - 127 + 1023);
+  const long long m = (long long)(u & 0x7fffff);
+  return __longlong_as_double((e << 52) | (m << 29));
+}
+
+// 1/d from the single-precision reciprocal x0 of d truncated to single precision, and one
+// third-order step of Householder's iteration for 1/x - d = 0: with e = 1 - d x0,
+// 1/d = x0 / (1 - e) = x0 (1 + e + e^2 + O(e^3)).  The seed (truncation of d plus the
+// approximation, |e| < 2^-21) leaves a truncation error below 2^-63; three dependent FP64
+// operations after the seed.  pivot_class(d) == 2.
 __device__ __forceinline__ double recip_third_order(double d) {
   float xf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"((float)d));
-  const double x0 = (double)xf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(trunc_to_float(d)));
+  const double x0 = widen_float(xf);
   const double e = fma(-d, x0, 1.0);
   const double w = fma(e, e, e);
   return fma(x0, w, x0);
