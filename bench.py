@@ -395,6 +395,88 @@ def run_batched(args, rank, world):
     return 0
 
 
+BLAS3_TREES = ["[F64]", "[F32]", "[F16,F16,F32]", "[F16,F16,F16,F16,F32]", "[F16]"]
+
+
+def blas3_baseline(spec):
+    """The paper's normalization (Sec. 4.2): a mixed list against the pure tree of its innermost
+    (diagonal) precision; Pure F16 against FP32."""
+    inner = spec.strip("[]").split(",")[-1]
+    return "[F32]" if spec == "[F16]" else f"[{inner}]"
+
+
+def run_blas3(args, rank, world):
+    """Standalone recursive SYRK (C -= A A^T, A n x n) and TRSM (X L^T = B, B n x n) of order
+    --blas3-n with the precision lists of Sec. 4.2: TFLOP/s (n^3 for SYRK and TRSM) and the
+    speed-up over the baseline the paper uses for each list."""
+    import numpy as np
+    import torch
+
+    import paper_2601_08082_gb300 as hrp
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    n = args.blas3_n
+    h = hrp.Handle(local)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2601008082 + 4000 + rank)
+    A = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    C0 = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    B0 = torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64)
+    # a well-conditioned lower factor: unit-ish diagonal, small off-diagonal entries
+    Lf = torch.tril(torch.randn((n, n), generator=g, device="cuda", dtype=torch.float64) / n ** 0.5, -1)
+    Lf.diagonal().copy_(1.0 + torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
+    Lt = Lf.T.contiguous()                        # column-major storage of L
+    C = torch.empty_like(C0)
+    Bx = torch.empty_like(B0)
+    stream = torch.cuda.current_stream()
+    out = {"syrk": {}, "trsm": {}}
+    for spec in BLAS3_TREES:
+        t = hrp.tree_parse(spec, leaf=128)
+        for op in ("syrk", "trsm"):
+            times = []
+            for rep in range(args.warmup + args.steps):
+                if op == "syrk":
+                    C.copy_(C0)
+                else:
+                    Bx.copy_(B0)
+                torch.cuda.synchronize()
+                reps.barrier()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if op == "syrk":
+                    h.syrk(t, A, C, stream=stream)
+                else:
+                    h.trsm(t, Lt, Bx, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            assert h.check() == 0
+            ms = reps.max(statistics.median(times))
+            out[op][spec] = {"ms": ms, "tflops": world * float(n) ** 3 / (ms * 1e-3) / 1e12}
+    for op in out:
+        for spec, v in out[op].items():
+            base = blas3_baseline(spec)
+            if base != spec and base in out[op]:
+                v["speedup_vs_" + base] = out[op][base]["ms"] / v["ms"]
+    line = {"metric": "recursive SYRK / TRSM TFLOP/s (n^3 per s) by precision list", "unit": "TFLOP/s",
+            "value": out["syrk"]["[F16,F16,F16,F16,F32]"]["tflops"], "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 (fp32 acc) / f32 / f64", "data": "synthetic (device generator)",
+            "config": {"workload": f"hrp_syrk and hrp_trsm, n={n}, leaf 128, precision lists {BLAS3_TREES}",
+                       "n": n, "value_is": "SYRK [F16,F16,F16,F16,F32]",
+                       "l2": "inputs larger than L2 (128 MB+ operands, fresh copy per step)"},
+            "syrk": out["syrk"], "trsm": out["trsm"]}
+    reps.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def run_fp8posv(args, rank, world):
     """n = 32768, A = (B + B^T)/2 with B iid N(0,1) and A_ii = 2 sum_{j!=i} |A_ij|, tree
     [F8,F16,F16,F32|F64@128] (E4M3 outermost off-diagonal level with one power-of-two scale per
@@ -492,7 +574,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768"])
+    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768", "blas3"])
+    ap.add_argument("--blas3-n", type=int, default=8192, help="order of the blas3 workload")
     ap.add_argument("--n3", type=int, default=32768, help="order of the fp8posv32768 workload")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--batch-tree", default="[F16,F32|F64@128]")
@@ -507,6 +590,8 @@ def main():
         return run_batched(args, rank, world)
     if args.workload == "fp8posv32768":
         return run_fp8posv(args, rank, world)
+    if args.workload == "blas3":
+        return run_blas3(args, rank, world)
 
     import numpy as np
     import torch

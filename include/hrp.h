@@ -280,6 +280,27 @@ hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* trees, int bat
                             double* const* dX, const int* ldx, int max_iter, double tol, int* info, int* iters,
                             double* resid, int* used_fallback, void* stream);
 
+/*
+ * Standalone recursive SYRK and TRSM (Alg. 3 and Alg. 2, the kernels of Sec. 4.2's SYRK and
+ * TRSM experiments) with the tree's precision list applied to their own recursion: the GEMM
+ * of a node at depth t runs at level[t] (deeper nodes at the last entry; a node of order <=
+ * inner_size at `inner`) with FP32 accumulation below FP64, and a base case at its node's
+ * precision (FP32 arithmetic for F16/F32 base cases unless trsm_compute = 1).  FP16 operands
+ * are copies rounded to nearest even; one beyond 65504 is recorded as HRP_ERR_RANGE (read by
+ * hrp_check).  F8 levels are not supported here.  Both calls only enqueue work.
+ * hrp_syrk: C <- C - A A^T on the lower triangle of the n x n dC (ldc); dA is n x k (lda).
+ *   Base case size: syrk_leaf (0 = leaf).  The strict upper triangle of C is not touched.
+ * hrp_trsm: B <- B L^{-T} (TRSM_{R,L,T}: solves X L^T = B) for dB m x n (ldb) and the lower
+ *   triangle of the n x n dL (ldl), which is not modified.  Base case: min(m, n) <= trsm_leaf
+ *   (0 = leaf), trsm_leaf <= 128 unless m <= 128.
+ * Workspace: an FP16 copy of A (n x k) or of [B; L] ((m + n) x n), and an FP32 copy when the
+ * tree has F32 levels, in the handle.
+ */
+hrp_status hrp_syrk(hrp_handle* h, const hrp_tree* tree, int n, int k, const double* dA, int lda, double* dC, int ldc,
+                    void* stream);
+hrp_status hrp_trsm(hrp_handle* h, const hrp_tree* tree, int m, int n, const double* dL, int ldl, double* dB, int ldb,
+                    void* stream);
+
 /* Number of kernel launches enqueued by the last hrp_potrf/potrs/posv call. */
 long long hrp_last_launch_count(const hrp_handle* h);
 

@@ -232,3 +232,83 @@ def level_flop_split(n: int, tree: Tree) -> dict:
     walk(n, 0)
     tot = sum(out.values())
     return {p: v / tot for p, v in out.items()}
+
+
+# ---------------------------------------------------------------------------------------
+# Standalone Tree-SYRK (Alg. 3) and Tree-TRSM (Alg. 2), the kernels of the paper's SYRK and
+# TRSM experiments (Sec. 4.2).  Reading of a precision list for them: the GEMM of a node at
+# recursion depth t is computed at levels[t] (deeper nodes at the last entry; a node of
+# order <= inner_size at `inner`), a base case at the precision of its node: the leaf SYRK
+# as the lower triangle of the product at that precision, the leaf TRSM in FP32 arithmetic
+# on FP32-rounded B and L unless the precision is F64.  Operands are rounded per Sec. 3.4
+# (alpha = max(1, amax / 65504) per operand block for FP16) and their exact products summed
+# in float64.
+# ---------------------------------------------------------------------------------------
+def _operand(p: str, X: np.ndarray):
+    if p == "F64":
+        return X, 1.0
+    if p == "F32":
+        return lowprec.round_f32(X), 1.0
+    if p == "F16":
+        return lowprec.quantize_f16(X)
+    raise ValueError("F8 levels are defined on the factorization's 128 x 128 tiles only")
+
+
+def emulate_syrk(C: np.ndarray, A: np.ndarray, tree: Tree) -> np.ndarray:
+    """Lower triangle of C - A A^T by Alg. 3 with the precision list applied by depth."""
+    C = np.array(C, dtype=np.float64, copy=True)
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+
+    def gemm(p, r0, m, c0, nd, lower):
+        X, ax = _operand(p, A[r0:r0 + m])
+        Y, ay = _operand(p, A[c0:c0 + nd])
+        prod = (ax * ay) * (X @ Y.T)
+        if lower:
+            prod = np.tril(prod)
+        C[r0:r0 + m, c0:c0 + nd] -= prod
+
+    def rec(c0, nc, depth):
+        if nc == 0:
+            return
+        p = node_prec(tree, depth, nc)
+        if nc <= tree.sleaf():
+            gemm(p, c0, nc, c0, nc, True)
+            return
+        n1 = split(nc)
+        rec(c0, n1, depth + 1)
+        gemm(p, c0 + n1, nc - n1, c0, n1, False)          # C21 -= A2 A1^T
+        rec(c0 + n1, nc - n1, depth + 1)
+
+    rec(0, n, 0)
+    return np.tril(C)
+
+
+def emulate_trsm(B: np.ndarray, L: np.ndarray, tree: Tree) -> np.ndarray:
+    """X = B L^{-T} (L lower) by Alg. 2 with the precision list applied by depth."""
+    X = np.array(B, dtype=np.float64, copy=True)
+    L = np.tril(np.asarray(L, dtype=np.float64))
+    m, n = X.shape
+
+    def leaf(c0, nc, p):
+        dt = np.float64 if p == "F64" else np.float32
+        X[:, c0:c0 + nc] = dense.trsm_rlt(X[:, c0:c0 + nc], L[c0:c0 + nc, c0:c0 + nc], dt)
+
+    def gemm(p, c0, n1, n2):
+        X1, a1 = _operand(p, X[:, c0:c0 + n1])
+        L21, a2 = _operand(p, L[c0 + n1:c0 + n1 + n2, c0:c0 + n1])
+        X[:, c0 + n1:c0 + n1 + n2] -= (a1 * a2) * (X1 @ L21.T)   # B2 -= B1 L21^T
+
+    def rec(c0, nc, depth):
+        p = node_prec(tree, depth, nc)
+        if min(m, nc) <= tree.tleaf():
+            leaf(c0, nc, p)
+            return
+        n1 = split(nc)
+        rec(c0, n1, depth + 1)
+        gemm(p, c0, n1, nc - n1)
+        rec(c0 + n1, nc - n1, depth + 1)
+
+    if m and n:
+        rec(0, n, 0)
+    return X

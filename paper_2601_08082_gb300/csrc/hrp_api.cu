@@ -1790,3 +1790,231 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
   if (!conv) return set_err(h, HRP_ERR_NO_CONVERGENCE, "a system did not reach tol");
   return HRP_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Standalone Tree-SYRK (Alg. 3) and Tree-TRSM (Alg. 2) with the precision list applied to
+// their own recursion (Sec. 4.2's SYRK and TRSM experiments): the GEMM of a node at
+// recursion depth t runs at level[t] (nodes deeper than the list use its last entry; a
+// node of order <= inner_size uses `inner`), and the base case at the precision of its node.
+// ---------------------------------------------------------------------------------------
+namespace hrp {
+namespace {
+
+struct Blas3 {
+  hrp_handle* h;
+  const hrp_tree* t;
+  cudaStream_t s;
+  cudaError_t err = cudaSuccess;
+  long long launches = 0;
+  void chk(cudaError_t e) {
+    ++launches;
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  int prec(int depth, int order) const { return node_prec(t, depth, order); }
+};
+
+// C (n x n lower, ldc) -= A A^T with A n x k (lda).  S16: row-major FP16 copy of A (lds), A32:
+// column-major FP32 copy (ld32), each present when the tree has that precision.
+struct SyrkRun : Blas3 {
+  double* C;
+  int ldc;
+  const double* A;
+  int lda, k;
+  const __half* S16;
+  int lds;
+  const float* A32;
+  int ld32;
+  bool tc;
+  int base() const { return t->syrk_leaf ? t->syrk_leaf : t->leaf; }
+  // C[r0:r0+m, c0:c0+nd] -= A[r0:r0+m, :] A[c0:c0+nd, :]^T at precision p
+  void gemm(int p, int r0, int m, int c0, int nd, bool lower) {
+    double* Cb = C + (size_t)c0 * ldc + r0;
+    switch (p) {
+      case HRP_F64:
+        chk(launch_gemm_simt(Cb, ldc, A + r0, lda, A + c0, lda, m, nd, k, OpRound::F64, lower, s));
+        break;
+      case HRP_F32:
+        chk(launch_gemm_simt_f32(Cb, ldc, A32 + r0, ld32, A32 + c0, ld32, m, nd, k, lower, s));
+        break;
+      case HRP_F16:
+        if (tc && k >= 16) chk(launch_gemm_f16_tc(Cb, ldc, S16, lds, r0, c0, 0, m, nd, k, lower, 1.0, h->d_err, s));
+        else chk(launch_gemm_simt(Cb, ldc, A + r0, lda, A + c0, lda, m, nd, k, OpRound::F16, lower, s));
+        break;
+      default:
+        if (err == cudaSuccess) err = cudaErrorNotSupported;
+    }
+  }
+  void rec(int c0, int nc, int depth) {
+    if (nc <= 0) return;
+    const int p = prec(depth, nc);
+    if (nc <= base()) {                          // base case: the lower triangle of one GEMM
+      gemm(p, c0, nc, c0, nc, true);
+      return;
+    }
+    const int n1 = split(nc), n2 = nc - n1;
+    rec(c0, n1, depth + 1);
+    gemm(p, c0 + n1, n2, c0, n1, false);         // C21 -= A2 A1^T
+    rec(c0 + n1, n2, depth + 1);
+  }
+};
+
+// B (m x n, ldb) <- B L^{-T} with L n x n lower (ldl).  S16: row-major FP16 rows [0, m) hold B's
+// solved columns (written by the base cases), rows [m, m + n) L; B32 / L32: column-major FP32
+// copies (ld m and n).
+struct TrsmRun : Blas3 {
+  double* B;
+  int ldb, m;
+  const double* L;
+  int ldl;
+  __half* S16;
+  int lds;
+  float* B32;
+  const float* L32;
+  bool tc;
+  int* info;
+  int tleaf() const { return t->trsm_leaf ? t->trsm_leaf : t->leaf; }
+  void leaf(int c0, int nc, int p) {
+    if (p == HRP_F64 || t->trsm_compute == 1)
+      chk(launch_trsm_leaf64(B, ldb, 0, m, c0, nc, S16, lds, B32, m, info, h->d_err, s, L, ldl));
+    else
+      chk(launch_trsm_leaf32_subst(B, ldb, 0, m, c0, nc, S16, lds, B32, m, info, h->d_err, s, L, ldl));
+  }
+  // B[:, c0+n1 : c0+nc] -= B[:, c0 : c0+n1] L[c0+n1 : c0+nc, c0 : c0+n1]^T at precision p
+  void gemm(int p, int c0, int n1, int n2) {
+    double* Cb = B + (size_t)(c0 + n1) * ldb;
+    switch (p) {
+      case HRP_F64:
+        chk(launch_gemm_simt(Cb, ldb, B + (size_t)c0 * ldb, ldb, L + (size_t)c0 * ldl + c0 + n1, ldl, m, n2, n1,
+                             OpRound::F64, false, s));
+        break;
+      case HRP_F32:
+        chk(launch_gemm_simt_f32(Cb, ldb, B32 + (size_t)c0 * m, m, L32 + (size_t)c0 * t_n + c0 + n1, t_n, m, n2, n1,
+                                 false, s));
+        break;
+      case HRP_F16:
+        if (tc && c0 % 8 == 0 && n1 >= 16)
+          chk(launch_gemm_f16_tc(Cb, ldb, S16, lds, 0, m + c0 + n1, c0, m, n2, n1, false, 1.0, h->d_err, s));
+        else
+          chk(launch_gemm_simt(Cb, ldb, B + (size_t)c0 * ldb, ldb, L + (size_t)c0 * ldl + c0 + n1, ldl, m, n2, n1,
+                               OpRound::F16, false, s));
+        break;
+      default:
+        if (err == cudaSuccess) err = cudaErrorNotSupported;
+    }
+  }
+  int t_n = 0;                                   // order of L (leading dimension of L32)
+  void rec(int c0, int nc, int depth) {
+    const int p = prec(depth, nc);
+    if (std::min(m, nc) <= tleaf()) {
+      leaf(c0, nc, p);
+      return;
+    }
+    const int n1 = split(nc), n2 = nc - n1;
+    rec(c0, n1, depth + 1);
+    gemm(p, c0, n1, n2);
+    rec(c0 + n1, n2, depth + 1);
+  }
+};
+
+hrp_status blas3_tree_check(hrp_handle* h, const hrp_tree* tree) {
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (tree_has(tree, HRP_F8E4M3)) return set_err(h, HRP_ERR_UNSUPPORTED, "F8 levels need the factorization's tiles");
+  return HRP_OK;
+}
+
+}  // namespace
+}  // namespace hrp
+
+extern "C" {
+
+hrp_status hrp_syrk(hrp_handle* h, const hrp_tree* tree, int n, int k, const double* dA, int lda, double* dC, int ldc,
+                    void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = blas3_tree_check(h, tree);
+  if (st != HRP_OK) return st;
+  if (n < 0) return bad_arg(h, 3, "n < 0");
+  if (k < 0) return bad_arg(h, 4, "k < 0");
+  if (n > 0 && k > 0 && !dA) return bad_arg(h, 5, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 6, "lda < max(1, n)");
+  if (n > 0 && !dC) return bad_arg(h, 7, "dC is NULL");
+  if (ldc < (n > 1 ? n : 1)) return bad_arg(h, 8, "ldc < max(1, n)");
+  if (n == 0 || k == 0) return HRP_OK;
+  cudaSetDevice(h->device);
+  SyrkRun r{};
+  r.h = h;
+  r.t = tree;
+  r.s = static_cast<cudaStream_t>(stream);
+  r.C = dC;
+  r.ldc = ldc;
+  r.A = dA;
+  r.lda = lda;
+  r.k = k;
+  r.tc = tc_gemm_supported();
+  r.lds = (k + 63) / 64 * 64;
+  r.ld32 = n;
+  if (tree_has(tree, HRP_F16)) {
+    if ((st = ensure(h, &h->shadow, &h->shadow_cap, (size_t)n * r.lds)) != HRP_OK) return st;
+    r.S16 = h->shadow;
+    r.chk(launch_cast_f16_rows(dA, lda, n, k, h->shadow, r.lds, h->d_err, r.s));
+  }
+  if (tree_has(tree, HRP_F32)) {
+    if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)n * k)) != HRP_OK) return st;
+    r.A32 = h->shadow32;
+    r.chk(launch_cast_f32(dA, lda, n, k, h->shadow32, n, r.s));
+  }
+  r.rec(0, n, 0);
+  launch_ctx() = LaunchCtx{};
+  h->launches = r.launches;
+  return cuda_status(h, r.err, "hrp_syrk");
+}
+
+hrp_status hrp_trsm(hrp_handle* h, const hrp_tree* tree, int m, int n, const double* dL, int ldl, double* dB, int ldb,
+                    void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = blas3_tree_check(h, tree);
+  if (st != HRP_OK) return st;
+  if (m < 0) return bad_arg(h, 3, "m < 0");
+  if (n < 0) return bad_arg(h, 4, "n < 0");
+  if (n > 0 && !dL) return bad_arg(h, 5, "dL is NULL");
+  if (ldl < (n > 1 ? n : 1)) return bad_arg(h, 6, "ldl < max(1, n)");
+  if (m > 0 && n > 0 && !dB) return bad_arg(h, 7, "dB is NULL");
+  if (ldb < (m > 1 ? m : 1)) return bad_arg(h, 8, "ldb < max(1, m)");
+  if (m == 0 || n == 0) return HRP_OK;
+  const int tl = tree->trsm_leaf ? tree->trsm_leaf : tree->leaf;
+  if (tl > 128 && m > 128) return bad_arg(h, 2, "trsm_leaf must be <= 128");
+  cudaSetDevice(h->device);
+  TrsmRun r{};
+  r.h = h;
+  r.t = tree;
+  r.s = static_cast<cudaStream_t>(stream);
+  r.B = dB;
+  r.ldb = ldb;
+  r.m = m;
+  r.L = dL;
+  r.ldl = ldl;
+  r.t_n = n;
+  r.tc = tc_gemm_supported();
+  r.lds = (n + 63) / 64 * 64;
+  r.info = h->d_info;
+  r.chk(launch_fill_int(h->d_info, INT_MAX, 1, r.s));
+  if (tree_has(tree, HRP_F16)) {
+    if ((st = ensure(h, &h->shadow, &h->shadow_cap, (size_t)(m + n) * r.lds)) != HRP_OK) return st;
+    r.S16 = h->shadow;
+    r.chk(launch_cast_f16_rows(dL, ldl, n, n, h->shadow + (size_t)m * r.lds, r.lds, h->d_err, r.s));
+  }
+  if (tree_has(tree, HRP_F32)) {
+    if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)m * n + (size_t)n * n)) != HRP_OK) return st;
+    r.B32 = h->shadow32;
+    r.L32 = h->shadow32 + (size_t)m * n;
+    r.chk(launch_cast_f32(dL, ldl, n, n, h->shadow32 + (size_t)m * n, n, r.s));
+  }
+  r.rec(0, n, 0);
+  launch_ctx() = LaunchCtx{};
+  h->launches = r.launches;
+  return cuda_status(h, r.err, "hrp_trsm");
+}
+
+}  // extern "C"

@@ -88,9 +88,10 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
 // (column-major, ld32, the master's indexing) FP32(X), each if non-null.  An entry of X
 // beyond kF16Max written to shadow16 sets DEV_ERR_RANGE16 in err (the FP16 operand would
 // need the Sec. 3.4 scale alpha > 1).
+// Lm, ldl: the matrix holding L when it is not A (a standalone TRSM); nullptr = A.
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
                                __half* shadow16, int lds, float* shadow32, int ld32, const int* info, unsigned* err,
-                               cudaStream_t s);
+                               cudaStream_t s, const double* Lm = nullptr, int ldl = 0);
 // Same in FP32 using the precomputed FP32 inverse W (nc x nc lower, ldw) of the block:
 // X = fl32(B) * W^T, result stored in FP64.
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
@@ -99,7 +100,7 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
 // FP32 substitution variant (no inverse), for blocks whose inverse is not available.
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
                                      __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
-                                     unsigned* err, cudaStream_t s);
+                                     unsigned* err, cudaStream_t s, const double* Lm = nullptr, int ldl = 0);
 
 // ---------------- SIMT GEMM (k_gemm_simt.cu) ----------------
 // C[m x n] -= X[m x k] * Y[n x k]^T, all FP64 column-major views of the master, with
@@ -177,6 +178,12 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
 // every 128 x 128 tile strictly below the diagonal tiles of A[off:off+nb, off:off+nb]
 cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, int lds, int* tile_exp,
                                     int ntile_ld, int G, unsigned* err, cudaStream_t s);
+// Operand copies for the standalone SYRK / TRSM: the m x k block X (column-major, ldx) into
+// S16 row-major (S16[r * lds + c], round to nearest even; an entry beyond kF16Max sets
+// DEV_ERR_RANGE16 in err) and into S32 column-major (S32[c * ld32 + r]).
+cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
+                                 cudaStream_t s);
+cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s);
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 

@@ -244,13 +244,14 @@ potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
 // ---------------------------------------------------------------------------------------
 // Leaf TRSM in FP64 (Alg. 2 base case "B <- TRSM(...; L, B)", right side, lower,
 // transposed): each thread owns one row of B and substitutes column by column,
-// x_j = (b_j - sum_{k<j} x_k l_jk) / l_jj.
+// x_j = (b_j - sum_{k<j} x_k l_jk) / l_jj.  B = A[r0.., c0..] and L = Lm[c0.., c0..]
+// (Lm = A inside the factorization, a separate factor for a standalone TRSM).
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(64)
-trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
-                  __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32, const int* __restrict__ info,
-                  unsigned* __restrict__ err, int rows_per_cta) {
+trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc, const double* __restrict__ Lm,
+                  int ldl, __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32,
+                  const int* __restrict__ info, unsigned* __restrict__ err, int rows_per_cta) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,7 +263,7 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
   const int row0 = blockIdx.x * RT;
   for (int idx = tid; idx < nc * nc; idx += blockDim.x) {
     int k = idx % nc, j = idx / nc;
-    Ls[j * nc + k] = (k <= j) ? (T)A[(size_t)(c0 + k) * ld + (c0 + j)] : (T)0;
+    Ls[j * nc + k] = (k <= j) ? (T)Lm[(size_t)(c0 + k) * ldl + (c0 + j)] : (T)0;
   }
   for (int idx = tid; idx < RT * nc; idx += blockDim.x) {
     int t = idx % RT, k = idx / RT;
@@ -468,7 +469,11 @@ cudaError_t launch_potrf_leaf(double* A, int ld, int n, int col0, bool compute64
 
 cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
                                __half* shadow16, int lds, float* shadow32, int ld32, const int* info, unsigned* err,
-                               cudaStream_t s) {
+                               cudaStream_t s, const double* Lm, int ldl) {
+  if (!Lm) {
+    Lm = A;
+    ldl = ld;
+  }
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = nc <= 128 ? 64 : 32;
@@ -482,13 +487,18 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
     attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
-  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, err, RT);
+  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds,
+                   shadow32, ld32, info, err, RT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
                                      __half* shadow16, int lds, float* shadow32, int ld32, const int* info,
-                                     unsigned* err, cudaStream_t s) {
+                                     unsigned* err, cudaStream_t s, const double* Lm, int ldl) {
+  if (!Lm) {
+    Lm = A;
+    ldl = ld;
+  }
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
   int RT = 64;
@@ -502,7 +512,8 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
     attr_mask |= attr_bit;
   }
   int grid = (m + RT - 1) / RT;
-  (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, shadow16, lds, shadow32, ld32, info, err, RT);
+  (void)launch_pdl(trsm_subst_kernel<float>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds,
+                   shadow32, ld32, info, err, RT);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 // and the FP64 backward error ||A - L L^T||_F / ||A||_F (Sec. 4.2 accuracy metric).
 #include <climits>
 
+#include <algorithm>
+
 #include "hrp_internal.cuh"
 
 namespace hrp {
@@ -300,6 +302,60 @@ cudaError_t launch_backward_error(const double* A, int lda, const double* L, int
   backward_error_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(A, lda, L, ldl, n, out);
   return cudaGetLastError();
 }
+// 32 x 32 tiles through shared memory: coalesced reads of the column-major block and
+// coalesced writes of the row-major copy
+__global__ void __launch_bounds__(256) cast_f16_rows_kernel(const double* __restrict__ X, int ldx, int m, int k,
+                                                            __half* __restrict__ S, int lds, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 8 rows of threads
+  for (int c = ty; c < 32; c += 8) {
+    const int gr = r0 + tx, gc = c0 + c;
+    t[c][tx] = (gr < m && gc < k) ? X[(size_t)gc * ldx + gr] : 0.0;
+  }
+  __syncthreads();
+  bool over = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int gr = r0 + r, gc = c0 + tx;
+    if (gr < m && gc < k) {
+      const double v = t[tx][r];
+      over |= fabs(v) > (double)kF16Max;
+      S[(size_t)gr * lds + gc] = __double2half(v);
+    }
+  }
+  if (__any_sync(0xffffffffu, over) && tx == 0) atomicOr(err, DEV_ERR_RANGE16);
+}
+
+__global__ void __launch_bounds__(256) cast_f32_kernel(const double* __restrict__ X, int ldx, int m, int k,
+                                                       float* __restrict__ S, int ld32) {
+  pdl_wait();
+  pdl_trigger();
+  const long long total = (long long)m * k;
+  for (long long e = blockIdx.x * 256ll + threadIdx.x; e < total; e += (long long)gridDim.x * 256) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    S[(size_t)c * ld32 + r] = (float)X[(size_t)c * ldx + r];
+  }
+}
+
+cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
+                                 cudaStream_t s) {
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  const dim3 grid((m + 31) / 32, (k + 31) / 32);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  (void)launch_pdl(cast_f16_rows_kernel, grid, dim3(256), 0, s, X, ldx, m, k, S16, lds, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s) {
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  const long long total = (long long)m * k;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 8LL * device_sm_count());
+  (void)launch_pdl(cast_f32_kernel, dim3(grid), dim3(256), 0, s, X, ldx, m, k, S32, ld32);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   diag_check_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(A, lda, n, limit, flag);

@@ -33,7 +33,7 @@ EXPORTED = [
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
-    "hrp_wait_selftest", "hrp_set_lookahead",
+    "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm",
 ]
 
 
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
     L.hrp_backward_error.argtypes = [vp, c_int, vp, c_int, vp, c_int, dp, vp]
     L.hrp_set_timing.argtypes = [vp, c_int]
     L.hrp_set_lookahead.argtypes = [vp, c_int]
+    L.hrp_syrk.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp]
+    L.hrp_trsm.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_get_timing.argtypes = [vp, dp, c_int]
     L.hrp_last_launch_count.argtypes = [vp]
     L.hrp_last_launch_count.restype = ctypes.c_longlong
@@ -183,6 +185,18 @@ class Handle:
 
     def launch_count(self) -> int:
         return self._lib.hrp_last_launch_count(self._h)
+
+    def syrk(self, tree: Tree, A, C, stream=None) -> None:
+        """C (n, ldc) column-major, lower triangle -= A A^T with A (k, lda) column-major n x k."""
+        n, k = C.shape[0], A.shape[0]
+        self._check(self._lib.hrp_syrk(self._h, ctypes.byref(tree), n, k, _ptr(A), A.shape[1], _ptr(C), C.shape[1],
+                                       _stream(stream)))
+
+    def trsm(self, tree: Tree, L, B, stream=None) -> None:
+        """B (n, ldb) column-major m x n <- B L^{-T}, L (n, ldl) column-major lower."""
+        n, m = L.shape[0], B.shape[1]
+        self._check(self._lib.hrp_trsm(self._h, ctypes.byref(tree), m, n, _ptr(L), L.shape[1], _ptr(B), B.shape[1],
+                                       _stream(stream)))
 
     def set_lookahead(self, enable: bool) -> None:
         self._check(self._lib.hrp_set_lookahead(self._h, 1 if enable else 0))
