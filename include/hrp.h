@@ -147,6 +147,20 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * Refinement of hrp_posv.  mode 0 (default): classical iterative refinement, each
+ * correction an FP32 POTRS with the factor.  mode 1: GMRES-IR (Carson and Higham, the
+ * refinement literature of the paper's Sec. 1-2): each correction d solves A d = r by
+ * GMRES on M^{-1} A d = M^{-1} r (M = L L^T the computed factor, applied by an FP64 POTRS;
+ * FP64 products with A) from d = 0, at most `restart` steps (1..60), stopped when the
+ * preconditioned residual falls to inner_tol (0 < inner_tol < 1) of its start; it converges
+ * where the classical iteration stalls or diverges (kappa(A) times the factor's error
+ * above 1).  The outer loop, stopping rule and fallback tree are those of hrp_posv.
+ * hrp_last_inner_iterations: GMRES steps of the last hrp_posv (0 in mode 0).
+ */
+hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner_tol);
+long long hrp_last_inner_iterations(const hrp_handle* h);
+
+/*
  * Relative backward error ||A - L L^T||_F / ||A||_F computed on the device in FP64
  * (A symmetric from its lower triangle in dA; L from the lower triangle of dL).
  * *out is a host double. Synchronous.

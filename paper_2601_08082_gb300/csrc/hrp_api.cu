@@ -11,6 +11,7 @@
 // exactly one GEMM (or leaf SYRK) of the recursion with the full inner dimension and the
 // node's precision, so the flattened launch performs the same arithmetic per entry.
 #include <algorithm>
+#include <cmath>
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
@@ -84,6 +85,13 @@ struct hrp_handle_s {
   bool lookahead = true;
   std::vector<cudaStream_t> lstreams;
   std::vector<cudaEvent_t> levents;
+  // refinement of hrp_posv: 0 = classical (POTRS corrections), 1 = GMRES-IR
+  int refine_mode = 0;
+  int gmres_restart = 20;
+  double gmres_tol = 1e-8;
+  double* kwork = nullptr;     // GMRES basis and vectors
+  size_t kwork_cap = 0;
+  long long inner_steps = 0;   // GMRES steps of the last hrp_posv
 };
 
 namespace hrp {
@@ -640,6 +648,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   for (cudaEvent_t e : h->levents) cudaEventDestroy(e);
   cudaFree(h->bwork);
   cudaFree(h->fwork);
+  cudaFree(h->kwork);
   cudaFree(h->policy);
   cudaFree(h->pio);
   delete h;
@@ -785,6 +794,90 @@ hrp_status hrp_potrs(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, 
   return potrs_impl(h, n, nrhs, dL, ldl, dB, ldb, false, static_cast<cudaStream_t>(stream));
 }
 
+// One GMRES-IR correction for one right-hand side (Carson and Higham): x += d, where d solves
+// A d = r by GMRES on M^{-1} A d = M^{-1} r from d = 0 with M = L L^T the factor in h->fact,
+// applied by the FP64 POTRS; classical Gram-Schmidt twice, Givens rotations on the host,
+// stop at |g_k| <= gmres_tol * beta or after gmres_restart steps.  Matrix-vector products
+// in FP64 from A's lower triangle.  Synchronous (a few 8-byte reads per step).
+static hrp_status gmres_correction(hrp_handle* h, const double* dA, int lda, int n, const double* r, double* x,
+                                   cudaStream_t s) {
+  const int m = h->gmres_restart;
+  hrp_status st = ensure(h, &h->kwork, &h->kwork_cap, (size_t)(m + 1) * n + 2 * (size_t)n + 2 * (m + 1));
+  if (st != HRP_OK) return st;
+  double* V = h->kwork;
+  double* w = V + (size_t)(m + 1) * n;
+  double* zero = w + n;
+  double* hd = zero + n;
+  double* hh = h->h_norms;                       // pinned host mirror (128 doubles)
+  cudaError_t e = cudaMemsetAsync(zero, 0, sizeof(double) * n, s);
+  auto sync_read = [&](int cnt) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hh, hd, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  };
+  // v0 = M^{-1} r / beta
+  if (e == cudaSuccess) e = cudaMemcpyAsync(V, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_status(h, e, "gmres");
+  if ((st = potrs_impl(h, n, 1, h->fact, n, V, n, false, s)) != HRP_OK) return st;
+  e = launch_multi_dot(V, n, 1, V, n, hd, s);
+  sync_read(1);
+  if (e != cudaSuccess) return cuda_status(h, e, "gmres");
+  const double beta = sqrt(hh[0]);
+  if (!(beta > 0.0) || !std::isfinite(beta)) return HRP_OK;   // nothing to correct (or NaN: left to the caller)
+  e = launch_scale(V, V, 1.0 / beta, n, false, s);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
+  g[0] = beta;
+  int k = 0;
+  while (k < m && e == cudaSuccess) {
+    double* vk = V + (size_t)k * n;
+    // w = M^{-1} A v_k (the residual kernel gives -A v_k from a zero right-hand side)
+    e = launch_residual(dA, lda, vk, n, zero, n, w, n, n, 1, s);
+    if (e == cudaSuccess) e = launch_scale(w, w, -1.0, n, false, s);
+    if (e != cudaSuccess) break;
+    if ((st = potrs_impl(h, n, 1, h->fact, n, w, n, false, s)) != HRP_OK) return st;
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+      e = launch_multi_dot(V, n, k + 1, w, n, hd, s);
+      if (e == cudaSuccess) e = launch_gemv_sub(w, V, n, k + 1, hd, n, s);
+      sync_read(k + 1);
+      for (int i = 0; i <= k; ++i) Hat(i, k) += hh[i];
+    }
+    if (e == cudaSuccess) e = launch_multi_dot(w, n, 1, w, n, hd, s);
+    sync_read(1);
+    if (e != cudaSuccess) break;
+    const double hn = sqrt(hh[0]);
+    Hat(k + 1, k) = hn;
+    for (int i = 0; i < k; ++i) {                 // earlier rotations on the new column
+      const double a = Hat(i, k), b = Hat(i + 1, k);
+      Hat(i, k) = cs[i] * a + sn[i] * b;
+      Hat(i + 1, k) = -sn[i] * a + cs[i] * b;
+    }
+    const double a = Hat(k, k), b = Hat(k + 1, k), rho = std::hypot(a, b);
+    cs[k] = rho > 0 ? a / rho : 1.0;
+    sn[k] = rho > 0 ? b / rho : 0.0;
+    Hat(k, k) = rho;
+    Hat(k + 1, k) = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    if (hn > 0.0) e = launch_scale(V + (size_t)(k + 1) * n, w, 1.0 / hn, n, false, s);
+    ++k;
+    if (!(fabs(g[k]) > h->gmres_tol * beta) || !(hn > 0.0)) break;
+  }
+  if (e != cudaSuccess) return cuda_status(h, e, "gmres");
+  // y from the rotated (upper triangular) H, then x += V y
+  std::vector<double> y(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int j = i + 1; j < k; ++j) t -= Hat(i, j) * y[j];
+    y[i] = t / Hat(i, i);
+  }
+  for (int i = 0; i < k; ++i) hh[i] = -y[i];
+  e = cudaMemcpyAsync(hd, hh, sizeof(double) * k, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_gemv_sub(x, V, n, k, hd, n, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);        // hh is reused by the caller
+  h->inner_steps += k;
+  return cuda_status(h, e, "gmres");
+}
+
 hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const double* dA, int lda, const double* dB,
                     int ldb, double* dX, int ldx, int max_iter, double tol, int* iters, double* resid, int* info,
                     int* used_fallback, void* stream) {
@@ -817,6 +910,7 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
   if (resid) *resid = 0.0;
   if (info) *info = 0;
   if (used_fallback) *used_fallback = 0;
+  h->inner_steps = 0;
   if (n == 0 || nrhs == 0) return HRP_OK;
   if ((st = ensure(h, &h->fact, &h->fact_cap, (size_t)n * n)) != HRP_OK) return st;
   if ((st = ensure(h, &h->work, &h->work_cap, (size_t)n * nrhs)) != HRP_OK) return st;
@@ -868,8 +962,15 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs, const 
       if (worst <= tol || it >= max_iter) break;
       if (!(worst < prev)) { diverged = true; break; }   // no decrease: this factor will not get there
       prev = worst;
-      if ((st = potrs_impl(h, n, nrhs, h->fact, n, h->work, n, true, s)) != HRP_OK) return st;
-      if ((e = launch_axpy_matrix(dX, ldx, h->work, n, n, nrhs, s)) != cudaSuccess) return cuda_status(h, e, "hrp_posv");
+      if (h->refine_mode == 1) {
+        for (int c = 0; c < nrhs; ++c)
+          if ((st = gmres_correction(h, dA, lda, n, h->work + (size_t)c * n, dX + (size_t)c * ldx, s)) != HRP_OK)
+            return st;
+      } else {
+        if ((st = potrs_impl(h, n, nrhs, h->fact, n, h->work, n, true, s)) != HRP_OK) return st;
+        if ((e = launch_axpy_matrix(dX, ldx, h->work, n, n, nrhs, s)) != cudaSuccess)
+          return cuda_status(h, e, "hrp_posv");
+      }
       ++it;
     }
     if (worst <= tol || (!diverged && attempt == 1)) break;
@@ -1026,6 +1127,20 @@ hrp_status hrp_set_timing(hrp_handle* h, int enable) {
   h->timing = enable != 0;
   return HRP_OK;
 }
+
+hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner_tol) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (mode != 0 && mode != 1) return bad_arg(h, 2, "mode must be 0 (classical) or 1 (GMRES)");
+  if (restart < 1 || restart > 60) return bad_arg(h, 3, "restart must be in [1, 60]");
+  if (!(inner_tol > 0.0 && inner_tol < 1.0)) return bad_arg(h, 4, "inner_tol must be in (0, 1)");
+  h->refine_mode = mode;
+  h->gmres_restart = restart;
+  h->gmres_tol = inner_tol;
+  return HRP_OK;
+}
+
+long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
 
 hrp_status hrp_set_lookahead(hrp_handle* h, int enable) {
   if (!h) return HRP_ERR_INVALID_ARG;

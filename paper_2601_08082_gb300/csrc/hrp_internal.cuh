@@ -184,6 +184,12 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
 cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
                                  cudaStream_t s);
 cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s);
+// Krylov helpers (FP64 vectors of length n; V column-major with leading dimension ldv):
+// out[j] = V[:, j] . w for j < nv (out device, zeroed here); w -= V[:, 0:nv] c (c device);
+// y = a x, or y += a x when accumulate.
+cudaError_t launch_multi_dot(const double* V, int ldv, int nv, const double* w, int n, double* out, cudaStream_t s);
+cudaError_t launch_gemv_sub(double* w, const double* V, int ldv, int nv, const double* c, int n, cudaStream_t s);
+cudaError_t launch_scale(double* y, const double* x, double a, int n, bool accumulate, cudaStream_t s);
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 

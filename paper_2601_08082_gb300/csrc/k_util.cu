@@ -356,6 +356,59 @@ cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, 
   return cudaGetLastError();
 }
 
+// ---- Krylov helpers of the GMRES refinement (FP64) ----
+// out[j] += sum_i V[j ldv + i] w[i] for j < nv: blocks of 1024 rows per column, reduced in
+// shared memory, one FP64 atomic per block and column (out is zeroed by the caller)
+__global__ void __launch_bounds__(256) multi_dot_kernel(const double* __restrict__ V, int ldv, int nv,
+                                                         const double* __restrict__ w, int n, double* out) {
+  __shared__ double red[8];
+  const int j = blockIdx.y;
+  const int i0 = blockIdx.x * 1024;
+  double acc = 0.0;
+  for (int i = i0 + threadIdx.x; i < min(n, i0 + 1024); i += 256) acc = fma(V[(size_t)j * ldv + i], w[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    atomicAdd(out + j, t);
+  }
+}
+// w[i] -= sum_{j<nv} V[j ldv + i] c[j] (c on the device)
+__global__ void gemv_sub_kernel(double* __restrict__ w, const double* __restrict__ V, int ldv, int nv,
+                                const double* __restrict__ c, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < nv; ++j) acc = fma(-V[(size_t)j * ldv + i], c[j], acc);
+    w[i] = acc;
+  }
+}
+// y = a x (+ y when accumulate)
+__global__ void scale_kernel(double* __restrict__ y, const double* __restrict__ x, double a, int n, int accumulate) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = accumulate ? fma(a, x[i], y[i]) : a * x[i];
+}
+
+cudaError_t launch_multi_dot(const double* V, int ldv, int nv, const double* w, int n, double* out, cudaStream_t s) {
+  if (n <= 0 || nv <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nv, s);
+  if (e != cudaSuccess) return e;
+  multi_dot_kernel<<<dim3((n + 1023) / 1024, nv), 256, 0, s>>>(V, ldv, nv, w, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_gemv_sub(double* w, const double* V, int ldv, int nv, const double* c, int n, cudaStream_t s) {
+  if (n <= 0 || nv <= 0) return cudaSuccess;
+  gemv_sub_kernel<<<std::min((n + 255) / 256, 4 * device_sm_count()), 256, 0, s>>>(w, V, ldv, nv, c, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale(double* y, const double* x, double a, int n, bool accumulate, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  scale_kernel<<<std::min((n + 255) / 256, 4 * device_sm_count()), 256, 0, s>>>(y, x, a, n, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   diag_check_kernel<<<grid_for((size_t)n, 256), 256, 0, s>>>(A, lda, n, limit, flag);

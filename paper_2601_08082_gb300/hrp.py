@@ -33,7 +33,8 @@ EXPORTED = [
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
-    "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm",
+    "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
+    "hrp_last_inner_iterations",
 ]
 
 
@@ -79,6 +80,9 @@ def load(path: str = LIB_PATH):
     L.hrp_backward_error.argtypes = [vp, c_int, vp, c_int, vp, c_int, dp, vp]
     L.hrp_set_timing.argtypes = [vp, c_int]
     L.hrp_set_lookahead.argtypes = [vp, c_int]
+    L.hrp_set_refinement.argtypes = [vp, c_int, c_int, c_double]
+    L.hrp_last_inner_iterations.argtypes = [vp]
+    L.hrp_last_inner_iterations.restype = ctypes.c_longlong
     L.hrp_syrk.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_trsm.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_get_timing.argtypes = [vp, dp, c_int]
@@ -197,6 +201,13 @@ class Handle:
         n, m = L.shape[0], B.shape[1]
         self._check(self._lib.hrp_trsm(self._h, ctypes.byref(tree), m, n, _ptr(L), L.shape[1], _ptr(B), B.shape[1],
                                        _stream(stream)))
+
+    def set_refinement(self, gmres: bool, restart: int = 20, inner_tol: float = 1e-8) -> None:
+        """hrp_set_refinement: classical refinement, or GMRES-IR with this restart and tolerance."""
+        self._check(self._lib.hrp_set_refinement(self._h, 1 if gmres else 0, restart, inner_tol))
+
+    def inner_iterations(self) -> int:
+        return self._lib.hrp_last_inner_iterations(self._h)
 
     def set_lookahead(self, enable: bool) -> None:
         self._check(self._lib.hrp_set_lookahead(self._h, 1 if enable else 0))
