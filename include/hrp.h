@@ -68,6 +68,10 @@ typedef enum { HRP_F64 = 0, HRP_F32 = 1, HRP_F16 = 2, HRP_F8E4M3 = 3 } hrp_prec;
  *   scale_block: tile edge of the FP8 power-of-two scales (128).
  *   trsm_compute: arithmetic of a leaf TRSM at a reduced-precision (F32/F16/F8) level:
  *     0 = FP32 (default), 1 = FP64.  Leaf TRSMs at F64 levels are always FP64.
+ *   tile_occupancy: tile width rule of the FP16/FP8 tensor-core GEMMs: each launch takes
+ *     the widest tile (256, 128, 64 or 32 columns) that still gives at least
+ *     tile_occupancy tiles per SM (0 = 1).  1, 2 and 4 are meaningful; the autotuner
+ *     chooses among them.
  * Split point of a node of order n (reading of "e.g. n1 = floor(n/2)"): n/2 rounded to
  * the nearest multiple of 128 for n >= 512, of 16 for 32 <= n < 512, floor(n/2) below.
  */
@@ -81,6 +85,7 @@ typedef struct {
   int syrk_leaf;
   int scale_block;
   int trsm_compute;
+  int tile_occupancy;
 } hrp_tree;
 
 typedef struct hrp_handle_s hrp_handle;
@@ -197,9 +202,10 @@ hrp_status hrp_set_lookahead(hrp_handle* h, int enable);
  * precision list, the inner region and trsm_compute are never changed.
  * hrp_autotune_candidates (host only, no device work): writes up to `cap` candidate trees
  *   into out and returns how many there are (-1 for an invalid tree): the given tree
- *   first, then leaf in {128, 64, 32} with trsm_leaf in {leaf, leaf/2}, without
- *   duplicates.  A tree with an F8 level admits only leaf = trsm_leaf = 128 (its E4M3
- *   tiles live on the 128 x 128 grid), so it is its only candidate.
+ *   first, then leaf in {128, 64, 32} with trsm_leaf in {leaf, leaf/2}, then, for trees
+ *   with an F16 or F8 level, each of those with tile_occupancy 2 and 4; no duplicates, at
+ *   most 24.  A tree with an F8 level admits only leaf = trsm_leaf = 128 (its E4M3 tiles
+ *   live on the 128 x 128 grid).
  * hrp_autotune: factors a seeded SPD matrix of order n (1 <= n <= 65535) drawn on the
  *   device (off-diagonal entries uniform in [-1, 1), n on the diagonal, the paper's
  *   synthetic generator of Sec. 4.1) with every candidate: one warm-up, then `reps`
@@ -213,6 +219,14 @@ hrp_status hrp_set_lookahead(hrp_handle* h, int enable);
  *   returned; other candidates that fail are skipped.
  */
 int hrp_autotune_candidates(const hrp_tree* tree, hrp_tree* out, int cap);
+/*
+ * hrp_autotune_orders: hrp_autotune for each of the `count` orders in orders[] (host
+ *   array).  The batched calls (hrp_potrf_batched, hrp_posv_batched) then give a system of
+ *   order n the cut-offs and tile rule tuned at the largest tuned order <= n with the same
+ *   precisions (its own tree's otherwise).  Synchronous.
+ */
+hrp_status hrp_autotune_orders(hrp_handle* h, const hrp_tree* tree, int count, const int* orders, int reps,
+                               void* stream);
 hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, int flags, hrp_tree* out,
                         float* ms, void* stream);
 

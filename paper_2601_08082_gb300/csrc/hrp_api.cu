@@ -78,8 +78,9 @@ struct hrp_handle_s {
   float* pio = nullptr;        // device, 12 inputs + 8 logits
   bool policy_set = false;
   int last_choice = -1;
-  // autotuner: tuned tree and its median time by (n, precision list, inner region, trsm_compute)
-  std::map<std::string, std::pair<hrp_tree, float>> tune_cache;
+  // autotuner: tuned tree and its median time by (precision list, inner region, trsm_compute)
+  // and order n
+  std::map<std::string, std::map<int, std::pair<hrp_tree, float>>> tune_cache;
   // lookahead: the critical stream (highest priority), side streams by recursion depth, and
   // a pool of events for the dependencies between them
   bool lookahead = true;
@@ -157,6 +158,7 @@ hrp_status validate_tree(hrp_handle* h, const hrp_tree* t, int pos) {
   int sl = t->syrk_leaf ? t->syrk_leaf : t->leaf;
   if (sl < 1) return bad_arg(h, pos, "syrk_leaf < 0");
   if (t->trsm_compute != 0 && t->trsm_compute != 1) return bad_arg(h, pos, "trsm_compute must be 0 or 1");
+  if (t->tile_occupancy < 0 || t->tile_occupancy > 8) return bad_arg(h, pos, "tile_occupancy must be in [0, 8]");
   if (t->level[t->depth - 1] == HRP_F8E4M3 && t->inner_size < t->leaf)
     return bad_arg(h, pos, "the innermost (diagonal) precision cannot be F8");
   return HRP_OK;
@@ -166,6 +168,29 @@ bool tree_has(const hrp_tree* t, int prec) {
   for (int i = 0; i < t->depth; ++i)
     if (t->level[i] == prec) return true;
   return t->inner_size > 0 && t->inner == prec;
+}
+
+// the autotuner's cache key: everything it never changes (precisions, inner region, TRSM
+// arithmetic); the tuned cut-offs and tile rule are filed under it by order
+std::string tune_key(const hrp_tree* t) {
+  std::string k = "d=" + std::to_string(t->depth) + ";in=" + std::to_string(t->inner) + "@" +
+                  std::to_string(t->inner_size) + ";tc=" + std::to_string(t->trsm_compute) + ";L=";
+  for (int i = 0; i < t->depth; ++i) k += std::to_string(t->level[i]) + ",";
+  return k;
+}
+
+// t with the cut-offs and tile rule tuned at the largest tuned order <= n (t unchanged if
+// none was tuned for its precisions)
+void apply_tuned(const hrp_handle* h, hrp_tree* t, int n) {
+  auto it = h->tune_cache.find(tune_key(t));
+  if (it == h->tune_cache.end() || it->second.empty()) return;
+  auto jt = it->second.upper_bound(n);
+  if (jt == it->second.begin()) return;
+  --jt;
+  t->leaf = jt->second.first.leaf;
+  t->trsm_leaf = jt->second.first.trsm_leaf;
+  t->syrk_leaf = jt->second.first.syrk_leaf;
+  t->tile_occupancy = jt->second.first.tile_occupancy;
 }
 
 // ------------------------------------------------------------------------------------
@@ -310,13 +335,14 @@ struct Fact {
         break;
       case HRP_F16:
         if (use_tc)
-          chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s));
+          chk(launch_gemm_f16_tc(C, lda, shadow, lds, r0, c0, k0, m, nd, k, lower, 1.0, h->d_err, s, t->tile_occupancy));
         else
           chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F16, lower, s));
         break;
       case HRP_F8E4M3:
         if (tc && shadow8 && (k0 % 8) == 0 && k >= 16)
-          chk(launch_gemm_f16_tc(C, lda, shadow8, lds, r0, c0, k0, m, nd, k, lower, ldexp(1.0, -2 * kG), h->d_err, s));
+          chk(launch_gemm_f16_tc(C, lda, shadow8, lds, r0, c0, k0, m, nd, k, lower, ldexp(1.0, -2 * kG), h->d_err, s,
+                                 t->tile_occupancy));
         else if (err == cudaSuccess)
           err = cudaErrorNotSupported;
         break;
@@ -1017,7 +1043,9 @@ int hrp_autotune_candidates(const hrp_tree* tree, hrp_tree* out, int cap) {
     t.leaf = leaf;
     t.trsm_leaf = (tl == leaf) ? 0 : tl;
     for (const auto& u : c)
-      if (u.leaf == t.leaf && (u.trsm_leaf ? u.trsm_leaf : u.leaf) == (t.trsm_leaf ? t.trsm_leaf : t.leaf)) return;
+      if (u.leaf == t.leaf && (u.trsm_leaf ? u.trsm_leaf : u.leaf) == (t.trsm_leaf ? t.trsm_leaf : t.leaf) &&
+          u.tile_occupancy == t.tile_occupancy)
+        return;
     if (validate_tree(nullptr, &t, 1) == HRP_OK) c.push_back(t);
   };
   add(tree->leaf, tree->trsm_leaf ? tree->trsm_leaf : tree->leaf);   // the given tree first
@@ -1026,6 +1054,20 @@ int hrp_autotune_candidates(const hrp_tree* tree, hrp_tree* out, int cap) {
       add(leaf, leaf);
       add(leaf, leaf / 2);
     }
+  }
+  // the tensor-core tile rule: the same cut-offs with 2 and 4 tiles per SM
+  if (tree_has(tree, HRP_F16) || tree_has(tree, HRP_F8E4M3)) {
+    const size_t base = c.size();
+    for (int occ : {2, 4})
+      for (size_t i = 0; i < base; ++i) {
+        hrp_tree t = c[i];
+        if ((t.tile_occupancy ? t.tile_occupancy : 1) == occ) continue;
+        t.tile_occupancy = occ;
+        bool dup = false;
+        for (const auto& u : c)
+          dup |= u.leaf == t.leaf && u.trsm_leaf == t.trsm_leaf && u.tile_occupancy == t.tile_occupancy;
+        if (!dup && validate_tree(nullptr, &t, 1) == HRP_OK) c.push_back(t);
+      }
   }
   for (int i = 0; i < (int)c.size() && i < cap; ++i) out[i] = c[i];
   return (int)c.size();
@@ -1040,22 +1082,20 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
   if (n < 1 || n > 65535) return bad_arg(h, 3, "n must be in [1, 65535]");
   if (reps < 1) return bad_arg(h, 4, "reps < 1");
   if (!out) return bad_arg(h, 6, "out is NULL");
-  char key[256];
-  {
-    int o = snprintf(key, sizeof(key), "n=%d;d=%d;in=%d@%d;tc=%d;L=", n, tree->depth, tree->inner, tree->inner_size,
-                     tree->trsm_compute);
-    for (int i = 0; i < tree->depth && o < (int)sizeof(key) - 4; ++i) o += snprintf(key + o, sizeof(key) - o, "%d,", tree->level[i]);
-  }
+  const std::string key = tune_key(tree);
   if (!(flags & 1)) {
     auto it = h->tune_cache.find(key);
     if (it != h->tune_cache.end()) {
-      *out = it->second.first;
-      if (ms) *ms = it->second.second;
-      return HRP_OK;
+      auto jt = it->second.find(n);
+      if (jt != it->second.end()) {
+        *out = jt->second.first;
+        if (ms) *ms = jt->second.second;
+        return HRP_OK;
+      }
     }
   }
-  hrp_tree cand[16];
-  const int nc = std::min(hrp_autotune_candidates(tree, cand, 16), 16);
+  hrp_tree cand[32];
+  const int nc = std::min(hrp_autotune_candidates(tree, cand, 32), 32);
   if (nc < 1) return set_err(h, HRP_ERR_INVALID_ARG, "no valid candidate tree");
   cudaSetDevice(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1118,7 +1158,21 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
   fail(HRP_OK);
   *out = cand[best];
   if (ms) *ms = best_ms;
-  h->tune_cache[key] = {cand[best], best_ms};
+  h->tune_cache[key][n] = {cand[best], best_ms};
+  return HRP_OK;
+}
+
+hrp_status hrp_autotune_orders(hrp_handle* h, const hrp_tree* tree, int count, const int* orders, int reps,
+                               void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (count < 0) return bad_arg(h, 3, "count < 0");
+  if (count > 0 && !orders) return bad_arg(h, 4, "orders is NULL");
+  for (int i = 0; i < count; ++i) {
+    hrp_tree out;
+    hrp_status st = hrp_autotune(h, tree, orders[i], reps, 0, &out, nullptr, stream);
+    if (st != HRP_OK) return st;
+  }
   return HRP_OK;
 }
 
@@ -1295,15 +1349,14 @@ hrp_status batch_trees(hrp_handle* h, const hrp_tree* const* trees, int batch, c
   out.assign(batch, nullptr);
   for (int i = 0; i < batch; ++i) {
     if (trees && trees[i]) {
-      out[i] = trees[i];
-      continue;
-    }
-    if (n[i] > 0) {
+      chosen[i] = *trees[i];
+    } else if (n[i] > 0) {
       hrp_status st = policy_choose(h, n[i], dA[i], lda[i], true, &chosen[i], nullptr, stream);
       if (st != HRP_OK) return st;
     } else {
       hrp_policy_tree(0, &chosen[i]);
     }
+    apply_tuned(h, &chosen[i], n[i]);         // cut-offs tuned for this order, if any
     out[i] = &chosen[i];
   }
   return HRP_OK;

@@ -118,9 +118,10 @@ cudaError_t launch_gemm_simt_f32(double* C, int ldc, const float* X, int ldx, co
 // Y = S[yr0.., k0..] (n x k) read from the row-major FP16 shadow S (lds), FP32 accumulation
 // in TMEM.  Requires k0 % 8 == 0 and lds % 8 == 0.
 bool tc_gemm_supported();
+// occupancy: tiles per SM the tile-width rule aims for (the tree's tile_occupancy; 0 = 1).
 cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds,
                                int xr0, int yr0, int k0, int m, int n, int k, bool lower,
-                               double scale, unsigned* dev_err, cudaStream_t s);
+                               double scale, unsigned* dev_err, cudaStream_t s, int occupancy = 0);
 
 // ---------------- POTRS (k_potrs.cu) ----------------
 // B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 or (fp32)

@@ -483,11 +483,12 @@ long long active_tiles(int m, int n, bool lower, int bn) {
   return t;
 }
 
-int pick_bn(int m, int n, bool lower) {
-  const int sms = device_sm_count();
-  if (n > 128 && active_tiles(m, n, lower, 256) >= sms) return 256;
-  if (n > 64 && active_tiles(m, n, lower, 128) >= sms) return 128;
-  if (n > 32 && active_tiles(m, n, lower, 64) >= sms) return 64;
+// the widest tile width that still gives occ tiles per SM
+int pick_bn(int m, int n, bool lower, int occ) {
+  const long long need = (long long)device_sm_count() * (occ > 0 ? occ : 1);
+  if (n > 128 && active_tiles(m, n, lower, 256) >= need) return 256;
+  if (n > 64 && active_tiles(m, n, lower, 128) >= need) return 128;
+  if (n > 32 && active_tiles(m, n, lower, 64) >= need) return 64;
   return 32;
 }
 
@@ -496,14 +497,14 @@ int pick_bn(int m, int n, bool lower) {
 bool tc_gemm_supported() { return get_encode() != nullptr; }
 
 cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n,
-                               int k, bool lower, double scale, unsigned* dev_err, cudaStream_t s) {
+                               int k, bool lower, double scale, unsigned* dev_err, cudaStream_t s, int occupancy) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   if ((k0 % 8) != 0 || (lds % 8) != 0 || (reinterpret_cast<uintptr_t>(S) & 15) != 0) return cudaErrorInvalidValue;
   // The FP64 read-modify-write of the epilogue runs on the SM's FP64 pipe and costs about
   // as much as the tile's MMAs, so small products are cut into narrower tiles until they
   // cover the SMs (tiles of 64 or 32 columns also fit two CTAs per SM, one CTA's epilogue
   // then overlapping the other's MMAs).
-  const int bn = pick_bn(m, n, lower);
+  const int bn = pick_bn(m, n, lower, occupancy);
   const int sms = device_sm_count();
   // more tiles than SMs: persistent CTAs with the epilogue of one tile under the MMAs of the next
   if (bn >= 128) {

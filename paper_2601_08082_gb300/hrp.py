@@ -34,14 +34,15 @@ EXPORTED = [
     "hrp_policy_set", "hrp_policy_predict", "hrp_policy_tree", "hrp_last_policy_choice",
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
     "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
-    "hrp_last_inner_iterations",
+    "hrp_last_inner_iterations", "hrp_autotune_orders",
 ]
 
 
 class Tree(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("level", ctypes.c_int * HRP_MAX_DEPTH), ("leaf", ctypes.c_int),
                 ("inner", ctypes.c_int), ("inner_size", ctypes.c_int), ("trsm_leaf", ctypes.c_int),
-                ("syrk_leaf", ctypes.c_int), ("scale_block", ctypes.c_int), ("trsm_compute", ctypes.c_int)]
+                ("syrk_leaf", ctypes.c_int), ("scale_block", ctypes.c_int), ("trsm_compute", ctypes.c_int),
+                ("tile_occupancy", ctypes.c_int)]
 
 
 class HrpError(RuntimeError):
@@ -109,12 +110,13 @@ def load(path: str = LIB_PATH):
     L.hrp_last_policy_choice.argtypes = [vp]
     L.hrp_autotune_candidates.argtypes = [tp, vp, c_int]
     L.hrp_autotune.argtypes = [vp, tp, c_int, c_int, c_int, tp, fp, vp]
+    L.hrp_autotune_orders.argtypes = [vp, tp, c_int, vp, c_int, vp]
     _lib = L
     return L
 
 
 def tree_parse(spec: str, leaf: int = 128, trsm_leaf: int = 0, syrk_leaf: int = 0,
-               trsm_fp64: bool = False) -> Tree:
+               trsm_fp64: bool = False, tile_occupancy: int = 0) -> Tree:
     t = Tree()
     st = load().hrp_tree_parse(spec.encode(), leaf, ctypes.byref(t))
     if st != 0:
@@ -122,6 +124,7 @@ def tree_parse(spec: str, leaf: int = 128, trsm_leaf: int = 0, syrk_leaf: int = 
     t.trsm_leaf = trsm_leaf
     t.syrk_leaf = syrk_leaf
     t.trsm_compute = 1 if trsm_fp64 else 0
+    t.tile_occupancy = tile_occupancy
     return t
 
 
@@ -381,6 +384,11 @@ class Handle:
         self._check(st)
         return out, float(ms.value)
 
+    def autotune_orders(self, tree: Tree, orders, reps: int = 2, stream=None) -> None:
+        """hrp_autotune_orders: tune each order; the batched calls then use the tuned cut-offs."""
+        arr = (ctypes.c_int * len(orders))(*[int(o) for o in orders])
+        self._check(self._lib.hrp_autotune_orders(self._h, ctypes.byref(tree), len(orders), arr, reps, _stream(stream)))
+
     def backward_error(self, A, L, n: int | None = None, stream=None) -> float:
         n = A.shape[0] if n is None else n
         out = ctypes.c_double(0.0)
@@ -393,7 +401,7 @@ class Handle:
 def autotune_candidates(tree: Tree) -> list[Tree]:
     """The autotuner's candidate trees for `tree` (host only): the given tree first."""
     L = load()
-    cap = 16
+    cap = 32
     arr = (Tree * cap)()
     cnt = L.hrp_autotune_candidates(ctypes.byref(tree), ctypes.cast(arr, ctypes.c_void_p), cap)
     if cnt < 0:

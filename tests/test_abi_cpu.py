@@ -84,19 +84,22 @@ def test_autotune_candidates_keep_the_precisions(lib, spec, leaf, trsm_leaf):
     for c in cands:
         tl = c.trsm_leaf or c.leaf
         assert 1 <= c.leaf <= 128 and 1 <= tl <= c.leaf
-        assert (c.leaf, tl) not in seen
-        seen.add((c.leaf, tl))
+        assert (c.leaf, tl, c.tile_occupancy) not in seen
+        seen.add((c.leaf, tl, c.tile_occupancy))
         assert hrp.tree_format(c) == hrp.tree_format(t)
         assert (c.depth, list(c.level)[:c.depth], c.inner, c.inner_size, c.trsm_compute) == \
             (t.depth, list(t.level)[:t.depth], t.inner, t.inner_size, t.trsm_compute)
-    assert {(128, 128), (64, 64), (64, 32)} <= seen
+    assert {(128, 128, 0), (64, 64, 0), (64, 32, 0)} <= seen
+    occ = {o for _, _, o in seen}
+    assert occ == ({0, 2, 4} if "F16" in spec else {0})     # tile rule only with tensor-core levels
 
 
-def test_autotune_candidates_for_an_f8_tree_are_only_the_tree(lib):
+def test_autotune_candidates_for_an_f8_tree_keep_its_cut_offs(lib):
     from paper_2601_08082_gb300 import hrp
     t = hrp.tree_parse("[F8,F16,F16,F32|F64@128]", leaf=128)
     cands = hrp.autotune_candidates(t)
-    assert len(cands) == 1 and cands[0].leaf == 128 and (cands[0].trsm_leaf or 128) == 128
+    assert all(c.leaf == 128 and (c.trsm_leaf or 128) == 128 for c in cands)
+    assert sorted(c.tile_occupancy for c in cands) == [0, 2, 4]      # only the tile rule varies
 
 
 def test_autotune_rejects_bad_arguments_without_a_gpu(lib):

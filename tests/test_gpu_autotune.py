@@ -48,14 +48,16 @@ def test_autotune_choice(hrp_mod, handle, spec, n):
     best, ms = handle.autotune(t, n, reps=3, retune=True)
     assert ms > 0
     cands = hrp_mod.autotune_candidates(t)
-    assert any((c.leaf, c.trsm_leaf) == (best.leaf, best.trsm_leaf) for c in cands)
+    assert any((c.leaf, c.trsm_leaf, c.tile_occupancy) == (best.leaf, best.trsm_leaf, best.tile_occupancy)
+               for c in cands)
     assert hrp_mod.tree_format(best) == hrp_mod.tree_format(t)
 
     # cached: the same key returns the same choice without running anything
     t0 = time.perf_counter()
     best2, ms2 = handle.autotune(t, n, reps=3)
     assert time.perf_counter() - t0 < 0.05
-    assert (best2.leaf, best2.trsm_leaf, ms2) == (best.leaf, best.trsm_leaf, ms)
+    assert (best2.leaf, best2.trsm_leaf, best2.tile_occupancy, ms2) == (best.leaf, best.trsm_leaf,
+                                                                         best.tile_occupancy, ms)
 
     # an independent matrix of another family: as accurate (backward error within the
     # tuner's own 4x acceptance rule) and not slower (10% for timing noise)
@@ -72,3 +74,29 @@ def test_autotune_of_an_f8_tree_returns_it(hrp_mod, handle):
     t = hrp_mod.tree_parse("[F8,F16,F32|F64@128]", leaf=128)
     best, ms = handle.autotune(t, 1024, reps=1)
     assert (best.leaf, best.trsm_leaf or best.leaf) == (128, 128) and ms > 0
+
+
+def test_batched_systems_take_the_cut_offs_tuned_for_their_order(hrp_mod, handle):
+    """hrp_autotune_orders tunes a few orders; a batched system of order n then runs with the
+    cut-offs and tile rule tuned at the largest tuned order <= n: bitwise the factor of a
+    single hrp_potrf with that tuned tree."""
+    import torch
+    h = hrp_mod.Handle(0)
+    try:
+        t = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
+        h.autotune_orders(t, [256, 1024], reps=1)
+        tuned = {o: h.autotune(t, o, reps=1)[0] for o in (256, 1024)}
+        sizes = [200, 300, 1100, 700]
+        mats = [dominant_spd(n, 2.0, seed_for(0, 90 + i)) for i, n in enumerate(sizes)]
+        As = [hrp_mod.colmajor(A).cuda() for A in mats]
+        d_info = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+        h.potrf_batched(t, As, d_info)
+        torch.cuda.synchronize()
+        assert d_info.cpu().tolist() == [0] * len(sizes)
+        for n, A, At in zip(sizes, mats, As):
+            ref_tree = t if n < 256 else tuned[1024 if n >= 1024 else 256]
+            single = hrp_mod.colmajor(A).cuda()
+            assert h.potrf(ref_tree, single) == 0
+            assert torch.equal(torch.tril(single.T), torch.tril(At.T)), n
+    finally:
+        h.close()
