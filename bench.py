@@ -315,32 +315,39 @@ def run_batched(args, rank, world):
     Bs = [B.clone() for B in B0]
     tree = hrp.tree_parse(args.batch_tree, leaf=128)
     d_info = torch.zeros(len(mine), dtype=torch.int32, device="cuda")
-    h.potrf_batched(tree, As, d_info)
-    h.potrs_batched(As, Bs)
-    torch.cuda.synchronize()
-    s = torch.cuda.Stream()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        with torch.cuda.graph(g, stream=s):
-            h.potrf_batched(tree, As, d_info, stream=s)
-            h.potrs_batched(As, Bs, stream=s)
     flops = sum(n ** 3 / 3.0 for n in sizes)
-    # (1) the factor + solve graph alone (no refinement): one replay per step
-    gtimes = []
-    for rep in range(args.warmup + args.steps):
-        for A, a0 in zip(As, A0):
-            A.copy_(a0)
-        for B, b0 in zip(Bs, B0):
-            B.copy_(b0)
+
+    def graph_ms(persistent):
+        """(1) the factor + solve graph alone (no refinement): one replay per step."""
+        h.set_batched_mode(persistent)
+        h.potrf_batched(tree, As, d_info)
+        h.potrs_batched(As, Bs)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        g.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        if rep >= args.warmup:
-            gtimes.append(e0.elapsed_time(e1))
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                h.potrf_batched(tree, As, d_info, stream=s)
+                h.potrs_batched(As, Bs, stream=s)
+        gt = []
+        for rep in range(args.warmup + args.steps):
+            for A, a0 in zip(As, A0):
+                A.copy_(a0)
+            for B, b0 in zip(Bs, B0):
+                B.copy_(b0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                gt.append(e0.elapsed_time(e1))
+        return sum(gt) / len(gt)
+
+    g_pool = graph_ms(False)
+    g_pers = graph_ms(True)                 # the persistent launch is the handle's default
     failed = [i for i, v in enumerate(d_info.cpu().tolist()) if v != 0]
     # (2) the full batched solve: mixed tree, fallback where it fails, FP64 refinement to 1e-12
     Xs = [torch.zeros_like(B) for B in B0]
@@ -387,7 +394,8 @@ def run_batched(args, rank, world):
             "speedup_vs_fp64_loop": ms64 / ms, "status": out["status"],
             "systems_refactored_with_fallback": int(sum(out["used_fallback"])),
             "max_refinement_rounds": int(max(out["iters"])), "worst_solution_residual": worst,
-            "graph_factor_solve_ms": sum(gtimes) / len(gtimes), "graph_systems_failing_mixed_tree": len(failed)}
+            "graph_factor_solve_ms": {"persistent": g_pers, "stream_pool": g_pool},
+            "graph_systems_failing_mixed_tree": len(failed)}
     reps.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

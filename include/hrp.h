@@ -241,6 +241,16 @@ hrp_status hrp_autotune(hrp_handle* h, const hrp_tree* tree, int n, int reps, in
  * hrp_potrf.  Each system runs the recursion of Alg. 1-3 on one stream of an internal
  * pool forked from `stream` (longest systems first) and joined back into it; the call only
  * enqueues work (capturable into one CUDA graph once the workspace for these sizes exists).
+ * That is batched mode 0 (the default).  Batched mode 1 (hrp_set_batched_mode): the same
+ * recursion is recorded per system as a list of base cases and GEMMs (each at the precision
+ * its tree gives it) and ONE persistent launch runs them: one CTA per SM takes the next
+ * system (longest first) from an atomic ticket and executes its list in order; no CTA waits
+ * on another.  Mode 1 runs every operation on CUDA cores (FP16 operands rounded on load,
+ * FP32 accumulation; FP32 substitution for reduced-precision leaf solves).  The first call
+ * with a given batch (orders, trees, pointers) uploads its lists to device memory that the
+ * handle keeps for that batch until it is destroyed (36 bytes per operation); later calls
+ * with the same batch, and graphs that capture them, reuse it.  Capturing a batch that was
+ * never run returns HRP_ERR_INVALID_ARG.
  */
 hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int batch, const int* n,
                              double* const* dA, const int* lda, int* d_info, void* stream);
@@ -250,6 +260,9 @@ hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees, int ba
  */
 hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* const* dL, const int* ldl,
                              int nrhs, double* const* dB, const int* ldb, void* stream);
+/* Batched factorization mode of the handle: 0 = stream pool, 1 = persistent launch (above;
+   also used by the factorizations of hrp_posv_batched). */
+hrp_status hrp_set_batched_mode(hrp_handle* h, int mode);
 
 /*
  * Learned precision policy (not in the paper; an extension of it).  A small network

@@ -93,6 +93,18 @@ struct hrp_handle_s {
   double* kwork = nullptr;     // GMRES basis and vectors
   size_t kwork_cap = 0;
   long long inner_steps = 0;   // GMRES steps of the last hrp_posv
+  // batched factorization: 0 = one stream per system (default), 1 = one persistent launch
+  int batched_mode = 0;
+  // persistent launch plans: every distinct batch (its operation and system lists, byte for
+  // byte) keeps its own device copy and ticket, so a graph that captured it stays valid
+  struct Plan {
+    std::string key;
+    hrp::BatchOp* ops = nullptr;
+    hrp::BatchSys* sys = nullptr;
+    int* ticket = nullptr;
+    int nsys = 0;
+  };
+  std::vector<Plan> plans;
 };
 
 namespace hrp {
@@ -223,6 +235,8 @@ struct Fact {
   size_t ev_used = 0;
   std::map<cudaStream_t, bool> waited;   // the stream's next kernel follows a cross-stream wait
   int side_ctas = 0;
+  // record mode (persistent batched launch): operations are appended here, nothing is launched
+  std::vector<BatchOp>* rec = nullptr;
   // timing mode: an event pair around every launch, tagged with its class and flops
   struct Rec { int cls; size_t ev; double flops; };
   std::vector<Rec> recs;
@@ -270,6 +284,10 @@ struct Fact {
   int tleaf() const { return t->trsm_leaf ? t->trsm_leaf : t->leaf; }
 
   void leaf_potrf(int off, int nb, int p) {
+    if (rec) {
+      rec->push_back(BatchOp{BOP_POTRF, p, off, nb, 0, 0, 0, 0, 0});
+      return;
+    }
     float* W = nullptr;
     if (w32) {
       W = w32 + (size_t)off * 128;
@@ -280,6 +298,10 @@ struct Fact {
   }
 
   void leaf_trsm(int r0, int m, int c0, int nc, int p) {
+    if (rec) {
+      rec->push_back(BatchOp{BOP_TRSM, p, r0, m, c0, nc, (p == HRP_F64 || t->trsm_compute == 1) ? 1 : 0, 0, 0});
+      return;
+    }
     double* Ab = A;
     __half* sh = shadow;
     begin(CLS_TRSM, (double)m * nc * nc);
@@ -316,6 +338,11 @@ struct Fact {
   // C = A[r0:r0+m, c0:c0+nd] -= X Y^T, X = A[r0:r0+m, k0:k0+k], Y = A[c0:c0+nd, k0:k0+k]
   void gemm(int p, int r0, int m, int c0, int nd, int k0, int k, bool lower) {
     if (m <= 0 || nd <= 0 || k <= 0) return;
+    if (rec) {
+      if (p == HRP_F8E4M3 && err == cudaSuccess) err = cudaErrorNotSupported;
+      rec->push_back(BatchOp{BOP_GEMM, p, r0, m, c0, nd, k0, k, lower ? 1 : 0});
+      return;
+    }
     double* C = A + (size_t)c0 * lda + r0;
     const double* X = A + (size_t)k0 * lda + r0;
     const double* Y = A + (size_t)k0 * lda + c0;
@@ -675,6 +702,11 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->bwork);
   cudaFree(h->fwork);
   cudaFree(h->kwork);
+  for (auto& pl : h->plans) {
+    cudaFree(pl.ops);
+    cudaFree(pl.sys);
+    cudaFree(pl.ticket);
+  }
   cudaFree(h->policy);
   cudaFree(h->pio);
   delete h;
@@ -1196,6 +1228,14 @@ hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner
 
 long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
 
+hrp_status hrp_set_batched_mode(hrp_handle* h, int mode) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (mode != 0 && mode != 1) return bad_arg(h, 2, "mode must be 0 (stream pool) or 1 (persistent)");
+  h->batched_mode = mode;
+  return HRP_OK;
+}
+
 hrp_status hrp_set_lookahead(hrp_handle* h, int enable) {
   if (!h) return HRP_ERR_INVALID_ARG;
   h->lookahead = enable != 0;
@@ -1362,6 +1402,89 @@ hrp_status batch_trees(hrp_handle* h, const hrp_tree* const* trees, int batch, c
   return HRP_OK;
 }
 
+// One system of a persistent batched launch.
+struct PSys {
+  const hrp_tree* tree;
+  int n;
+  double* A;
+  int lda;
+  const double* src;   // non-null: factor a copy of src's lower triangle into A
+  int ldsrc;
+  int* info;
+};
+
+// Records every system's operations (the recursion of Alg. 1-3 with its tree), orders the
+// systems longest first, and enqueues the one persistent launch on the batch's plan (its
+// device copy of the lists, uploaded on the first call with this batch).  Capturable once
+// the plan exists.
+hrp_status enqueue_persistent(hrp_handle* h, const std::vector<PSys>& sys, cudaStream_t s, long long* launches) {
+  std::vector<int> order(sys.size());
+  for (size_t i = 0; i < sys.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sys[a].n > sys[b].n; });
+  std::vector<BatchOp> ops;
+  std::vector<BatchSys> bs;
+  for (int i : order) {
+    const PSys& q = sys[i];
+    if (q.n <= 0) continue;
+    Fact f{};
+    f.h = h;
+    f.t = q.tree;
+    f.A = q.A;
+    f.lda = q.lda;
+    f.n = q.n;
+    f.info = q.info;
+    f.rec = &ops;
+    const int op0 = (int)ops.size();
+    f.potrf(0, q.n, 0);
+    if (f.err != cudaSuccess) return cuda_status(h, f.err, "batched (persistent)");
+    bs.push_back(BatchSys{q.A, q.lda, q.n, op0, (int)ops.size(), q.info, q.src, q.ldsrc});
+  }
+  // systems of order 0: info = 0
+  for (const PSys& q : sys)
+    if (q.n <= 0) {
+      cudaError_t e = launch_fill_int(q.info, 0, 1, s);
+      if (e != cudaSuccess) return cuda_status(h, e, "batched (persistent)");
+    }
+  if (bs.empty()) return HRP_OK;
+  const size_t bytes_ops = ops.size() * sizeof(BatchOp), bytes_sys = bs.size() * sizeof(BatchSys);
+  std::string key(bytes_ops + bytes_sys, '\0');
+  memcpy(&key[0], ops.data(), bytes_ops);
+  memcpy(&key[bytes_ops], bs.data(), bytes_sys);
+  hrp_handle_s::Plan* plan = nullptr;
+  for (auto& pl : h->plans)
+    if (pl.key == key) plan = &pl;
+  if (!plan) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+      return set_err(h, HRP_ERR_INVALID_ARG,
+                     "batched (persistent): make one call with this batch before capturing it in a graph");
+    hrp_handle_s::Plan pl;
+    pl.key = key;
+    pl.nsys = (int)bs.size();
+    if (cudaMalloc(&pl.ops, bytes_ops) != cudaSuccess || cudaMalloc(&pl.sys, bytes_sys) != cudaSuccess ||
+        cudaMalloc(&pl.ticket, sizeof(int)) != cudaSuccess) {
+      cudaFree(pl.ops);
+      cudaFree(pl.sys);
+      cudaGetLastError();
+      return set_err(h, HRP_ERR_ALLOC, "batched (persistent): plan buffers");
+    }
+    // from pageable memory: the call returns once the bytes are staged, before they are used
+    cudaError_t e = cudaMemcpyAsync(pl.ops, ops.data(), bytes_ops, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl.sys, bs.data(), bytes_sys, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFree(pl.ops);
+      cudaFree(pl.sys);
+      cudaFree(pl.ticket);
+      return cuda_status(h, e, "batched (persistent)");
+    }
+    h->plans.push_back(std::move(pl));
+    plan = &h->plans.back();
+  }
+  cudaError_t e = launch_batched_interp(plan->ops, plan->sys, plan->nsys, plan->ticket, h->d_err, s);
+  if (launches) *launches = 1;
+  return cuda_status(h, e, "batched (persistent)");
+}
+
 hrp_status check_batch_args(hrp_handle* h, int batch, const int* n, double* const* dA, const int* lda) {
   if (batch < 0) return bad_arg(h, 3, "batch < 0");
   if (batch > 0 && (!n || !dA || !lda)) return bad_arg(h, 4, "NULL array");
@@ -1395,6 +1518,13 @@ hrp_status hrp_potrf_batched(hrp_handle* h, const hrp_tree* const* trees_in, int
   }
   cudaSetDevice(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->batched_mode == 1) {
+    if (batch == 0) return HRP_OK;
+    std::vector<PSys> ps(batch);
+    for (int i = 0; i < batch; ++i) ps[i] = PSys{trees[i], n[i], dA[i], lda[i], nullptr, 0, d_info + i};
+    h->launches = 0;
+    return enqueue_persistent(h, ps, s, &h->launches);
+  }
   std::vector<SysWork> ws;
   if ((st = batch_prepare(h, batch, n, ws, true)) != HRP_OK) return st;
   if (batch == 0) return HRP_OK;
@@ -1813,6 +1943,15 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
   h->timing = false;
   // factor copies of every system (mixed trees), then the fallback tree where that failed
   for (int pass = 0; pass < 2 && err == cudaSuccess; ++pass) {
+    if (h->batched_mode == 1) {
+      std::vector<PSys> ps;
+      for (int i = 0; i < batch; ++i) {
+        if (n[i] == 0 || (pass == 1 && hinfo[i] == 0)) continue;
+        ps.push_back(PSys{pass == 0 ? trees[i] : &fallback, n[i], fact_of(i), n[i], dA[i], lda[i], d_info + i});
+        if (pass == 1) fb[i] = 1;
+      }
+      if ((st = enqueue_persistent(h, ps, s, nullptr)) != HRP_OK) break;
+    } else {
     if ((st = fork(h, s)) != HRP_OK) break;
     for (int i = 0; i < batch; ++i) {
       if (n[i] == 0 || (pass == 1 && hinfo[i] == 0)) continue;
@@ -1839,6 +1978,7 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
       if (pass == 1) fb[i] = 1;
     }
     if ((st = join(h, s)) != HRP_OK) break;
+    }
     note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
     note(cudaStreamSynchronize(s));
     if (err != cudaSuccess) break;
@@ -1904,6 +2044,21 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
       } else {
         all = false;
       }
+    }
+    if (!restart.empty() && h->batched_mode == 1) {
+      std::vector<PSys> ps;
+      for (int i : restart) {
+        ps.push_back(PSys{&fallback, n[i], fact_of(i), n[i], dA[i], lda[i], d_info + i});
+        fb[i] = 1;
+        fresh[i] = 1;
+        its[i] = 0;
+        res[i] = 1e300;
+      }
+      if ((st = enqueue_persistent(h, ps, s, nullptr)) != HRP_OK) break;
+      note(cudaMemcpyAsync(hinfo.data(), d_info, sizeof(int) * batch, cudaMemcpyDeviceToHost, s));
+      note(cudaStreamSynchronize(s));
+      if (err == cudaSuccess && (st = check_dev_err(h, s)) != HRP_OK) break;
+      restart.clear();
     }
     if (!restart.empty()) {
       // refactor the stalled systems with the fallback tree; they restart their solve

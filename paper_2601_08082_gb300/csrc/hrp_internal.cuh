@@ -194,6 +194,29 @@ cudaError_t launch_scale(double* y, const double* x, double a, int n, bool accum
 // sets *flag = 1 if any diagonal entry of A exceeds `limit` (or is not finite)
 cudaError_t launch_diag_check(const double* A, int lda, int n, double limit, int* flag, cudaStream_t s);
 
+// ---------------- persistent batched factorization (k_batched.cu) ----------------
+// One recorded operation of a system's factorization (the launches the recursion of Alg. 1-3
+// would make), on that system's FP64 master:
+//   BOP_POTRF: leaf POTRF of the diagonal block at offset a, order b, precision p;
+//   BOP_TRSM:  leaf TRSM of rows [a, a+b), columns [c, c+d), FP64 if e else FP32;
+//   BOP_GEMM:  A[a:a+b, c:c+d] -= A[a:a+b, e:e+f] A[c:c+d, e:e+f]^T at precision p, lower if g.
+enum { BOP_POTRF = 1, BOP_TRSM = 2, BOP_GEMM = 3 };
+struct BatchOp {
+  int type, p, a, b, c, d, e, f, g;
+};
+struct BatchSys {
+  double* A;          // the system's matrix (column-major, lda), overwritten with L
+  int lda, n;
+  int op0, op1;       // its operations: ops[op0 .. op1)
+  int* info;          // device int: 0 or the failing column
+  const double* src;  // when non-null, A's lower triangle is first copied from src (ldsrc)
+  int ldsrc;
+};
+// Every system's operations by one persistent launch (one CTA per SM, systems taken from
+// *ticket in array order).  ticket: device int scratch.
+cudaError_t launch_batched_interp(const BatchOp* ops, const BatchSys* sys, int nsys, int* ticket, unsigned* err,
+                                  cudaStream_t s);
+
 // ---------------- learned policy (k_policy.cu) ----------------
 int policy_nparam();
 cudaError_t launch_rowsum(const double* A, int lda, int n, double* rowsum, double* stats, cudaStream_t s);

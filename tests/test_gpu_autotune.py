@@ -83,6 +83,7 @@ def test_batched_systems_take_the_cut_offs_tuned_for_their_order(hrp_mod, handle
     import torch
     h = hrp_mod.Handle(0)
     try:
+        h.set_batched_mode(False)          # stream pool: the single factorization's kernels
         t = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
         h.autotune_orders(t, [256, 1024], reps=1)
         tuned = {o: h.autotune(t, o, reps=1)[0] for o in (256, 1024)}

@@ -377,7 +377,10 @@ def test_posv_with_fp8_tree_refines(hrp_mod, handle):
 # batched factorization / solve (many independent systems, one stream pool, graph-capturable)
 # ---------------------------------------------------------------------------------------
 def test_batched_equals_one_by_one(hrp_mod, handle):
+    """Stream-pool mode: every system runs the single factorization's kernels in the same
+    order, so the factors are bitwise those of hrp_potrf."""
     import torch
+    handle.set_batched_mode(False)
     sizes = [64, 200, 128, 513, 96, 1000, 1, 300, 777, 65]
     mats = [dominant_spd(n, 1.5, seed_for(4, i), shift=1.0) for i, n in enumerate(sizes)]
     tree = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
@@ -401,10 +404,13 @@ def test_batched_equals_one_by_one(hrp_mod, handle):
         X_ref = dense.potrs(L, rhs(A.shape[0], 4, seed_for(4, 100 + sizes.index(A.shape[0]))))
         X = hrp_mod.from_colmajor(B)
         assert np.max(np.abs(X - X_ref)) <= 1e-12 * np.max(np.abs(X_ref))
+    handle.set_batched_mode(False)
 
 
-def test_batched_reports_per_system_info(hrp_mod, handle):
+@pytest.mark.parametrize("persistent", [True, False])
+def test_batched_reports_per_system_info(hrp_mod, handle, persistent):
     import torch
+    handle.set_batched_mode(persistent)
     sizes = [100, 150, 80]
     mats = [dominant_spd(n, 2.0, seed_for(4, 50 + i)) for i, n in enumerate(sizes)]
     mats[1][40, 40] = -1.0
@@ -413,6 +419,7 @@ def test_batched_reports_per_system_info(hrp_mod, handle):
     d_info = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
     handle.potrf_batched(hrp_mod.tree_parse("[F64]", leaf=64), As, d_info)
     torch.cuda.synchronize()
+    handle.set_batched_mode(False)
     assert d_info.cpu().tolist() == [0, info1, 0] and info1 == 41
 
 
@@ -461,3 +468,93 @@ def test_posv_batched_refines_every_system(hrp_mod, handle):
         B = hrp_mod.from_colmajor(Bs[i])
         assert np.max(dense.column_residuals(A, X, B)) <= 1e-12
         assert abs(out["resid"][i] - np.max(dense.column_residuals(A, X, B))) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# persistent batched launch (batched mode 1): many uneven systems in one launch
+# ---------------------------------------------------------------------------------------
+def _uneven_sizes(count, lo, hi, seed):
+    return [int(x) for x in np.random.default_rng(seed).integers(lo, hi + 1, count)]
+
+
+def test_persistent_batched_fp64_tree_matches_cholesky(hrp_mod, handle):
+    import torch
+    handle.set_batched_mode(True)
+    sizes = _uneven_sizes(40, 1, 600, seed_for(4, 400))
+    mats = [dominant_spd(n, 1.2, seed_for(4, 410 + i), shift=1.0) for i, n in enumerate(sizes)]
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    d_info = torch.full((len(sizes),), -7, dtype=torch.int32, device="cuda")
+    handle.potrf_batched(hrp_mod.tree_parse("[F64]", leaf=64), As, d_info)
+    torch.cuda.synchronize()
+    assert handle.launch_count() == 1
+    assert d_info.cpu().tolist() == [0] * len(sizes)
+    for A, At in zip(mats, As):
+        L0, _ = dense.cholesky(A)
+        L = np.tril(hrp_mod.from_colmajor(At))
+        assert np.max(np.abs(L - L0)) <= 1e-12 * np.max(np.abs(L0))
+    handle.set_batched_mode(False)
+
+
+def test_persistent_batched_mixed_tree_matches_emulator(hrp_mod, handle):
+    """[F16,F32|F64@128] over 36 uneven systems: every factor within the FP32 noise of the
+    emulator's (max-norm 1e-5 of max|L|, backward error within 2x of the emulator's), and the
+    projection check against mis-levelled trees on the largest systems."""
+    import torch
+    handle.set_batched_mode(True)
+    spec = "[F16,F32|F64@128]"
+    sizes = _uneven_sizes(36, 64, 900, seed_for(4, 500)) + [1100, 1300]
+    mats = [dominant_spd(n, 1.05, seed_for(4, 510 + i)) for i, n in enumerate(sizes)]
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    d_info = torch.full((len(sizes),), -7, dtype=torch.int32, device="cuda")
+    handle.potrf_batched(hrp_mod.tree_parse(spec, leaf=128), As, d_info)
+    torch.cuda.synchronize()
+    assert d_info.cpu().tolist() == [0] * len(sizes)
+    for n, A, At in zip(sizes, mats, As):
+        L = np.tril(hrp_mod.from_colmajor(At))
+        L_emu, info, _ = otree.emulate_potrf(A, otree.parse(spec, leaf=128))
+        assert info == 0
+        assert np.max(np.abs(L - L_emu)) <= 1e-5 * np.max(np.abs(L_emu)), n
+        be, be_emu = dense.backward_error(A, L), dense.backward_error(A, L_emu)
+        assert be <= 2 * be_emu + 1e-15, (n, be, be_emu)
+        if n >= 1100:
+            check_mixed_factor(L, A, spec, 128, L_emu=L_emu)
+    handle.set_batched_mode(False)
+
+
+def test_persistent_batched_posv_and_graph_replay(hrp_mod, handle):
+    import torch
+    from synth import rbf_spd
+    handle.set_batched_mode(True)
+    sizes = _uneven_sizes(32, 64, 700, seed_for(4, 600))
+    mats = [rbf_spd(n, seed_for(4, 610 + i)) for i, n in enumerate(sizes)]
+    As = [hrp_mod.colmajor(A).cuda() for A in mats]
+    Bs = [hrp_mod.colmajor(rhs(n, 4, seed_for(4, 650 + i))).cuda() for i, n in enumerate(sizes)]
+    Xs = [torch.zeros_like(B) for B in Bs]
+    out = handle.posv_batched(hrp_mod.tree_parse("[F16,F32|F64@128]", 128), As, Bs, Xs, tol=1e-12)
+    assert out["status"] == 0 and out["info"] == [0] * len(sizes)
+    assert max(out["resid"]) <= 1e-12
+    # recomputed on the CPU in another summation order: the FP64 residual of these RBF systems
+    # (kappa up to ~1e5) carries rounding noise of order u ||A|| ||x|| / ||b|| ~ 1e-13..1e-12
+    for A, B, X in zip(mats, Bs, Xs):
+        assert np.max(dense.column_residuals(A, hrp_mod.from_colmajor(X), hrp_mod.from_colmajor(B))) <= 2e-12
+    # one persistent launch captured in a graph and replayed: the same factors each time
+    tree = hrp_mod.tree_parse("[F16,F32|F64@128]", leaf=128)
+    A0 = [A.clone() for A in As]
+    W = [A.clone() for A in As]
+    d_info = torch.zeros(len(sizes), dtype=torch.int32, device="cuda")
+    handle.potrf_batched(tree, W, d_info)
+    torch.cuda.synchronize()
+    ref = [w.clone() for w in W]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            handle.potrf_batched(tree, W, d_info, stream=s)
+    for rep in range(2):
+        for w, a0 in zip(W, A0):
+            w.copy_(a0)
+        g.replay()
+        torch.cuda.synchronize()
+        for w, r in zip(W, ref):
+            assert torch.equal(w, r), rep
+    handle.set_batched_mode(False)
