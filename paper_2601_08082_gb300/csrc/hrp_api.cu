@@ -103,6 +103,7 @@ struct hrp_handle_s {
     hrp::BatchSys* sys = nullptr;
     int* ticket = nullptr;
     int nsys = 0;
+    unsigned char* shadows = nullptr;   // the systems' FP32 and FP16 shadows (owned by the plan)
   };
   std::vector<Plan> plans;
 };
@@ -706,6 +707,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
     cudaFree(pl.ops);
     cudaFree(pl.sys);
     cudaFree(pl.ticket);
+    cudaFree(pl.shadows);
   }
   cudaFree(h->policy);
   cudaFree(h->pio);
@@ -1423,6 +1425,7 @@ hrp_status enqueue_persistent(hrp_handle* h, const std::vector<PSys>& sys, cudaS
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sys[a].n > sys[b].n; });
   std::vector<BatchOp> ops;
   std::vector<BatchSys> bs;
+  size_t shadow_bytes = 0;
   for (int i : order) {
     const PSys& q = sys[i];
     if (q.n <= 0) continue;
@@ -1437,7 +1440,18 @@ hrp_status enqueue_persistent(hrp_handle* h, const std::vector<PSys>& sys, cudaS
     const int op0 = (int)ops.size();
     f.potrf(0, q.n, 0);
     if (f.err != cudaSuccess) return cuda_status(h, f.err, "batched (persistent)");
-    bs.push_back(BatchSys{q.A, q.lda, q.n, op0, (int)ops.size(), q.info, q.src, q.ldsrc});
+    const bool shad = tree_has(q.tree, HRP_F32) || tree_has(q.tree, HRP_F16);
+    // shadow offsets (bytes from the plan's shadow block) ride in the pointers until the plan
+    // allocates the block: FP32 then FP16, each n x n, 256-byte aligned
+    float* s32 = nullptr;
+    __half* s16 = nullptr;
+    if (shad) {
+      s32 = reinterpret_cast<float*>(shadow_bytes + 1);
+      shadow_bytes += ((size_t)q.n * q.n * sizeof(float) + 255) / 256 * 256;
+      s16 = reinterpret_cast<__half*>(shadow_bytes + 1);
+      shadow_bytes += ((size_t)q.n * q.n * sizeof(__half) + 255) / 256 * 256;
+    }
+    bs.push_back(BatchSys{q.A, q.lda, q.n, op0, (int)ops.size(), q.info, q.src, q.ldsrc, s32, s16});
   }
   // systems of order 0: info = 0
   for (const PSys& q : sys)
@@ -1447,6 +1461,7 @@ hrp_status enqueue_persistent(hrp_handle* h, const std::vector<PSys>& sys, cudaS
     }
   if (bs.empty()) return HRP_OK;
   const size_t bytes_ops = ops.size() * sizeof(BatchOp), bytes_sys = bs.size() * sizeof(BatchSys);
+  // the key holds the shadow offsets (not yet addresses): the same batch finds its plan
   std::string key(bytes_ops + bytes_sys, '\0');
   memcpy(&key[0], ops.data(), bytes_ops);
   memcpy(&key[bytes_ops], bs.data(), bytes_sys);
@@ -1462,12 +1477,19 @@ hrp_status enqueue_persistent(hrp_handle* h, const std::vector<PSys>& sys, cudaS
     pl.key = key;
     pl.nsys = (int)bs.size();
     if (cudaMalloc(&pl.ops, bytes_ops) != cudaSuccess || cudaMalloc(&pl.sys, bytes_sys) != cudaSuccess ||
-        cudaMalloc(&pl.ticket, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&pl.ticket, sizeof(int)) != cudaSuccess ||
+        (shadow_bytes && cudaMalloc(&pl.shadows, shadow_bytes) != cudaSuccess)) {
       cudaFree(pl.ops);
       cudaFree(pl.sys);
+      cudaFree(pl.ticket);
       cudaGetLastError();
       return set_err(h, HRP_ERR_ALLOC, "batched (persistent): plan buffers");
     }
+    for (auto& b : bs)                    // offsets -> addresses in the plan's shadow block
+      if (b.s32) {
+        b.s32 = reinterpret_cast<float*>(pl.shadows + (reinterpret_cast<uintptr_t>(b.s32) - 1));
+        b.s16 = reinterpret_cast<__half*>(pl.shadows + (reinterpret_cast<uintptr_t>(b.s16) - 1));
+      }
     // from pageable memory: the call returns once the bytes are staged, before they are used
     cudaError_t e = cudaMemcpyAsync(pl.ops, ops.data(), bytes_ops, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pl.sys, bs.data(), bytes_sys, cudaMemcpyHostToDevice, s);

@@ -211,6 +211,9 @@ struct BatchSys {
   int* info;          // device int: 0 or the failing column
   const double* src;  // when non-null, A's lower triangle is first copied from src (ldsrc)
   int ldsrc;
+  float* s32;         // FP32 and FP16 copies of the finished off-diagonal entries (column-
+  __half* s16;        // major, leading dimension n), read by the FP32 and FP16 GEMMs; null
+                      // when the system's tree has neither precision
 };
 // Every system's operations by one persistent launch (one CTA per SM, systems taken from
 // *ticket in array order).  ticket: device int scratch.

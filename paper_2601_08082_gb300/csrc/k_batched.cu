@@ -11,9 +11,11 @@
 // Operations (single-CTA versions of the stream path's kernels, same arithmetic classes):
 //   POTRF  leaf Cholesky of a diagonal block, FP64, or FP32 (on FP16-rounded input for an
 //          F16 leaf, result rounded to FP16), in registers, right-looking;
-//   TRSM   leaf X L^T = B by substitution in FP64 or FP32 (one row per thread);
-//   GEMM   C -= X Y^T on the FP64 master, operands rounded to the level's precision on
-//          load (FP64, FP32, FP16), accumulated in FP64 or FP32, 64 x 64 tiles.
+//   TRSM   leaf X L^T = B by substitution in FP64 or FP32 (one row per thread); it also
+//          writes the FP32 and FP16 roundings of X into the system's shadows;
+//   GEMM   C -= X Y^T, operands from the FP64 master (F64 levels) or the FP32 / FP16 shadow
+//          (rounded once, when the leaf TRSM finished them: conversions from FP64 run on this
+//          GPU's FP64 pipe), accumulated in FP64 or FP32, 64 x 64 tiles.
 // A system whose leaf POTRF fails stops at once (its info holds the failing column).
 #include <climits>
 
@@ -135,7 +137,8 @@ __device__ void dev_potrf(double* __restrict__ A, int ld, int n, int col0, bool 
 // substitution in T; rows in groups of RT, one row per thread (RT keeps L and the group
 // within batched_interp_smem()) ----
 template <typename T>
-__device__ void dev_trsm(double* __restrict__ A, int ld, int r0, int m, int c0, int nc, unsigned char* smem) {
+__device__ void dev_trsm(double* __restrict__ A, int ld, int r0, int m, int c0, int nc, float* __restrict__ s32,
+                         __half* __restrict__ s16, int lds, unsigned* __restrict__ err, unsigned char* smem) {
   const int RT = sizeof(T) == 8 ? (nc > 128 ? 32 : 64) : 128;
   T* Ls = reinterpret_cast<T*>(smem);                 // row-major nc x nc
   T* Xs = Ls + nc * nc;                               // Xs[k * RT + t]
@@ -167,10 +170,23 @@ __device__ void dev_trsm(double* __restrict__ A, int ld, int r0, int m, int c0, 
       }
     }
     __syncthreads();
+    bool over16 = false;
     for (int idx = tid; idx < RT * nc; idx += BT) {
       const int t = idx % RT, k = idx / RT;
-      if (g0 + t < m) A[(size_t)(c0 + k) * ld + r0 + g0 + t] = (double)Xs[k * RT + t];
+      if (g0 + t < m) {
+        const double v = (double)Xs[k * RT + t];
+        A[(size_t)(c0 + k) * ld + r0 + g0 + t] = v;
+        if (s32) {
+          const size_t o = (size_t)(c0 + k) * lds + r0 + g0 + t;
+          s32[o] = (float)Xs[k * RT + t];
+          // FP32 results round to FP16 from FP32 (the same value, off the FP64 pipe)
+          if constexpr (sizeof(T) == 4) s16[o] = __float2half_rn(Xs[k * RT + t]);
+          else s16[o] = __double2half(v);
+          over16 |= fabs(v) > (double)kF16Max;
+        }
+      }
     }
+    if (s32 && __any_sync(0xffffffffu, over16) && (tid & 31) == 0) atomicOr(err, DEV_ERR_RANGE16);
   }
 }
 
@@ -180,16 +196,14 @@ __device__ void dev_trsm(double* __restrict__ A, int ld, int r0, int m, int c0, 
 template <int RND> struct BAcc { using T = float; };
 template <> struct BAcc<0> { using T = double; };
 
-template <int RND>
-__device__ __forceinline__ typename BAcc<RND>::T bcvt(double x) {
-  if constexpr (RND == 0) return x;
-  else if constexpr (RND == 1) return __double2float_rn(x);
-  else return __half2float(__double2half(x));
-}
+__device__ __forceinline__ double bload(double x) { return x; }
+__device__ __forceinline__ float bload(float x) { return x; }
+__device__ __forceinline__ float bload(__half x) { return __half2float(x); }
 
-template <int RND>
-__device__ void dev_gemm(double* __restrict__ C, int ldc, const double* __restrict__ X, int ldx,
-                         const double* __restrict__ Y, int ldy, int m, int n, int k, bool lower,
+// TIN: operand storage (double master, float or __half shadow); RND 0 accumulates in FP64
+template <int RND, typename TIN>
+__device__ void dev_gemm(double* __restrict__ C, int ldc, const TIN* __restrict__ X, int ldx,
+                         const TIN* __restrict__ Y, int ldy, int m, int n, int k, bool lower,
                          unsigned char* smem) {
   using T = typename BAcc<RND>::T;
   constexpr int TL = 64, BK = 16, R = TL / 16;
@@ -211,8 +225,8 @@ __device__ void dev_gemm(double* __restrict__ C, int ldc, const double* __restri
         const int e = tid + BT * q;
         const int r = e % TL, kk = e / TL;
         const int gk = k0 + kk;
-        Xs[kk][r] = (m0 + r < m && gk < k) ? bcvt<RND>(X[(size_t)gk * ldx + m0 + r]) : (T)0;
-        Ys[kk][r] = (n0 + r < n && gk < k) ? bcvt<RND>(Y[(size_t)gk * ldy + n0 + r]) : (T)0;
+        Xs[kk][r] = (m0 + r < m && gk < k) ? (T)bload(X[(size_t)gk * ldx + m0 + r]) : (T)0;
+        Ys[kk][r] = (n0 + r < n && gk < k) ? (T)bload(Y[(size_t)gk * ldy + n0 + r]) : (T)0;
       }
       __syncthreads();
 #pragma unroll
@@ -273,16 +287,19 @@ batched_interp_kernel(const BatchOp* __restrict__ ops, const BatchSys* __restric
           break;
         }
         case BOP_TRSM:
-          if (op.e) dev_trsm<double>(A, ld, op.a, op.b, op.c, op.d, smem);
-          else dev_trsm<float>(A, ld, op.a, op.b, op.c, op.d, smem);
+          if (op.e) dev_trsm<double>(A, ld, op.a, op.b, op.c, op.d, S.s32, S.s16, S.n, err, smem);
+          else dev_trsm<float>(A, ld, op.a, op.b, op.c, op.d, S.s32, S.s16, S.n, err, smem);
           break;
         case BOP_GEMM: {
           double* C = A + (size_t)op.c * ld + op.a;
-          const double* X = A + (size_t)op.e * ld + op.a;
-          const double* Y = A + (size_t)op.e * ld + op.c;
-          if (op.p == HRP_F64) dev_gemm<0>(C, ld, X, ld, Y, ld, op.b, op.d, op.f, op.g != 0, smem);
-          else if (op.p == HRP_F32) dev_gemm<1>(C, ld, X, ld, Y, ld, op.b, op.d, op.f, op.g != 0, smem);
-          else dev_gemm<2>(C, ld, X, ld, Y, ld, op.b, op.d, op.f, op.g != 0, smem);
+          const size_t xo = (size_t)op.e * S.n + op.a, yo = (size_t)op.e * S.n + op.c;
+          if (op.p == HRP_F64)
+            dev_gemm<0>(C, ld, A + (size_t)op.e * ld + op.a, ld, A + (size_t)op.e * ld + op.c, ld, op.b, op.d, op.f,
+                        op.g != 0, smem);
+          else if (op.p == HRP_F32)
+            dev_gemm<1>(C, ld, S.s32 + xo, S.n, S.s32 + yo, S.n, op.b, op.d, op.f, op.g != 0, smem);
+          else
+            dev_gemm<2>(C, ld, S.s16 + xo, S.n, S.s16 + yo, S.n, op.b, op.d, op.f, op.g != 0, smem);
           break;
         }
         default:
