@@ -33,10 +33,12 @@ TREE = "[F16,F16,F16,F16,F32|F64@128]"
 LEAF = 128
 FP64_TREE, FP64_LEAF = "[F64]", 64
 METRIC = "POTRF TFLOP/s (n^3/3 per s) mixed vs FP64 tree on GB300 at stated backward error"
-# FP64 rate of the GB300s from a DFMA microbenchmark: 1.7 lane-FMAs per clock per SM
-# (one warp instruction per ~19 cycles) x 152 SMs x 2 flops x 2.07 GHz.  FP64 kernels report
-# against it (NVIDIA's nominal figure is 1.25 TFLOP/s).
-FP64_MEASURED_TFLOPS = 1.18
+# FMA rates of the GB300s from a throughput microbenchmark (8 independent FMA chains
+# per thread, 4 x 152 CTAs of 256 threads, CUDA-event timed, SM clock 2.0 GHz): FP64 1.20 and
+# FP32 75.2 TFLOP/s.  ALU-bound kernels report against them (NVIDIA's nominal FP64 figure is
+# 1.25 TFLOP/s).
+FP64_MEASURED_TFLOPS = 1.20
+FP32_MEASURED_TFLOPS = 75.2
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture, reported
 # while the kernel's device code is the code captured: the source up to its launcher, hashed.
 LEAF_TRAFFIC = {"bytes": 150528, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
@@ -694,9 +696,9 @@ def main():
         if name == "gemm_f16_tcgen05":
             peak, bound, src = pk["bf16_tflops"], "tensor", f"{pk['src']} bf16 dense burst (FP16 same rate)"
         elif name in ("leaf_potrf_fp64",):
-            peak, bound, src = FP64_MEASURED_TFLOPS, "alu", "FP64 1.18 TFLOP/s (DFMA microbenchmark, this pool)"
+            peak, bound, src = FP64_MEASURED_TFLOPS, "alu", "FP64 1.20 TFLOP/s (DFMA microbenchmark, this pool)"
         else:
-            peak, bound, src = 69.0, "alu", "FP32 FFMA 69 TFLOP/s (152 SMs x 128 lanes x 2 x 1.77 GHz)"
+            peak, bound, src = FP32_MEASURED_TFLOPS, "alu", "FP32 75.2 TFLOP/s (FFMA microbenchmark, this pool)"
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": leaf_traffic() if name == "leaf_potrf_fp64" else None, "kernel": name,
                 "avg_launch_ms": avg_ms, "peak_src": src}
