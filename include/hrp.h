@@ -152,6 +152,17 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * Scaling before the recursion (dynamic quantization, the paper's future work for matrices of
+ * extreme dynamic range, Sec. 4.5).  mode 0 (default): none; every FP16 operand is checked
+ * against 65504 (Sec. 3.4 with alpha = 1, HRP_ERR_RANGE otherwise).  mode 1: hrp_potrf and
+ * hrp_posv factor D^-1 A D^-1 with D = diag(2^e_i), e_i = floor(ex_i / 2) for
+ * a_ii = m 2^ex_i (m in [0.5, 1)), so every scaled diagonal entry lies in [0.5, 2); the factor
+ * returned is L = D L_hat.  Powers of two make both scalings exact (away from subnormals), and
+ * every row meets the FP16 range at the scale of its own diagonal.
+ */
+hrp_status hrp_set_scaling(hrp_handle* h, int mode);
+
+/*
  * Refinement of hrp_posv.  mode 0 (default): classical iterative refinement, each
  * correction an FP32 POTRS with the factor.  mode 1: GMRES-IR (Carson and Higham, the
  * refinement literature of the paper's Sec. 1-2): each correction d solves A d = r by

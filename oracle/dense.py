@@ -101,6 +101,16 @@ def backward_error(A: np.ndarray, L: np.ndarray) -> float:
     return float(np.linalg.norm(As - Lt @ Lt.T) / np.linalg.norm(As))
 
 
+def scaled_backward_error(A: np.ndarray, L: np.ndarray) -> float:
+    """Backward error of the diagonally scaled problem: ||S (A - L L^T) S||_F / ||S A S||_F with
+    S = diag(a_ii^-1/2), the measure that sees every row whatever its scale."""
+    As = sym_from_lower(np.asarray(A, dtype=np.float64))
+    s = 1.0 / np.sqrt(np.diag(As))
+    Lt = np.tril(np.asarray(L, dtype=np.float64)) * s[:, None]
+    Ss = As * s[:, None] * s[None, :]
+    return float(np.linalg.norm(Ss - Lt @ Lt.T) / np.linalg.norm(Ss))
+
+
 def factor_error(L_hat: np.ndarray, L: np.ndarray) -> float:
     """||L_hat - L||_F / ||L||_F over the lower triangles."""
     return float(np.linalg.norm(np.tril(L_hat) - np.tril(L)) / np.linalg.norm(np.tril(L)))

@@ -312,3 +312,29 @@ def emulate_trsm(B: np.ndarray, L: np.ndarray, tree: Tree) -> np.ndarray:
     if m and n:
         rec(0, n, 0)
     return X
+
+
+# ---------------------------------------------------------------------------------------
+# Dynamic quantization (the paper's future work, Sec. 4.5 and 5): two-sided diagonal scaling
+# by powers of two before the recursion.  Reading: with a_ii = m 2^ex (m in [0.5, 1)),
+# d_i = 2^floor(ex / 2) (d_i = 1 for a_ii <= 0 or not finite), so that a_ii / d_i^2 lies in
+# [0.5, 2); A_hat = D^-1 A D^-1 (exact in float64), L_hat by the tree, then L = D L_hat
+# (exact).  Every row then meets the FP16 range at the scale of its own diagonal, whatever the
+# dynamic range of A; powers of two keep the scaling itself free of rounding.
+# ---------------------------------------------------------------------------------------
+def diagonal_scale_exponents(A: np.ndarray) -> np.ndarray:
+    d = np.diag(np.asarray(A, dtype=np.float64)).copy()
+    ok = np.isfinite(d) & (d > 0)
+    e = np.zeros(d.shape[0], dtype=np.int64)
+    _, ex = np.frexp(d[ok])
+    e[ok] = np.floor_divide(ex, 2)
+    return e
+
+
+def emulate_potrf_scaled(A: np.ndarray, tree: Tree, leaf_compute: str | None = None):
+    """(L, info, emulator) of the tree on D^-1 A D^-1, unscaled (see above)."""
+    e = diagonal_scale_exponents(A)
+    A = np.asarray(A, dtype=np.float64)
+    Ah = np.ldexp(np.ldexp(A, -e[:, None]), -e[None, :])
+    Lh, info, em = emulate_potrf(Ah, tree, leaf_compute)
+    return np.ldexp(Lh, e[:, None]), info, em

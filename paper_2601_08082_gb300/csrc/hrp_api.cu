@@ -93,6 +93,11 @@ struct hrp_handle_s {
   double* kwork = nullptr;     // GMRES basis and vectors
   size_t kwork_cap = 0;
   long long inner_steps = 0;   // GMRES steps of the last hrp_posv
+  // scaling before the recursion: 0 = none (the static Sec. 3.4 rule, alpha = 1 checked),
+  // 1 = two-sided power-of-two diagonal scaling (dynamic quantization)
+  int scaling = 0;
+  int* scale_exp = nullptr;
+  size_t scale_exp_cap = 0;
   // batched factorization: 0 = one stream per system (default), 1 = one persistent launch
   int batched_mode = 0;
   // persistent launch plans: every distinct batch (its operation and system lists, byte for
@@ -563,9 +568,19 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
   } else {
     f.main_s = s;
   }
+  const bool scaled = h->scaling == 1 && n > 0;
+  if (scaled && (st = ensure(h, &h->scale_exp, &h->scale_exp_cap, (size_t)n)) != HRP_OK) return st;
   f.begin(CLS_OTHER, 0.0);
   f.chk(launch_fill_int(d_info, INT_MAX, 1, f.s));
+  if (scaled) {                               // A_hat = D^-1 A D^-1, D = diag(2^e_i)
+    f.begin(CLS_OTHER, 0.0);
+    f.chk(launch_diag_scale(dA, lda, n, h->scale_exp, false, f.s));
+  }
   f.potrf(0, n, 0);
+  if (scaled) {                               // L = D L_hat
+    f.begin(CLS_OTHER, 0.0);
+    f.chk(launch_diag_scale(dA, lda, n, h->scale_exp, true, f.s));
+  }
   f.begin(CLS_OTHER, 0.0);
   f.chk(launch_finalize_info(d_info, f.s));
   if (f.la) {
@@ -703,6 +718,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->bwork);
   cudaFree(h->fwork);
   cudaFree(h->kwork);
+  cudaFree(h->scale_exp);
   for (auto& pl : h->plans) {
     cudaFree(pl.ops);
     cudaFree(pl.sys);
@@ -1229,6 +1245,14 @@ hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner
 }
 
 long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
+
+hrp_status hrp_set_scaling(hrp_handle* h, int mode) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (mode != 0 && mode != 1) return bad_arg(h, 2, "mode must be 0 (static) or 1 (diagonal scaling)");
+  h->scaling = mode;
+  return HRP_OK;
+}
 
 hrp_status hrp_set_batched_mode(hrp_handle* h, int mode) {
   if (!h) return HRP_ERR_INVALID_ARG;

@@ -185,6 +185,10 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
 cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
                                  cudaStream_t s);
 cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s);
+// Two-sided power-of-two diagonal scaling of the lower triangle of A (n x n): unscale = false
+// computes e[i] = floor(ex_i / 2) from a_ii = m 2^ex_i and sets a_ij <- a_ij 2^-(e_i + e_j);
+// unscale = true sets l_ij <- l_ij 2^(e_i) (the factor of the original matrix).  e: n ints.
+cudaError_t launch_diag_scale(double* A, int lda, int n, int* e, bool unscale, cudaStream_t s);
 // Krylov helpers (FP64 vectors of length n; V column-major with leading dimension ldv):
 // out[j] = V[:, j] . w for j < nv (out device, zeroed here); w -= V[:, 0:nv] c (c device);
 // y = a x, or y += a x when accumulate.

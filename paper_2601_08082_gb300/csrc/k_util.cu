@@ -356,6 +356,45 @@ cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, 
   return cudaGetLastError();
 }
 
+// ---- dynamic quantization: two-sided power-of-two diagonal scaling ----
+// e[i] = floor(ex / 2) for a_ii = m 2^ex, m in [0.5, 1) (0 when a_ii <= 0 or not finite)
+__global__ void diag_exponents_kernel(const double* __restrict__ A, int lda, int n, int* __restrict__ e) {
+  pdl_wait();
+  pdl_trigger();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = A[(size_t)i * lda + i];
+    int ex = 0;
+    if (a > 0.0 && isfinite(a)) frexp(a, &ex);
+    e[i] = (a > 0.0 && isfinite(a)) ? (ex >= 0 ? ex / 2 : -((1 - ex) / 2)) : 0;   // floor(ex / 2)
+  }
+}
+// lower triangle: a_ij <- a_ij 2^(sign (e_i + e_j)) with sign = -1 (scale) or the rows only,
+// a_ij <- a_ij 2^(e_i) (unscale the factor); exact in FP64 away from the subnormal range
+__global__ void diag_scale_kernel(double* __restrict__ A, int lda, int n, const int* __restrict__ e, int unscale) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.y;
+  for (int j0 = j; j0 < n; j0 += gridDim.y) {
+    const int ej = e[j0];
+    for (int i = j0 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double* p = A + (size_t)j0 * lda + i;
+      *p = unscale ? ldexp(*p, e[i]) : ldexp(*p, -(e[i] + ej));
+    }
+  }
+}
+
+cudaError_t launch_diag_scale(double* A, int lda, int n, int* e, bool unscale, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t err = cudaSuccess;
+  if (!unscale) {
+    (void)launch_pdl(diag_exponents_kernel, dim3((n + 255) / 256), dim3(256), 0, s, A, lda, n, e);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const dim3 grid((n + 255) / 256 < 8 ? (n + 255) / 256 : 8, n < 4096 ? n : 4096);
+  (void)launch_pdl(diag_scale_kernel, grid, dim3(256), 0, s, A, lda, n, (const int*)e, unscale ? 1 : 0);
+  return cudaGetLastError();
+}
+
 // ---- Krylov helpers of the GMRES refinement (FP64) ----
 // out[j] += sum_i V[j ldv + i] w[i] for j < nv: blocks of 1024 rows per column, reduced in
 // shared memory, one FP64 atomic per block and column (out is zeroed by the caller)

@@ -12,6 +12,7 @@ from .generators import (  # noqa: F401
     paper_spd,
     rbf_spd,
     gram_spd,
+    wide_range_spd,
     rhs,
     known_factor,
 )

@@ -15,6 +15,8 @@ Workloads (matrix definitions):
     synthetic matrices of the paper's evaluation (Sec. 4.1).
   * ``rbf_spd``: A_ij = exp(-|x_i - x_j|^2 / (2 l^2)) + jitter * delta_ij, x_i ~ U[0,1]^3.
   * ``gram_spd``: A = G G^T / k + alpha I with G n x k N(0,1), k = n/2.
+  * ``wide_range_spd``: D C D with a dominant or Gram core and a diagonal D spanning many
+    decades (extreme dynamic range).
   * ``known_factor``: a random lower-triangular L with positive diagonal (for A = L L^T tests).
 
 All matrices are returned as full symmetric float64 numpy arrays (C order; since
@@ -36,6 +38,7 @@ STREAM_RHS = 2
 STREAM_POINTS = 3
 STREAM_FACTOR = 4
 STREAM_GRAM = 5
+STREAM_SCALE = 6
 
 
 def seed_for(config_index: int, instance: int = 0) -> int:
@@ -132,6 +135,17 @@ def gram_spd(n: int, alpha: float, seed: int) -> np.ndarray:
     A = 0.5 * (A + A.T)
     A[np.arange(n), np.arange(n)] += alpha
     return A
+
+
+def wide_range_spd(n: int, decades: float, seed: int, core: str = "dominant", rho: float = 1.5,
+                   alpha: float = 1e-2) -> np.ndarray:
+    """A = D C D with C a "dominant" (rho) or "gram" (alpha) SPD core and D = diag(d),
+    d_i = 10^((decades / 4)(2 u_i - 1)), u_i ~ U[0,1): the diagonal spans about `decades`
+    decades and the entries far more (matrices with an extreme dynamic range, Sec. 4.5)."""
+    C = dominant_spd(n, rho, seed) if core == "dominant" else gram_spd(n, alpha, seed)
+    u = uniforms(seed, STREAM_SCALE, np.arange(n, dtype=np.uint64))
+    d = 10.0 ** ((decades / 4.0) * (2.0 * u - 1.0))
+    return C * d[:, None] * d[None, :]
 
 
 def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:

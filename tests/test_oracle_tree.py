@@ -375,3 +375,65 @@ def test_fp32_trsm_recovers_an_exact_solution():
     B = X @ L.T
     assert np.max(np.abs(B)) < 2 ** 24
     assert np.array_equal(dense.trsm_rlt(B, L, np.float32), X)
+
+
+# ---------------------------------------------------------------------------------------
+# dynamic quantization: power-of-two two-sided diagonal scaling (emulate_potrf_scaled)
+# ---------------------------------------------------------------------------------------
+def test_scaled_factor_is_row_scaled_exactly():
+    """For A = P C P with P a diagonal of powers of two, the scaled emulation returns exactly
+    P times C's scaled factor: the exponents shift by those of P and the tree sees the same
+    A_hat.  A mistake in the exponents (one-sided scaling, wrong sign, rounding of the scale)
+    breaks the equality."""
+    n = 300
+    from synth import dominant_spd
+    C = dominant_spd(n, 1.5, seed_for(10, 1))
+    rng = np.random.default_rng(5)
+    p = 2.0 ** rng.integers(-40, 41, n)
+    A = C * p[:, None] * p[None, :]
+    t = tree.parse("[F16,F32]", leaf=64)
+    LA, infoA, _ = tree.emulate_potrf_scaled(A, t)
+    LC, infoC, _ = tree.emulate_potrf_scaled(C, t)
+    assert infoA == infoC == 0
+    assert np.array_equal(LA, LC * p[:, None])
+
+
+def test_scaling_is_the_identity_on_a_unit_diagonal():
+    n = 256
+    from synth import dominant_spd
+    C = dominant_spd(n, 1.5, seed_for(10, 2))
+    s = 1 / np.sqrt(np.diag(C))
+    C1 = C * s[:, None] * s[None, :]           # unit diagonal: every exponent is 0
+    assert not tree.diagonal_scale_exponents(C1).any()
+    t = tree.parse("[F16,F16,F32|F64@64]", leaf=64)
+    assert np.array_equal(tree.emulate_potrf_scaled(C1, t)[0], tree.emulate_potrf(C1, t)[0])
+
+
+def test_static_quantization_fails_on_an_extreme_range_and_scaling_does_not():
+    """Sec. 4.5: with an extreme dynamic range the static per-block scaling flushes the small
+    values and the factorization loses positive definiteness (info > 0); the dynamic scheme
+    factors the same matrix with the scaled backward error of the core matrix alone."""
+    from synth import gram_spd, wide_range_spd
+    n = 512
+    t = tree.parse("[F16,F16,F32|F64@128]", leaf=64)
+    A = wide_range_spd(n, 24, seed_for(10, 3), core="gram", alpha=1e-3)
+    _, info, _ = tree.emulate_potrf(A, t)
+    assert info > 0
+    L, info_s, _ = tree.emulate_potrf_scaled(A, t)
+    assert info_s == 0
+    C = gram_spd(n, 1e-3, seed_for(10, 3))
+    Lc, _, _ = tree.emulate_potrf_scaled(C, t)
+    assert dense.scaled_backward_error(A, L) <= 2 * dense.scaled_backward_error(C, Lc)
+
+
+def test_scaled_diagonal_lies_in_half_to_two():
+    """The exponents bring every positive, finite diagonal entry into [0.5, 2) whatever its
+    magnitude (including subnormal and near-overflow entries), and leave the others alone."""
+    rng = np.random.default_rng(7)
+    d = np.ldexp(rng.uniform(0.5, 1.0, 400), rng.integers(-1070, 1020, 400))
+    A = np.diag(d)
+    e = tree.diagonal_scale_exponents(A)
+    s = np.ldexp(np.ldexp(d, -e), -e)
+    assert np.all((s >= 0.5) & (s < 2.0))
+    bad = np.diag(np.array([0.0, -3.0, np.inf, np.nan, 1e300]))
+    assert tree.diagonal_scale_exponents(bad).tolist()[:4] == [0, 0, 0, 0]
