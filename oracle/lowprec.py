@@ -13,6 +13,14 @@ format's range before the low-precision product and scales the result back.
     Written here from that definition (numpy has no FP8 type); saturating
     ("satfinite") rounding clamps finite overflow to +-448.
 
+  * TF32: binary32's exponent range with 10 explicit mantissa bits (11 significant bits),
+    the tensor-core input format of the FP32 levels when they run on tensor cores; round to
+    nearest even, written here from that definition.
+  * TF32 split (Ootomo and Yokota, 2022, error-corrected single-precision GEMM on tensor
+    cores; the remedy for FP32 diagonal regions named by the paper's Sec. 5): an FP32
+    operand x becomes hi = tf32(x) and lo = tf32(x - hi); the product a b is taken as
+    hi_a hi_b + (hi_a lo_b + lo_a hi_b), dropping lo_a lo_b.  |x - hi - lo| <= 2^-22 |x|.
+
 Scaling rules
   * FP16 (Sec. 3.4): alpha = max(1, ||B||_inf / R_max) with R_max = 65504 and
     ||B||_inf read as the largest |b_ij| of the operand block; the block is
@@ -31,6 +39,33 @@ E4M3_MAX = 448.0
 
 def round_f32(x: np.ndarray) -> np.ndarray:
     return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def round_tf32(x: np.ndarray) -> np.ndarray:
+    """Round to TF32 (11 significant bits, binary32's exponent range), nearest even."""
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    _, ex = np.frexp(ax)                      # ax = f * 2^ex, f in [0.5, 1)
+    e = np.maximum(ex - 1, -126)              # binade exponent (binary32's subnormal binade)
+    quantum = np.exp2((e - 10).astype(np.float64))
+    r = np.rint(ax / quantum) * quantum       # power-of-two divide: exact; rint: ties to even
+    r = np.where(ax == 0.0, 0.0, r)
+    out = np.copysign(r, x)
+    return np.where(np.isfinite(x), out, x)
+
+
+def split_tf32(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(hi, lo) of the FP32 rounding of x: hi = tf32(x32), lo = tf32(x32 - hi)."""
+    x32 = round_f32(x)
+    hi = round_tf32(x32)
+    return hi, round_tf32(x32 - hi)           # x32 - hi is exact in binary32
+
+
+def gemm_tf32x3(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """X Y^T from the TF32 splits of X and Y: hi hi^T + (hi lo^T + lo hi^T), summed in float64."""
+    hx, lx = split_tf32(X)
+    hy, ly = split_tf32(Y)
+    return hx @ hy.T + (hx @ ly.T + lx @ hy.T)
 
 
 def round_f16(x: np.ndarray) -> np.ndarray:

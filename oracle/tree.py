@@ -96,8 +96,9 @@ def _compute_dtype(p: str):
 class Emulator:
     """State of one emulated factorization: the float64 master and counters."""
 
-    def __init__(self, A: np.ndarray, tree: Tree, leaf_compute: str | None = None):
+    def __init__(self, A: np.ndarray, tree: Tree, leaf_compute: str | None = None, f32_split: bool = False):
         self.M = np.array(A, dtype=np.float64, copy=True)
+        self.f32_split = f32_split           # FP32-level GEMMs by the TF32 split (lowprec)
         self.n = self.M.shape[0]
         self.tree = tree
         self.leaf_compute = leaf_compute     # None, or "F64" to run every leaf in FP64
@@ -156,8 +157,11 @@ class Emulator:
     def _gemm(self, p, r0, m, c0, nd, k0, k, lower=False):
         if m == 0 or nd == 0 or k == 0:
             return
-        X, Y, scale = self._operands(p, r0, m, c0, nd, k0, k)
-        prod = scale * (X @ Y.T)
+        if p == "F32" and self.f32_split:
+            prod = lowprec.gemm_tf32x3(self.M[r0:r0 + m, k0:k0 + k], self.M[c0:c0 + nd, k0:k0 + k])
+        else:
+            X, Y, scale = self._operands(p, r0, m, c0, nd, k0, k)
+            prod = scale * (X @ Y.T)
         D = self.M[r0:r0 + m, c0:c0 + nd]
         if lower:
             # only entries on or below the diagonal of the (square) destination
@@ -207,9 +211,10 @@ class Emulator:
         self.potrf(off + n1, n2, depth + 1)
 
 
-def emulate_potrf(A: np.ndarray, tree: Tree, leaf_compute: str | None = None):
-    """(L, info, emulator) of the tree-precision recursive Cholesky of A's lower triangle."""
-    em = Emulator(A, tree, leaf_compute)
+def emulate_potrf(A: np.ndarray, tree: Tree, leaf_compute: str | None = None, f32_split: bool = False):
+    """(L, info, emulator) of the tree-precision recursive Cholesky of A's lower triangle.
+    f32_split: FP32-level GEMMs by the TF32 split (lowprec.gemm_tf32x3)."""
+    em = Emulator(A, tree, leaf_compute, f32_split)
     em.potrf(0, em.n, 0)
     return np.tril(em.M), em.info, em
 
@@ -254,16 +259,20 @@ def _operand(p: str, X: np.ndarray):
     raise ValueError("F8 levels are defined on the factorization's 128 x 128 tiles only")
 
 
-def emulate_syrk(C: np.ndarray, A: np.ndarray, tree: Tree) -> np.ndarray:
-    """Lower triangle of C - A A^T by Alg. 3 with the precision list applied by depth."""
+def emulate_syrk(C: np.ndarray, A: np.ndarray, tree: Tree, f32_split: bool = False) -> np.ndarray:
+    """Lower triangle of C - A A^T by Alg. 3 with the precision list applied by depth
+    (f32_split: FP32-level GEMMs by the TF32 split)."""
     C = np.array(C, dtype=np.float64, copy=True)
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
 
     def gemm(p, r0, m, c0, nd, lower):
-        X, ax = _operand(p, A[r0:r0 + m])
-        Y, ay = _operand(p, A[c0:c0 + nd])
-        prod = (ax * ay) * (X @ Y.T)
+        if p == "F32" and f32_split:
+            prod = lowprec.gemm_tf32x3(A[r0:r0 + m], A[c0:c0 + nd])
+        else:
+            X, ax = _operand(p, A[r0:r0 + m])
+            Y, ay = _operand(p, A[c0:c0 + nd])
+            prod = (ax * ay) * (X @ Y.T)
         if lower:
             prod = np.tril(prod)
         C[r0:r0 + m, c0:c0 + nd] -= prod

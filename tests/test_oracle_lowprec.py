@@ -112,3 +112,73 @@ def test_e4m3_tiles_use_the_global_grid():
     # a sub-block read through an offset sees the same scales
     q2, s2 = lowprec.quantize_e4m3_tiles(M, 160, 100, 64, 100, tile=128)
     assert s2[40, 40] == s[72, 140] and s2[0, 0] == s[32, 100]
+
+
+# ---------------------------------------------------------------------------------------
+# TF32 rounding and the error-corrected TF32 split (FP32 levels on tensor cores)
+# ---------------------------------------------------------------------------------------
+def _tf32_by_bits(x32: np.ndarray) -> np.ndarray:
+    """Round-to-nearest-even on the binary32 bit pattern: keep 10 of the 23 mantissa bits."""
+    b = x32.astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = b + 0x0FFF + ((b >> 13) & 1)
+    b = b & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_tf32_rounding_matches_the_bit_pattern_rule():
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal(200000) * np.exp2(rng.integers(-120, 120, 200000))).astype(np.float32)
+    assert np.array_equal(lowprec.round_tf32(x.astype(np.float64)), _tf32_by_bits(x))
+    # exact midpoints: low 13 bits = 0x1000, bit 13 even and odd
+    base = (rng.integers(0x00800000, 0x7E000000, 4000).astype(np.uint32) & np.uint32(0xFFFFE000))
+    mids = (base | np.uint32(0x1000)).view(np.float32)
+    got = lowprec.round_tf32(mids.astype(np.float64))
+    assert np.array_equal(got, _tf32_by_bits(mids))
+    even = np.where((base >> 13) & 1, (base + np.uint32(0x2000)).view(np.float32), base.view(np.float32))
+    assert np.array_equal(got, even.astype(np.float64))
+
+
+def test_tf32_values_round_trip():
+    e = np.arange(1, 255, dtype=np.uint32)
+    m = np.arange(0, 1024, dtype=np.uint32)
+    codes = ((e[:, None] << 23) | (m[None, :] << 13)).ravel()
+    v = codes.view(np.float32).astype(np.float64)
+    assert np.array_equal(lowprec.round_tf32(v), v)
+    assert np.array_equal(lowprec.round_tf32(-v), -v)
+
+
+def test_tf32_split_reconstructs_to_22_bits():
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(100000) * np.exp2(rng.integers(-60, 60, 100000))
+    hi, lo = lowprec.split_tf32(x)
+    x32 = lowprec.round_f32(x)
+    assert np.array_equal(lowprec.round_tf32(hi), hi) and np.array_equal(lowprec.round_tf32(lo), lo)
+    assert np.all(np.abs(x32 - hi - lo) <= 2.0 ** -22 * np.abs(x32))
+    assert np.all(np.abs(lo) <= 2.0 ** -11 * np.abs(hi))
+    # a value with at most 11 significant bits has no low part
+    small = np.round(rng.uniform(-1024, 1024, 1000)) * np.exp2(rng.integers(-30, 30, 1000))
+    assert not lowprec.split_tf32(small)[1].any()
+
+
+def test_tf32x3_product_is_exact_on_small_integers():
+    rng = np.random.default_rng(13)
+    X = rng.integers(-1000, 1001, (40, 300)).astype(np.float64)
+    Y = rng.integers(-1000, 1001, (30, 300)).astype(np.float64)
+    assert np.array_equal(lowprec.gemm_tf32x3(X, Y), X @ Y.T)
+
+
+def test_tf32x3_error_bound_and_the_correction_terms():
+    """|x y - (hx hy + hx ly + lx hy)| <= 3 2^-22 |x y| per term (la lb dropped, two
+    representation errors of 2^-22): the split product stays inside 3.01 2^-22 |X||Y|^T of the
+    exact product of the FP32 operands.  Dropping the correction terms (plain TF32) or
+    either one of them leaves that bound."""
+    rng = np.random.default_rng(14)
+    X = lowprec.round_f32(rng.standard_normal((64, 512)))
+    Y = lowprec.round_f32(rng.standard_normal((48, 512)))
+    exact = X @ Y.T
+    bound = 3.01 * 2.0 ** -22 * (np.abs(X) @ np.abs(Y).T)
+    assert np.all(np.abs(lowprec.gemm_tf32x3(X, Y) - exact) <= bound)
+    hx, lx = lowprec.split_tf32(X)
+    hy, ly = lowprec.split_tf32(Y)
+    for wrong in (hx @ hy.T, hx @ hy.T + hx @ ly.T, hx @ hy.T + lx @ hy.T, hx @ hy.T + hx @ ly.T - lx @ hy.T):
+        assert np.any(np.abs(wrong - exact) > bound)

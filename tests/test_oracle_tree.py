@@ -437,3 +437,27 @@ def test_scaled_diagonal_lies_in_half_to_two():
     assert np.all((s >= 0.5) & (s < 2.0))
     bad = np.diag(np.array([0.0, -3.0, np.inf, np.nan, 1e300]))
     assert tree.diagonal_scale_exponents(bad).tolist()[:4] == [0, 0, 0, 0]
+
+
+def test_split_fp32_levels_recover_an_exact_factor():
+    """Integer L with a unit diagonal and entries in {-3..3}: every operand is exact in TF32 and
+    every leaf exact in FP32, so the split emulation returns L itself."""
+    n = 300
+    L = np.tril(np.floor(np.random.default_rng(15).uniform(0, 7, (n, n))) - 3.0, -1) + np.eye(n)
+    A = L @ L.T
+    Le, info, _ = tree.emulate_potrf(A, tree.parse("[F32,F32|F64@64]", leaf=64), f32_split=True)
+    assert info == 0 and np.array_equal(Le, L)
+
+
+def test_split_fp32_levels_are_fp32_accurate_and_differ_from_plain_fp32():
+    from synth import dominant_spd
+    n = 512
+    A = dominant_spd(n, 1.5, seed_for(10, 20))
+    t = tree.parse("[F32,F32|F64@64]", leaf=64)
+    Ls, _, _ = tree.emulate_potrf(A, t, f32_split=True)
+    Lp, _, _ = tree.emulate_potrf(A, t)
+    L64, _ = dense.cholesky(A)
+    assert not np.array_equal(Ls, Lp)
+    for L in (Ls, Lp):
+        assert dense.backward_error(A, L) <= 8 * 2.0 ** -24
+        assert dense.factor_error(L, L64) <= 1e-6
