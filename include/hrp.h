@@ -152,6 +152,19 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * FP32 levels on tensor cores (the paper names tensor-core FP32 regions as future work,
+ * Sec. 5).  on = 0 (default): the FP32-level GEMMs of hrp_potrf, hrp_potrf_async, hrp_posv and
+ * hrp_syrk run on the SIMT FP32 pipe.  on = 1: products of at least 2e6 multiply-adds with
+ * K >= 32 run on tcgen05 by the error-corrected TF32 split of Ootomo and Yokota (2022): each
+ * FP32 operand x is held as hi = tf32(x), lo = tf32(x - hi) (|x - hi - lo| <= 2^-22 |x|), the
+ * product is hi hi^T + (hi lo^T + lo hi^T) with FP32 accumulation, the two parts in separate
+ * accumulators, and the result is within 3 2^-22 |X||Y|^T plus the FP32 accumulation error of
+ * the FP32 product.  The split arrays take 8 bytes per entry of L (n x ceil64(n) x 2 floats).
+ * The batched calls and hrp_trsm keep the SIMT path.
+ */
+hrp_status hrp_set_fp32_split(hrp_handle* h, int on);
+
+/*
  * Scaling before the recursion (dynamic quantization, the paper's future work for matrices of
  * extreme dynamic range, Sec. 4.5).  mode 0 (default): none; every FP16 operand is checked
  * against 65504 (Sec. 3.4 with alpha = 1, HRP_ERR_RANGE otherwise).  mode 1: hrp_potrf and
@@ -189,7 +202,7 @@ hrp_status hrp_backward_error(hrp_handle* h, int n, const double* dA, int lda,
  * bracketed by CUDA events on the call's stream, and the factorization synchronizes the
  * stream once at its end (so do not enable it while capturing a graph).
  * hrp_get_timing writes, for each kernel class c = 0..4 (leaf POTRF, leaf TRSM, tcgen05
- * FP16 GEMM, SIMT GEMM, other), the triple out[3c] = summed device milliseconds,
+ * GEMM (FP16, F8 and TF32-split levels), SIMT GEMM, other), the triple out[3c] = summed device milliseconds,
  * out[3c+1] = launches, out[3c+2] = algorithmic flops of the last factorization.
  * Returns the number of doubles written (<= n).
  */

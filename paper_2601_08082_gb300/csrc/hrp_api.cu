@@ -98,6 +98,10 @@ struct hrp_handle_s {
   int scaling = 0;
   int* scale_exp = nullptr;
   size_t scale_exp_cap = 0;
+  // FP32-level GEMMs: 0 = SIMT FP32 (default), 1 = error-corrected TF32 split on tcgen05
+  int fp32_split = 0;
+  float* split32 = nullptr;    // hi then lo, row-major (see Fact::h32)
+  size_t split32_cap = 0;
   // batched factorization: 0 = one stream per system (default), 1 = one persistent launch
   int batched_mode = 0;
   // persistent launch plans: every distinct batch (its operation and system lists, byte for
@@ -214,6 +218,10 @@ void apply_tuned(const hrp_handle* h, hrp_tree* t, int n) {
 // ------------------------------------------------------------------------------------
 // One factorization: the recursion of Alg. 1-3 turned into stream-ordered launches.
 // ------------------------------------------------------------------------------------
+// FP32-level products large enough to pay for the tensor-core kernel's fixed cost (TMEM
+// allocation, barrier set-up, pipeline fill); smaller ones stay on the SIMT pipe
+bool split_tc_worth(int m, int n, int k) { return k >= 32 && (double)m * n * k >= 2.0e6; }
+
 struct Fact {
   hrp_handle* h;
   const hrp_tree* t;
@@ -229,6 +237,11 @@ struct Fact {
   int* tile_exp;
   float* shadow32;      // null: FP32-level GEMMs round their operands from the master
   int ld32;
+  // TF32 split of every block finished by an F32 or F64 leaf TRSM (row-major, ld ldh): the
+  // operands of the FP32-level GEMMs on tensor cores; null when they run on the SIMT pipe
+  float* h32 = nullptr;
+  float* l32 = nullptr;
+  int ldh = 0;
   bool tc;
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
   cudaError_t err = cudaSuccess;
@@ -314,6 +327,7 @@ struct Fact {
     if (p == HRP_F64 || t->trsm_compute == 1) {
       chk(launch_trsm_leaf64(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, h->d_err, s));
       quant8(r0, m, c0, nc, p);
+      split_block(r0, m, c0, nc, p);
       return;
     }
     auto it = leaves.find(c0);
@@ -324,6 +338,14 @@ struct Fact {
       chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, h->d_err, s));
     }
     quant8(r0, m, c0, nc, p);
+    split_block(r0, m, c0, nc, p);
+  }
+  // the FP32-level GEMMs of a node read blocks finished inside it, by leaves of precision F32
+  // (or F64 below an |F64@S cut-off)
+  void split_block(int r0, int m, int c0, int nc, int p) {
+    if (!h32 || (p != HRP_F32 && p != HRP_F64)) return;
+    begin(CLS_OTHER, 0.0);
+    chk(launch_split_tf32(A, lda, r0, m, c0, nc, h32, l32, ldh, s));
   }
 
   // FP8 levels: E4M3 tiles (scale per 128 x 128 tile) of what the F8-level GEMMs of a node
@@ -353,14 +375,18 @@ struct Fact {
     const double* X = A + (size_t)k0 * lda + r0;
     const double* Y = A + (size_t)k0 * lda + c0;
     const double fl = lower ? (double)m * (m + 1) * k : 2.0 * m * nd * k;
-    const bool use_tc = (p == HRP_F16 || p == HRP_F8E4M3) && tc && (k0 % 8) == 0 && k >= 16;
+    const bool split_tc = p == HRP_F32 && h32 && (k0 % 4) == 0 && split_tc_worth(m, nd, k);
+    const bool use_tc = ((p == HRP_F16 || p == HRP_F8E4M3) && tc && (k0 % 8) == 0 && k >= 16) || split_tc;
     begin(use_tc ? CLS_GEMM_TC : CLS_GEMM_SIMT, fl);
     switch (p) {
       case HRP_F64: chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F64, lower, s)); break;
       case HRP_F32:
         // every FP32-level operand is an off-diagonal block of L, finished by a leaf TRSM that
         // also wrote its FP32 rounding into the shadow
-        if (shadow32)
+        if (split_tc)
+          chk(launch_gemm_tf32x3_tc(C, lda, h32, l32, ldh, r0, c0, k0, m, nd, k, lower, h->d_err, s,
+                                    t->tile_occupancy));
+        else if (shadow32)
           chk(launch_gemm_simt_f32(C, lda, shadow32 + (size_t)k0 * ld32 + r0, ld32, shadow32 + (size_t)k0 * ld32 + c0,
                                    ld32, m, nd, k, lower, s));
         else
@@ -552,6 +578,12 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
   }
   f.shadow32 = nullptr;
   f.ld32 = n;
+  if (h->fp32_split && f.tc && tree_has(t, HRP_F32) && n > 0) {
+    f.ldh = f.lds;
+    if ((st = ensure(h, &h->split32, &h->split32_cap, 2 * (size_t)n * f.ldh)) != HRP_OK) return st;
+    f.h32 = h->split32;
+    f.l32 = h->split32 + (size_t)n * f.ldh;
+  }
   if (tree_has(t, HRP_F32) && n > 0) {
     if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)n * n)) != HRP_OK) return st;
     f.shadow32 = h->shadow32;
@@ -719,6 +751,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->fwork);
   cudaFree(h->kwork);
   cudaFree(h->scale_exp);
+  cudaFree(h->split32);
   for (auto& pl : h->plans) {
     cudaFree(pl.ops);
     cudaFree(pl.sys);
@@ -1245,6 +1278,14 @@ hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner
 }
 
 long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
+
+hrp_status hrp_set_fp32_split(hrp_handle* h, int on) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (on != 0 && on != 1) return bad_arg(h, 2, "on must be 0 (SIMT FP32) or 1 (TF32 split on tensor cores)");
+  h->fp32_split = on;
+  return HRP_OK;
+}
 
 hrp_status hrp_set_scaling(hrp_handle* h, int mode) {
   if (!h) return HRP_ERR_INVALID_ARG;
@@ -2193,6 +2234,9 @@ struct SyrkRun : Blas3 {
   int lds;
   const float* A32;
   int ld32;
+  const float* h32 = nullptr;    // TF32 split of A (row-major, ldh), when FP32 levels run on tcgen05
+  const float* l32 = nullptr;
+  int ldh = 0;
   bool tc;
   int base() const { return t->syrk_leaf ? t->syrk_leaf : t->leaf; }
   // C[r0:r0+m, c0:c0+nd] -= A[r0:r0+m, :] A[c0:c0+nd, :]^T at precision p
@@ -2203,7 +2247,10 @@ struct SyrkRun : Blas3 {
         chk(launch_gemm_simt(Cb, ldc, A + r0, lda, A + c0, lda, m, nd, k, OpRound::F64, lower, s));
         break;
       case HRP_F32:
-        chk(launch_gemm_simt_f32(Cb, ldc, A32 + r0, ld32, A32 + c0, ld32, m, nd, k, lower, s));
+        if (h32 && split_tc_worth(m, nd, k))
+          chk(launch_gemm_tf32x3_tc(Cb, ldc, h32, l32, ldh, r0, c0, 0, m, nd, k, lower, h->d_err, s));
+        else
+          chk(launch_gemm_simt_f32(Cb, ldc, A32 + r0, ld32, A32 + c0, ld32, m, nd, k, lower, s));
         break;
       case HRP_F16:
         if (tc && k >= 16) chk(launch_gemm_f16_tc(Cb, ldc, S16, lds, r0, c0, 0, m, nd, k, lower, 1.0, h->d_err, s));
@@ -2332,6 +2379,13 @@ hrp_status hrp_syrk(hrp_handle* h, const hrp_tree* tree, int n, int k, const dou
     if ((st = ensure(h, &h->shadow32, &h->shadow32_cap, (size_t)n * k)) != HRP_OK) return st;
     r.A32 = h->shadow32;
     r.chk(launch_cast_f32(dA, lda, n, k, h->shadow32, n, r.s));
+    if (h->fp32_split && r.tc) {
+      r.ldh = (k + 63) / 64 * 64;
+      if ((st = ensure(h, &h->split32, &h->split32_cap, 2 * (size_t)n * r.ldh)) != HRP_OK) return st;
+      r.h32 = h->split32;
+      r.l32 = h->split32 + (size_t)n * r.ldh;
+      r.chk(launch_split_tf32(dA, lda, 0, n, 0, k, h->split32, h->split32 + (size_t)n * r.ldh, r.ldh, r.s));
+    }
   }
   r.rec(0, n, 0);
   launch_ctx() = LaunchCtx{};

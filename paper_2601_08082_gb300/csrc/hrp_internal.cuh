@@ -185,6 +185,16 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
 cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
                                  cudaStream_t s);
 cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s);
+// TF32 split of an FP32-level block: hi = tf32(fp32(a)), lo = tf32(fp32(a) - hi), read from the
+// column-major FP64 block A[r0.., c0..] (m x nc) and written row-major at [(r0 + i) ldh + c0 + j].
+cudaError_t launch_split_tf32(const double* A, int lda, int r0, int m, int c0, int nc, float* H, float* Lo, int ldh,
+                              cudaStream_t s);
+// C[.., ..] -= X Y^T from TF32 splits (error-corrected FP32 GEMM on tcgen05, kind::tf32):
+// X rows xr0.., Y rows yr0.., K columns k0.. of the row-major hi (H) / lo (Lo) arrays (ldh);
+// k0 and ldh multiples of 4, H and Lo 16-byte aligned.  `lower` as for the FP16 GEMM.
+cudaError_t launch_gemm_tf32x3_tc(double* C, int ldc, const float* H, const float* Lo, int ldh, int xr0, int yr0,
+                                  int k0, int m, int n, int k, bool lower, unsigned* dev_err, cudaStream_t s,
+                                  int occupancy = 0);
 // Two-sided power-of-two diagonal scaling of the lower triangle of A (n x n): unscale = false
 // computes e[i] = floor(ex_i / 2) from a_ii = m 2^ex_i and sets a_ij <- a_ij 2^-(e_i + e_j);
 // unscale = true sets l_ij <- l_ij 2^(e_i) (the factor of the original matrix).  e: n ints.

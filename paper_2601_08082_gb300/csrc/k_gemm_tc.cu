@@ -6,6 +6,14 @@
 // `lower` it is the leaf SYRK of Alg. 3 (entries above the diagonal are skipped, and
 // tiles entirely above it are never computed).
 //
+// The same kernels, with SPLIT, run the FP32 levels on tensor cores by the error-corrected
+// TF32 split (Ootomo and Yokota, 2022): each FP32 operand is stored as hi = tf32(x) and
+// lo = tf32(x - hi) (row-major FP32 arrays written once per finished block of L); per K
+// slice the MMA warp issues hi hi^T into one TMEM accumulator and hi lo^T + lo hi^T into a
+// second (kind::tf32, FP32 accumulation), and the epilogue subtracts their sum in FP64.
+// Keeping the small correction terms in their own accumulator keeps them from being
+// rounded away against the large one.
+//
 // One CTA computes one 128 x BN tile.  Warp roles: warp 0 issues TMA loads into a
 // STAGES-deep ring of 128B-swizzled K-major tiles, warp 1 owns the TMEM allocation and
 // issues the MMAs (one elected thread), warps 2-5 read the accumulator back with
@@ -20,9 +28,11 @@ namespace hrp {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;          // 64 fp16 = one 128-byte swizzle row
+constexpr int TC_ROW_BYTES = 128;  // one 128-byte swizzle row of K: 64 fp16 or 32 fp32 (tf32)
 constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 192;
+template <bool SPLIT> struct TcElem { static constexpr int BK = 64; };   // K elements per stage
+template <> struct TcElem<true> { static constexpr int BK = 32; };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -88,6 +98,40 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+// kind::tf32: A = B = TF32 (2) at bits 7-9 and 10-12, D = F32; K = 8 per instruction.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+// The MMAs of one 128-byte K slice (4 instructions of 32 bytes each) into the accumulator
+// set at `acc` (SPLIT: hi hi^T at acc, hi lo^T + lo hi^T at acc + BN).
+template <int BN, bool SPLIT>
+__device__ __forceinline__ void mma_slice(uint32_t acc, const uint8_t* a, const uint8_t* b, size_t a_tile,
+                                          size_t b_tile, bool first) {
+  const uint64_t ad = sw128_desc(a), bd = sw128_desc(b);
+  if constexpr (!SPLIT) {
+    constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)                 // K = 16 per instruction: +32 bytes
+      mma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (!first || kk > 0) ? 1u : 0u);
+  } else {
+    constexpr uint32_t idesc = idesc_tf32(TC_BM, BN);
+    const uint64_t adl = sw128_desc(a + a_tile), bdl = sw128_desc(b + b_tile);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {               // K = 8 per instruction: +32 bytes
+      const uint32_t accum = (!first || kk > 0) ? 1u : 0u;
+      mma_tf32(acc, ad + 2 * kk, bd + 2 * kk, idesc, accum);
+      mma_tf32(acc + BN, ad + 2 * kk, bdl + 2 * kk, idesc, accum);
+      mma_tf32(acc + BN, adl + 2 * kk, bd + 2 * kk, idesc, 1u);
+    }
+  }
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                ::"r"(smem_u32(bar)) : "memory");
@@ -108,39 +152,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN>
+// SPLIT: two operand tiles (hi, lo) per matrix and stage, and two accumulators per tile.
+template <int BN, bool SPLIT = false>
 struct TcLayout {
-  static constexpr size_t a_stage = (size_t)TC_BM * TC_BK * 2;
-  static constexpr size_t b_stage = (size_t)BN * TC_BK * 2;
+  static constexpr int ops = SPLIT ? 2 : 1;
+  static constexpr int stages = SPLIT && BN >= 128 ? 3 : TC_STAGES;
+  static constexpr size_t a_tile = (size_t)TC_BM * TC_ROW_BYTES;
+  static constexpr size_t b_tile = (size_t)BN * TC_ROW_BYTES;
+  static constexpr size_t a_stage = ops * a_tile;
+  static constexpr size_t b_stage = ops * b_tile;
+  static constexpr uint32_t acc_cols = SPLIT ? 2 * BN : BN;   // TMEM columns of one tile
   static constexpr size_t bars = 1024;  // barriers + tmem slot, padded
-  static constexpr size_t bytes = 1024 /*alignment slack*/ + TC_STAGES * (a_stage + b_stage) + bars;
+  static constexpr size_t bytes = 1024 /*alignment slack*/ + stages * (a_stage + b_stage) + bars;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, BN <= 64 ? 2 : 1)
-gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-                   double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
-                   unsigned* __restrict__ err) {
-  pdl_wait();
-  pdl_trigger();
-  using Lay = TcLayout<BN>;
+template <int BN, bool SPLIT>
+__device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXl,
+                                             const CUtensorMap* tmYl, double* __restrict__ C, int ldc, int m, int n,
+                                             int k, int lower, double scale, unsigned* __restrict__ err) {
+  using Lay = TcLayout<BN, SPLIT>;
+  constexpr int STAGES = Lay::stages;
+  constexpr int BK = TcElem<SPLIT>::BK;
   extern __shared__ unsigned char smem_raw[];
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
   if (lower && m0 + TC_BM - 1 < n0) return;          // tile strictly above the diagonal
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
-  uint8_t* sB = base + TC_STAGES * Lay::a_stage;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * Lay::b_stage);
-  uint64_t* empty = full + TC_STAGES;
-  uint64_t* accum = empty + TC_STAGES;
+  uint8_t* sB = base + STAGES * Lay::a_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Lay::b_stage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = (k + TC_BK - 1) / TC_BK;
+  const int nk = (k + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -150,7 +199,7 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"((uint32_t)BN) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(Lay::acc_cols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -160,31 +209,30 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 
   if (warp == 0) {
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmX)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmY)) : "memory");
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (kb / TC_STAGES) & 1;
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1)) { atomicOr(err, DEV_ERR_TIMEOUT); break; }
         mbar_arrive_expect_tx(&full[s], (uint32_t)(Lay::a_stage + Lay::b_stage));
-        tma_load_2d(sA + s * Lay::a_stage, &tmX, kb * TC_BK, m0, &full[s]);
-        tma_load_2d(sB + s * Lay::b_stage, &tmY, kb * TC_BK, n0, &full[s]);
+        tma_load_2d(sA + s * Lay::a_stage, tmX, kb * BK, m0, &full[s]);
+        tma_load_2d(sB + s * Lay::b_stage, tmY, kb * BK, n0, &full[s]);
+        if constexpr (SPLIT) {
+          tma_load_2d(sA + s * Lay::a_stage + Lay::a_tile, tmXl, kb * BK, m0, &full[s]);
+          tma_load_2d(sB + s * Lay::b_stage + Lay::b_tile, tmYl, kb * BK, n0, &full[s]);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
       bool ok = true;
       for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (kb / TC_STAGES) & 1;
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
         if (!mbar_wait(&full[s], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
         tc_fence_after();
-        const uint64_t ad = sw128_desc(sA + s * Lay::a_stage);
-        const uint64_t bd = sw128_desc(sB + s * Lay::b_stage);
-#pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk)      // K = 16 per instruction: +32 bytes
-          mma_f16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_slice<BN, SPLIT>(tmem, sA + s * Lay::a_stage, sB + s * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0);
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(accum);
@@ -199,8 +247,11 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
       const int row = m0 + q * 32 + lane;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= n) break;                       // uniform across the warp
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        tmem_ld32(taddr, r);
+        uint32_t r2[SPLIT ? 32 : 1];
+        if constexpr (SPLIT) tmem_ld32(taddr + BN, r2);
         if (row < m) {
           // all 32 loads first (independent, in flight together), then the 32 stores
           double* base_p = C + (size_t)(n0 + c0) * ldc + row;
@@ -213,8 +264,9 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
-            if (col < n && (!lower || row >= col))
-              __stcs(base_p + (size_t)j * ldc, cv[j] - scale * (double)__uint_as_float(r[j]));
+            double v = (double)__uint_as_float(r[j]);
+            if constexpr (SPLIT) v += (double)__uint_as_float(r2[j]);
+            if (col < n && (!lower || row >= col)) __stcs(base_p + (size_t)j * ldc, cv[j] - scale * v);
           }
         }
       }
@@ -224,8 +276,28 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::acc_cols) : "memory");
   }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, BN <= 64 ? 2 : 1)
+gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                   double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
+                   unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tile<BN, false>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, err);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                      const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
+                      double* __restrict__ C, int ldc, int m, int n, int k, int lower, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tile<BN, true>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, err);
 }
 
 // Persistent variant for products with more tiles than SMs: each CTA walks the active
@@ -252,31 +324,31 @@ __device__ __forceinline__ bool tile_of(int idx, int gm, int gn, bool lower, int
   return false;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-                       double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
-                       int ntiles, unsigned* __restrict__ err) {
-  pdl_wait();
-  pdl_trigger();
-  using Lay = TcLayout<BN>;
+template <int BN, bool SPLIT>
+__device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXl,
+                                              const CUtensorMap* tmYl, double* __restrict__ C, int ldc, int m, int n,
+                                              int k, int lower, double scale, int ntiles, unsigned* __restrict__ err) {
+  using Lay = TcLayout<BN, SPLIT>;
+  constexpr int STAGES = Lay::stages;
+  constexpr int BK = TcElem<SPLIT>::BK;
+  constexpr uint32_t ACC = Lay::acc_cols;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
-  uint8_t* sB = base + TC_STAGES * Lay::a_stage;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * Lay::b_stage);
-  uint64_t* empty = full + TC_STAGES;
-  uint64_t* acc_full = empty + TC_STAGES;          // [2]
+  uint8_t* sB = base + STAGES * Lay::a_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Lay::b_stage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;             // [2]
   uint64_t* acc_empty = acc_full + 2;              // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nk = (k + TC_BK - 1) / TC_BK;
+  const int nk = (k + BK - 1) / BK;
   const int gm = (m + TC_BM - 1) / TC_BM, gn = (n + BN - 1) / BN;
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < TC_STAGES; ++q) {
+    for (int q = 0; q < STAGES; ++q) {
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], 1);
     }
@@ -290,7 +362,7 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"((uint32_t)(2 * BN)) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(2 * ACC) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -301,30 +373,33 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
 
   if (warp == 0) {
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmX)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmY)) : "memory");
       long long kb_all = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int mt, nt;
         if (!tile_of<BN>(t, gm, gn, lower != 0, mt, nt)) break;
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
-          const int q = (int)(kb_all % TC_STAGES);
-          const uint32_t ph = (uint32_t)((kb_all / TC_STAGES) & 1);
+          const int q = (int)(kb_all % STAGES);
+          const uint32_t ph = (uint32_t)((kb_all / STAGES) & 1);
           if (!mbar_wait(&empty[q], ph ^ 1)) { atomicOr(err, DEV_ERR_TIMEOUT); *abort_flag = 1; break; }
           mbar_arrive_expect_tx(&full[q], (uint32_t)(Lay::a_stage + Lay::b_stage));
-          tma_load_2d(sA + q * Lay::a_stage, &tmX, kb * TC_BK, mt * TC_BM, &full[q]);
-          tma_load_2d(sB + q * Lay::b_stage, &tmY, kb * TC_BK, nt * BN, &full[q]);
+          tma_load_2d(sA + q * Lay::a_stage, tmX, kb * BK, mt * TC_BM, &full[q]);
+          tma_load_2d(sB + q * Lay::b_stage, tmY, kb * BK, nt * BN, &full[q]);
+          if constexpr (SPLIT) {
+            tma_load_2d(sA + q * Lay::a_stage + Lay::a_tile, tmXl, kb * BK, mt * TC_BM, &full[q]);
+            tma_load_2d(sB + q * Lay::b_stage + Lay::b_tile, tmYl, kb * BK, nt * BN, &full[q]);
+          }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
       long long kb_all = 0;
       int it = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++it) {
         const int b = it & 1;
-        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        const uint32_t acc = tmem + (uint32_t)b * ACC;
         if (!mbar_wait(&acc_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1))) {
           atomicOr(err, DEV_ERR_TIMEOUT);
           *abort_flag = 1;
@@ -333,15 +408,11 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
         tc_fence_after();
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
-          const int q = (int)(kb_all % TC_STAGES);
-          const uint32_t ph = (uint32_t)((kb_all / TC_STAGES) & 1);
+          const int q = (int)(kb_all % STAGES);
+          const uint32_t ph = (uint32_t)((kb_all / STAGES) & 1);
           if (!mbar_wait(&full[q], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
           tc_fence_after();
-          const uint64_t ad = sw128_desc(sA + q * Lay::a_stage);
-          const uint64_t bd = sw128_desc(sB + q * Lay::b_stage);
-#pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk)
-            mma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_slice<BN, SPLIT>(acc, sA + q * Lay::a_stage, sB + q * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0);
           mma_commit(&empty[q]);
         }
         if (!ok) { *abort_flag = 1; break; }
@@ -363,8 +434,11 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
       const int row = m0 + qd * 32 + lane;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= n) break;                       // uniform across the warp
+        const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)b * ACC + (uint32_t)c0;
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + c0), r);
+        tmem_ld32(taddr, r);
+        uint32_t r2[SPLIT ? 32 : 1];
+        if constexpr (SPLIT) tmem_ld32(taddr + BN, r2);
         if (row < m) {
           double* base_p = C + (size_t)(n0 + c0) * ldc + row;
           double cv[32];
@@ -376,8 +450,9 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
-            if (col < n && (!lower || row >= col))
-              __stcs(base_p + (size_t)j * ldc, cv[j] - scale * (double)__uint_as_float(r[j]));
+            double v = (double)__uint_as_float(r[j]);
+            if constexpr (SPLIT) v += (double)__uint_as_float(r2[j]);
+            if (col < n && (!lower || row >= col)) __stcs(base_p + (size_t)j * ldc, cv[j] - scale * v);
           }
         }
       }
@@ -391,9 +466,29 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC) : "memory");
   }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                       double* __restrict__ C, int ldc, int m, int n, int k, int lower, double scale,
+                       int ntiles, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tiles<BN, false>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, ntiles, err);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_tf32x3_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                          const __grid_constant__ CUtensorMap tmXl, const __grid_constant__ CUtensorMap tmYl,
+                          double* __restrict__ C, int ldc, int m, int n, int k, int lower, int ntiles,
+                          unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tiles<BN, true>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, ntiles, err);
 }
 
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -414,18 +509,20 @@ PFN_encodeTiled_t get_encode() {
   return fn;
 }
 
-// 2-D map over a rows x cols block of a row-major fp16 matrix (leading dimension ld elements),
-// box = box_rows x 64 columns, 128B swizzle, zero fill outside the block.
-bool make_map(CUtensorMap* map, const __half* base, int rows, int cols, int ld, int box_rows) {
+// 2-D map over a rows x cols block of a row-major fp16 or fp32 matrix (leading dimension ld
+// elements), box = box_rows x 128 bytes of K, 128B swizzle, zero fill outside the block.
+template <typename T>
+bool make_map(CUtensorMap* map, const T* base, int rows, int cols, int ld, int box_rows) {
+  static_assert(sizeof(T) == 2 || sizeof(T) == 4, "fp16 or fp32 operands");
   PFN_encodeTiled_t enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
+  cuuint32_t box[2] = {(cuuint32_t)(TC_ROW_BYTES / sizeof(T)), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt = sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -471,6 +568,40 @@ cudaError_t launch_bn(double* C, int ldc, const __half* S, int lds, int xr0, int
   return cudaGetLastError();
 }
 
+// TF32 split: hi / lo row-major FP32 arrays with the same layout (leading dimension ldh)
+template <int BN>
+cudaError_t launch_split(double* C, int ldc, const float* H, const float* Lo, int ldh, int xr0, int yr0, int k0,
+                         int m, int n, int k, bool lower, long long ntiles, int sms, bool persistent,
+                         unsigned* dev_err, cudaStream_t s) {
+  CUtensorMap mx, my, mxl, myl;
+  const size_t xo = (size_t)xr0 * ldh + k0, yo = (size_t)yr0 * ldh + k0;
+  if (!make_map(&mx, H + xo, m, k, ldh, TC_BM) || !make_map(&my, H + yo, n, k, ldh, BN) ||
+      !make_map(&mxl, Lo + xo, m, k, ldh, TC_BM) || !make_map(&myl, Lo + yo, n, k, ldh, BN))
+    return cudaErrorInvalidValue;
+  using Lay = TcLayout<BN, true>;
+  static unsigned long long attr_mask[2] = {0, 0};
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask[persistent] & attr_bit)) {
+    cudaError_t e = persistent ? cudaFuncSetAttribute(gemm_tf32x3_tc_persistent<BN>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes)
+                               : cudaFuncSetAttribute(gemm_tf32x3_tc_kernel<BN>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+    if (e != cudaSuccess) return e;
+    attr_mask[persistent] |= attr_bit;
+  }
+  if (persistent) {
+    const int cap = launch_ctx().max_ctas > 0 ? std::min(sms, launch_ctx().max_ctas) : sms;
+    const int grid = (int)std::min<long long>(ntiles, cap);
+    (void)launch_pdl(gemm_tf32x3_tc_persistent<BN>, dim3(grid), dim3(TC_THREADS), Lay::bytes, s, mx, my, mxl, myl, C,
+                     ldc, m, n, k, lower ? 1 : 0, (int)ntiles, dev_err);
+  } else {
+    dim3 grid((m + TC_BM - 1) / TC_BM, (n + BN - 1) / BN);
+    (void)launch_pdl(gemm_tf32x3_tc_kernel<BN>, grid, dim3(TC_THREADS), Lay::bytes, s, mx, my, mxl, myl, C, ldc, m, n,
+                     k, lower ? 1 : 0, dev_err);
+  }
+  return cudaGetLastError();
+}
+
 // tiles of a BN-wide grid that hold work (tiles wholly above the diagonal are skipped)
 long long active_tiles(int m, int n, bool lower, int bn) {
   const int gm = (m + TC_BM - 1) / TC_BM, gn = (n + bn - 1) / bn;
@@ -495,6 +626,25 @@ int pick_bn(int m, int n, bool lower, int occ) {
 }  // namespace
 
 bool tc_gemm_supported() { return get_encode() != nullptr; }
+
+cudaError_t launch_gemm_tf32x3_tc(double* C, int ldc, const float* H, const float* Lo, int ldh, int xr0, int yr0,
+                                  int k0, int m, int n, int k, bool lower, unsigned* dev_err, cudaStream_t s,
+                                  int occupancy) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if ((k0 % 4) != 0 || (ldh % 4) != 0 || (reinterpret_cast<uintptr_t>(H) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(Lo) & 15) != 0)
+    return cudaErrorInvalidValue;
+  // two accumulators per tile: at most 128 columns, so that a persistent CTA's two tiles
+  // (4 x 128 TMEM columns) fit the SM's 512
+  int bn = pick_bn(m, n, lower, occupancy);
+  if (bn > 128) bn = 128;
+  const int sms = device_sm_count();
+  const long long nt = active_tiles(m, n, lower, bn);
+  const bool persistent = bn == 128 && nt > sms;
+  if (bn == 128) return launch_split<128>(C, ldc, H, Lo, ldh, xr0, yr0, k0, m, n, k, lower, nt, sms, persistent, dev_err, s);
+  if (bn == 64) return launch_split<64>(C, ldc, H, Lo, ldh, xr0, yr0, k0, m, n, k, lower, nt, sms, false, dev_err, s);
+  return launch_split<32>(C, ldc, H, Lo, ldh, xr0, yr0, k0, m, n, k, lower, nt, sms, false, dev_err, s);
+}
 
 cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds, int xr0, int yr0, int k0, int m, int n,
                                int k, bool lower, double scale, unsigned* dev_err, cudaStream_t s, int occupancy) {

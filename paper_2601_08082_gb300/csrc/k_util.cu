@@ -356,6 +356,51 @@ cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, 
   return cudaGetLastError();
 }
 
+// ---- TF32 split of FP32 operands (error-corrected FP32 GEMM on tensor cores) ----
+// round to nearest even at 10 explicit mantissa bits, on the binary32 bit pattern
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t b = __float_as_uint(x);
+  if ((b & 0x7F800000u) != 0x7F800000u) {
+    b += 0x0FFFu + ((b >> 13) & 1u);
+    b &= 0xFFFFE000u;
+  }
+  return __uint_as_float(b);
+}
+// A: column-major FP64 block (rows r0 .. r0 + m, columns c0 .. c0 + nc); writes the row-major
+// hi = tf32(x) and lo = tf32(x - hi) of x = fp32(a) at [(r0 + i) ldh + c0 + j], through a
+// 32 x 32 shared-memory transpose (reads and writes both coalesced)
+__global__ void split_tf32_kernel(const double* __restrict__ A, int lda, int r0, int m, int c0, int nc,
+                                  float* __restrict__ H, float* __restrict__ Lo, int ldh) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float t[32][33];
+  const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  for (int jj = threadIdx.y; jj < 32; jj += 8) {
+    const int i = i0 + threadIdx.x, j = j0 + jj;
+    t[jj][threadIdx.x] = (i < m && j < nc) ? (float)A[(size_t)(c0 + j) * lda + r0 + i] : 0.f;
+  }
+  __syncthreads();
+  for (int ii = threadIdx.y; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + threadIdx.x;
+    if (i < m && j < nc) {
+      const float x = t[threadIdx.x][ii];
+      const float hi = round_tf32(x);
+      const size_t o = (size_t)(r0 + i) * ldh + c0 + j;
+      H[o] = hi;
+      Lo[o] = round_tf32(x - hi);                 // x - hi is exact in binary32
+    }
+  }
+}
+
+cudaError_t launch_split_tf32(const double* A, int lda, int r0, int m, int c0, int nc, float* H, float* Lo, int ldh,
+                              cudaStream_t s) {
+  if (m <= 0 || nc <= 0) return cudaSuccess;
+  const dim3 grid((nc + 31) / 32, (m + 31) / 32);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  (void)launch_pdl(split_tf32_kernel, grid, dim3(32, 8), 0, s, A, lda, r0, m, c0, nc, H, Lo, ldh);
+  return cudaGetLastError();
+}
+
 // ---- dynamic quantization: two-sided power-of-two diagonal scaling ----
 // e[i] = floor(ex / 2) for a_ii = m 2^ex, m in [0.5, 1) (0 when a_ii <= 0 or not finite)
 __global__ void diag_exponents_kernel(const double* __restrict__ A, int lda, int n, int* __restrict__ e) {

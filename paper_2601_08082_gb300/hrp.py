@@ -35,6 +35,7 @@ EXPORTED = [
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
     "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
     "hrp_last_inner_iterations", "hrp_autotune_orders", "hrp_set_batched_mode", "hrp_set_scaling",
+    "hrp_set_fp32_split",
 ]
 
 
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
     L.hrp_set_lookahead.argtypes = [vp, c_int]
     L.hrp_set_batched_mode.argtypes = [vp, c_int]
     L.hrp_set_scaling.argtypes = [vp, c_int]
+    L.hrp_set_fp32_split.argtypes = [vp, c_int]
     L.hrp_set_refinement.argtypes = [vp, c_int, c_int, c_double]
     L.hrp_last_inner_iterations.argtypes = [vp]
     L.hrp_last_inner_iterations.restype = ctypes.c_longlong
@@ -217,6 +219,10 @@ class Handle:
     def set_scaling(self, dynamic: bool) -> None:
         """hrp_set_scaling: two-sided power-of-two diagonal scaling before the recursion."""
         self._check(self._lib.hrp_set_scaling(self._h, 1 if dynamic else 0))
+
+    def set_fp32_split(self, on: bool) -> None:
+        """hrp_set_fp32_split: FP32-level GEMMs by the TF32 split on tensor cores."""
+        self._check(self._lib.hrp_set_fp32_split(self._h, 1 if on else 0))
 
     def set_batched_mode(self, persistent: bool) -> None:
         """hrp_set_batched_mode: one persistent launch (True) or one stream per system (False)."""
