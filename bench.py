@@ -441,13 +441,19 @@ def run_blas3(args, rank, world):
     C = torch.empty_like(C0)
     Bx = torch.empty_like(B0)
     stream = torch.cuda.current_stream()
-    out = {"syrk": {}, "trsm": {}}
+    hs = hrp.Handle(local)
+    hs.set_fp32_split(True)
+    out = {"syrk": {}, "trsm": {}, "syrk_tf32x3": {}}
     for spec in BLAS3_TREES:
         t = hrp.tree_parse(spec, leaf=128)
-        for op in ("syrk", "trsm"):
+        # syrk_tf32x3: the same SYRK with the FP32 levels on tensor cores (TF32 split)
+        for op in ("syrk", "trsm", "syrk_tf32x3"):
+            if op == "syrk_tf32x3" and "F32" not in spec:
+                continue
+            hh = hs if op == "syrk_tf32x3" else h
             times = []
             for rep in range(args.warmup + args.steps):
-                if op == "syrk":
+                if op != "trsm":
                     C.copy_(C0)
                 else:
                     Bx.copy_(B0)
@@ -456,22 +462,25 @@ def run_blas3(args, rank, world):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                if op == "syrk":
-                    h.syrk(t, A, C, stream=stream)
+                if op != "trsm":
+                    hh.syrk(t, A, C, stream=stream)
                 else:
-                    h.trsm(t, Lt, Bx, stream=stream)
+                    hh.trsm(t, Lt, Bx, stream=stream)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 if rep >= args.warmup:
                     times.append(e0.elapsed_time(e1))
-            assert h.check() == 0
+            assert hh.check() == 0
             ms = reps.max(statistics.median(times))
             out[op][spec] = {"ms": ms, "tflops": world * float(n) ** 3 / (ms * 1e-3) / 1e12}
-    for op in out:
+    for op in ("syrk", "trsm"):
         for spec, v in out[op].items():
             base = blas3_baseline(spec)
             if base != spec and base in out[op]:
                 v["speedup_vs_" + base] = out[op][base]["ms"] / v["ms"]
+    for spec, v in out["syrk_tf32x3"].items():
+        v["speedup_vs_simt_fp32"] = out["syrk"][spec]["ms"] / v["ms"]
+    hs.close()
     line = {"metric": "recursive SYRK / TRSM TFLOP/s (n^3 per s) by precision list", "unit": "TFLOP/s",
             "value": out["syrk"]["[F16,F16,F16,F16,F32]"]["tflops"], "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -544,6 +553,19 @@ def run_fp8posv(args, rank, world):
         out, t = timed(lambda: h.posv(tree, A, Bm, X, max_iter=30, tol=1e-12))
         if rep >= 1:
             tp.append(t)
+    # the same factorization with the FP32 diagonal regions on tensor cores (TF32 split)
+    hs = hrp.Handle(local)
+    hs.set_fp32_split(True)
+    ts = []
+    for rep in range(1 + max(1, args.steps // 2)):
+        Af.copy_(A)
+        _, t = timed(lambda: hs.potrf_async(tree, Af, d_info, stream=stream))
+        if rep >= 1:
+            ts.append(t)
+    split = {"ms": statistics.median(ts), "tflops": n ** 3 / 3.0 / (statistics.median(ts) * 1e-3) / 1e12,
+             "info": int(d_info.item()), "backward_error": hs.backward_error(A, Af)}
+    assert hs.check() == 0
+    hs.close()
     fp64 = None
     if args.fp64_steps > 0:
         # cut-offs tuned at n = 8192 (tuning at n = 32768 would take minutes: ~10 s per run)
@@ -566,6 +588,7 @@ def run_fp8posv(args, rank, world):
             "posv": {"ms": statistics.median(tp), "status": out["status"], "iters": out["iters"],
                      "resid": out["resid"], "used_fallback": out["used_fallback"],
                      "tflops_incl_refinement": flops / (statistics.median(tp) * 1e-3) / 1e12},
+            "fp32_tf32x3": split,
             "fp64_tree": fp64, "speedup_vs_fp64_tree": (fp64["ms"] / ms) if fp64 else None,
             "clocks": clk.summary()}
     reps.close()

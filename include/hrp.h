@@ -152,6 +152,16 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * F8 levels (E4M3 with one power-of-two scale 2^e per 128 x 128 tile of L).  mode 0 (default):
+ * the F8-level GEMMs are block-scaled E4M3 tensor-core products (kind::mxf8f6f4, one UE8M0
+ * scale 127 + e per row and 32 K elements, constant over each tile), at the FP8 rate.  mode 1:
+ * the same E4M3 values times 2^(e + 8), exact in FP16, multiplied by the FP16 GEMM and scaled
+ * back by 2^-16 (FP16 rate).  Both form the exact products of the quantized operands with
+ * FP32 accumulation.
+ */
+hrp_status hrp_set_f8_gemm(hrp_handle* h, int mode);
+
+/*
  * FP32 levels on tensor cores (the paper names tensor-core FP32 regions as future work,
  * Sec. 5).  on = 0 (default): the FP32-level GEMMs of hrp_potrf, hrp_potrf_async, hrp_posv and
  * hrp_syrk run on the SIMT FP32 pipe.  on = 1: products of at least 2e6 multiply-adds with

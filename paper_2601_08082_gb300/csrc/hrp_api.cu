@@ -47,6 +47,11 @@ struct hrp_handle_s {
   size_t w32_cap = 0;          // elements
   __half* shadow8 = nullptr;   // E4M3 values (times 2^G, exact) in FP16 storage
   size_t shadow8_cap = 0;
+  unsigned char* bytes8 = nullptr;   // E4M3 codes (row-major, ld lds) for the block-scaled MMAs
+  size_t bytes8_cap = 0;
+  // F8-level GEMMs: 0 = block-scaled E4M3 MMAs (FP8 rate, default), 1 = the E4M3 values in
+  // FP16 storage on kind::f16 (FP16 rate; same products)
+  int f8_gemm = 0;
   float* shadow32 = nullptr;   // FP32 copy of L (column-major, ld n) for the FP32-level GEMMs
   size_t shadow32_cap = 0;
   int* tile_exp = nullptr;     // power-of-two scale exponent of every 128 x 128 tile
@@ -233,7 +238,8 @@ struct Fact {
   __half* shadow;       // null if no F16 level
   int lds;
   float* w32;           // null if every level is F64
-  __half* shadow8;      // null if no F8 level
+  __half* shadow8;      // null if no F8 level, or if the F8 GEMMs read bytes8
+  unsigned char* bytes8 = nullptr;   // E4M3 codes for the block-scaled F8 GEMMs
   int* tile_exp;
   float* shadow32;      // null: FP32-level GEMMs round their operands from the master
   int ld32;
@@ -353,14 +359,14 @@ struct Fact {
   // off-diagonal tiles of its L11 in one launch once L11 is factored (quant8_lower)
   static constexpr int kG = 8;   // storage upshift: entries are 2^8 s e4m3(x/s)
   void quant8(int r0, int m, int c0, int nc, int p) {
-    if (!shadow8 || p != HRP_F8E4M3) return;
+    if ((!shadow8 && !bytes8) || p != HRP_F8E4M3) return;
     begin(CLS_OTHER, 0.0);
-    chk(launch_quant_e4m3(A, lda, r0, m, c0, nc, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
+    chk(launch_quant_e4m3(A, lda, r0, m, c0, nc, shadow8, bytes8, lds, tile_exp, n / 128, kG, h->d_err, s));
   }
   void quant8_lower(int off, int nb) {
-    if (!shadow8 || nb < 256) return;
+    if ((!shadow8 && !bytes8) || nb < 256) return;
     begin(CLS_OTHER, 0.0);
-    chk(launch_quant_e4m3_lower(A, lda, off, nb, shadow8, lds, tile_exp, n / 128, kG, h->d_err, s));
+    chk(launch_quant_e4m3_lower(A, lda, off, nb, shadow8, bytes8, lds, tile_exp, n / 128, kG, h->d_err, s));
   }
 
   // C = A[r0:r0+m, c0:c0+nd] -= X Y^T, X = A[r0:r0+m, k0:k0+k], Y = A[c0:c0+nd, k0:k0+k]
@@ -399,7 +405,10 @@ struct Fact {
           chk(launch_gemm_simt(C, lda, X, lda, Y, lda, m, nd, k, OpRound::F16, lower, s));
         break;
       case HRP_F8E4M3:
-        if (tc && shadow8 && (k0 % 8) == 0 && k >= 16)
+        if (tc && bytes8)
+          chk(launch_gemm_f8_tc(C, lda, bytes8, lds, r0, c0, k0, m, nd, k, lower, tile_exp, n / 128, h->d_err, s,
+                                t->tile_occupancy));
+        else if (tc && shadow8 && (k0 % 8) == 0 && k >= 16)
           chk(launch_gemm_f16_tc(C, lda, shadow8, lds, r0, c0, k0, m, nd, k, lower, ldexp(1.0, -2 * kG), h->d_err, s,
                                  t->tile_occupancy));
         else if (err == cudaSuccess)
@@ -565,7 +574,13 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
     if ((st = ensure(h, &h->shadow, &h->shadow_cap, (size_t)n * f.lds)) != HRP_OK) return st;
     f.shadow = h->shadow;
   }
-  if (has8 && n > 0) {
+  if (has8 && n > 0 && h->f8_gemm == 0 && f.tc) {
+    if ((st = ensure(h, &h->bytes8, &h->bytes8_cap, (size_t)n * f.lds)) != HRP_OK) return st;
+    const size_t nt = (size_t)(n / 128);
+    if ((st = ensure(h, &h->tile_exp, &h->tile_exp_cap, nt * nt)) != HRP_OK) return st;
+    f.bytes8 = h->bytes8;
+    f.tile_exp = h->tile_exp;
+  } else if (has8 && n > 0) {
     if ((st = ensure(h, &h->shadow8, &h->shadow8_cap, (size_t)n * f.lds)) != HRP_OK) return st;
     const size_t nt = (size_t)(n / 128);
     if ((st = ensure(h, &h->tile_exp, &h->tile_exp_cap, nt * nt)) != HRP_OK) return st;
@@ -735,6 +750,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->shadow);
   cudaFree(h->w32);
   cudaFree(h->shadow8);
+  cudaFree(h->bytes8);
   cudaFree(h->shadow32);
   cudaFree(h->tile_exp);
   cudaFree(h->fact);
@@ -1278,6 +1294,14 @@ hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner
 }
 
 long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
+
+hrp_status hrp_set_f8_gemm(hrp_handle* h, int mode) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (mode != 0 && mode != 1) return bad_arg(h, 2, "mode must be 0 (block-scaled E4M3) or 1 (FP16 storage)");
+  h->f8_gemm = mode;
+  return HRP_OK;
+}
 
 hrp_status hrp_set_fp32_split(hrp_handle* h, int on) {
   if (!h) return HRP_ERR_INVALID_ARG;

@@ -172,19 +172,27 @@ cudaError_t launch_axpy_matrix(double* X, int ldx, const double* D, int ldd, int
 cudaError_t launch_backward_error(const double* A, int lda, const double* L, int ldl, int n,
                                   double* out, cudaStream_t s);
 // E4M3 quantization of the finished panel A[r0:r0+m, c0:c0+128] (r0, c0 multiples of 128)
-// into the FP8 shadow S8 (FP16 storage of 2^G s e4m3(x/s)), one power-of-two scale
+// into the FP8 shadows (each optional): S8, FP16 storage of 2^G s e4m3(x/s), and B8, the E4M3
+// codes of e4m3(x/s) (bytes), both row-major with row stride lds; one power-of-two scale
 // exponent per 128 x 128 tile into tile_exp[(row tile) * ntile_ld + (col tile)].
-cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
-                              int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s);
+cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, unsigned char* B8,
+                              int lds, int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s);
 // every 128 x 128 tile strictly below the diagonal tiles of A[off:off+nb, off:off+nb]
-cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, int lds, int* tile_exp,
-                                    int ntile_ld, int G, unsigned* err, cudaStream_t s);
+cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, unsigned char* B8, int lds,
+                                    int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s);
 // Operand copies for the standalone SYRK / TRSM: the m x k block X (column-major, ldx) into
 // S16 row-major (S16[r * lds + c], round to nearest even; an entry beyond kF16Max sets
 // DEV_ERR_RANGE16 in err) and into S32 column-major (S32[c * ld32 + r]).
 cudaError_t launch_cast_f16_rows(const double* X, int ldx, int m, int k, __half* S16, int lds, unsigned* err,
                                  cudaStream_t s);
 cudaError_t launch_cast_f32(const double* X, int ldx, int m, int k, float* S32, int ld32, cudaStream_t s);
+// C[.., ..] -= X Y^T for an F8 level by block-scaled E4M3 MMAs (kind::mxf8f6f4, UE8M0 scale
+// 2^e per 128 x 128 tile): X rows xr0.., Y rows yr0.., K columns k0.. of the row-major E4M3
+// codes S (lds bytes per row), tile_exp as written by the quantization (ntile_ld tiles per
+// row of tiles).  xr0, yr0, k0 multiples of 128; lds a multiple of 16.
+cudaError_t launch_gemm_f8_tc(double* C, int ldc, const uint8_t* S, int lds, int xr0, int yr0, int k0, int m, int n,
+                              int k, bool lower, const int* tile_exp, int ntile_ld, unsigned* dev_err, cudaStream_t s,
+                              int occupancy = 0);
 // TF32 split of an FP32-level block: hi = tf32(fp32(a)), lo = tf32(fp32(a) - hi), read from the
 // column-major FP64 block A[r0.., c0..] (m x nc) and written row-major at [(r0 + i) ldh + c0 + j].
 cudaError_t launch_split_tf32(const double* A, int lda, int r0, int m, int c0, int nc, float* H, float* Lo, int ldh,

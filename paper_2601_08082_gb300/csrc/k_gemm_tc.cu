@@ -6,7 +6,7 @@
 // `lower` it is the leaf SYRK of Alg. 3 (entries above the diagonal are skipped, and
 // tiles entirely above it are never computed).
 //
-// The same kernels, with SPLIT, run the FP32 levels on tensor cores by the error-corrected
+// The same kernels run the FP32 levels on tensor cores by the error-corrected
 // TF32 split (Ootomo and Yokota, 2022): each FP32 operand is stored as hi = tf32(x) and
 // lo = tf32(x - hi) (row-major FP32 arrays written once per finished block of L); per K
 // slice the MMA warp issues hi hi^T into one TMEM accumulator and hi lo^T + lo hi^T into a
@@ -31,8 +31,22 @@ constexpr int TC_BM = 128;
 constexpr int TC_ROW_BYTES = 128;  // one 128-byte swizzle row of K: 64 fp16 or 32 fp32 (tf32)
 constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 192;
-template <bool SPLIT> struct TcElem { static constexpr int BK = 64; };   // K elements per stage
-template <> struct TcElem<true> { static constexpr int BK = 32; };
+// operand kinds: FP16 (kind::f16), TF32 split (kind::tf32, two operand tiles and two
+// accumulators), E4M3 with one power-of-two scale per 128 x 128 tile (kind::mxf8f6f4 with UE8M0
+// block scales)
+constexpr int KIND_F16 = 0, KIND_TF32X3 = 1, KIND_F8 = 2;
+template <int KIND> struct TcElem { static constexpr int BK = 64; };      // K elements per stage
+template <> struct TcElem<KIND_TF32X3> { static constexpr int BK = 32; };
+template <> struct TcElem<KIND_F8> { static constexpr int BK = 128; };
+// E4M3 scales: tile_exp[I * ntile_ld + J] = exponent of the 128 x 128 tile (I, J) of L; the
+// operands' first row tiles (xt0, yt0) and first K tile (kt0) on that grid
+struct F8Scales {
+  const int* tile_exp;
+  int ntile_ld, xt0, yt0, kt0;
+};
+__host__ __device__ constexpr uint32_t tmem_cols_pow2(uint32_t c) {
+  return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -109,17 +123,55 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+// Block-scaled kind::mxf8f6f4: A = B = E4M3 (0) at bits 7-9 and 10-12, scale factors UE8M0
+// (bit 23), scale-factor IDs 0 (bits 4-5, 29-30), N >> 3 at 17-22, M >> 4 at 24-28; D = F32,
+// K = 32 per instruction with one scale per row and 32 K elements (scale_vec::1X).
+__host__ __device__ constexpr uint32_t idesc_f8bs(int M, int N) {
+  return ((uint32_t)(N >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f8bs(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate));
+}
+// Shared-memory descriptor of a scale-factor source for tcgen05.cp .32x128b: 32 rows of 16
+// bytes, 8-row core matrices 128 bytes apart, no swizzle.  The sources hold one byte value
+// throughout (1 KB each), so every row and column the copy reads carries the tile's scale.
+__device__ __forceinline__ uint64_t sf_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(128 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// 32 lanes x 128 bits from shared memory into the TMEM columns at taddr, replicated into the
+// four lane quarters (tcgen05 pipeline: ordered before the MMAs this thread issues next)
+__device__ __forceinline__ void sf_copy(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
 // The MMAs of one 128-byte K slice (4 instructions of 32 bytes each) into the accumulator
-// set at `acc` (SPLIT: hi hi^T at acc, hi lo^T + lo hi^T at acc + BN).
-template <int BN, bool SPLIT>
+// set at `acc` (TF32 split: hi hi^T at acc, hi lo^T + lo hi^T at acc + BN; E4M3: the slice's
+// scale factors are first copied from sf (A at 0, B at 1 KB) into TMEM columns sf_t .. + 7).
+template <int BN, int KIND>
 __device__ __forceinline__ void mma_slice(uint32_t acc, const uint8_t* a, const uint8_t* b, size_t a_tile,
-                                          size_t b_tile, bool first) {
+                                          size_t b_tile, bool first, const uint8_t* sf = nullptr,
+                                          uint32_t sf_t = 0) {
   const uint64_t ad = sw128_desc(a), bd = sw128_desc(b);
-  if constexpr (!SPLIT) {
+  if constexpr (KIND == KIND_F16) {
     constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)                 // K = 16 per instruction: +32 bytes
       mma_f16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (!first || kk > 0) ? 1u : 0u);
+  } else if constexpr (KIND == KIND_F8) {
+    constexpr uint32_t idesc = idesc_f8bs(TC_BM, BN);
+    sf_copy(sf_t, sf_desc(sf));
+    sf_copy(sf_t + 4, sf_desc(sf + 1024));
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)                 // K = 32 per instruction: +32 bytes
+      mma_f8bs(acc, ad + 2 * kk, bd + 2 * kk, idesc, sf_t, sf_t + 4, (!first || kk > 0) ? 1u : 0u);
   } else {
     constexpr uint32_t idesc = idesc_tf32(TC_BM, BN);
     const uint64_t adl = sw128_desc(a + a_tile), bdl = sw128_desc(b + b_tile);
@@ -152,27 +204,78 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// SPLIT: two operand tiles (hi, lo) per matrix and stage, and two accumulators per tile.
-template <int BN, bool SPLIT = false>
+// TF32 split: two operand tiles (hi, lo) per matrix and stage, and two accumulators per tile.
+// E4M3: per stage two 1 KB scale-factor sources in shared memory and 8 TMEM columns (A: 4,
+// B: 4) after the accumulators.
+template <int BN, int KIND = KIND_F16>
 struct TcLayout {
-  static constexpr int ops = SPLIT ? 2 : 1;
-  static constexpr int stages = SPLIT && BN >= 128 ? 3 : TC_STAGES;
+  static_assert(KIND != KIND_F8 || BN <= 128, "an E4M3 column tile lies within one 128-row scale tile");
+  static constexpr int ops = KIND == KIND_TF32X3 ? 2 : 1;
+  static constexpr int stages = KIND == KIND_TF32X3 && BN >= 128 ? 3 : TC_STAGES;
   static constexpr size_t a_tile = (size_t)TC_BM * TC_ROW_BYTES;
   static constexpr size_t b_tile = (size_t)BN * TC_ROW_BYTES;
   static constexpr size_t a_stage = ops * a_tile;
   static constexpr size_t b_stage = ops * b_tile;
-  static constexpr uint32_t acc_cols = SPLIT ? 2 * BN : BN;   // TMEM columns of one tile
+  static constexpr size_t sf_stage = KIND == KIND_F8 ? 2048 : 0;
+  static constexpr uint32_t acc_cols = KIND == KIND_TF32X3 ? 2 * BN : BN;   // TMEM columns of one tile
+  static constexpr uint32_t sf_cols = KIND == KIND_F8 ? 8 * stages : 0;
   static constexpr size_t bars = 1024;  // barriers + tmem slot, padded
-  static constexpr size_t bytes = 1024 /*alignment slack*/ + stages * (a_stage + b_stage) + bars;
+  static constexpr size_t bytes = 1024 /*alignment slack*/ + stages * (a_stage + b_stage + sf_stage) + bars;
 };
 
-template <int BN, bool SPLIT>
+// E4M3 tile exponents of the A and B tiles at K tiles kb0 .. kb0 + 31: lane l loads those of
+// K tile kb0 + l (one load latency per 32 stages; each stage takes its pair by a shuffle)
+__device__ __forceinline__ void f8_exponents(const F8Scales& f8, int at, int bt, int kb0, int nk, int& ea, int& eb) {
+  const int kt = kb0 + (threadIdx.x & 31);
+  ea = kt < nk ? f8.tile_exp[(size_t)(f8.xt0 + at) * f8.ntile_ld + f8.kt0 + kt] : 0;
+  eb = kt < nk ? f8.tile_exp[(size_t)(f8.yt0 + bt) * f8.ntile_ld + f8.kt0 + kt] : 0;
+}
+// E4M3 producer step (warp 0, all lanes): fill the stage's two scale-factor sources with the
+// UE8M0 codes 127 + e of the A and B tiles at K tile kb (exponents from f8_exponents, held by
+// lane kb % 32), then (lane 0) the operand loads.  Returns false (all lanes) when the wait
+// for a free stage expired.
+template <int BN>
+__device__ __forceinline__ bool f8_produce(int ea_l, int eb_l, int kb, uint8_t* sf, uint64_t* empty_s, uint32_t ph,
+                                           uint64_t* full_s, uint8_t* a, uint8_t* b, const CUtensorMap* tmX,
+                                           const CUtensorMap* tmY, int xk, int xm, int yn, unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  int ea = __shfl_sync(0xffffffffu, ea_l, kb & 31) + 127;
+  int eb = __shfl_sync(0xffffffffu, eb_l, kb & 31) + 127;
+  bool ok = true;
+  if (lane == 0) ok = mbar_wait(empty_s, ph ^ 1);
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  if (!ok) return false;
+  if (ea < 0 || ea > 254 || eb < 0 || eb > 254) {
+    if (lane == 0) atomicOr(err, DEV_ERR_RANGE);
+    ea = min(max(ea, 0), 254);
+    eb = min(max(eb, 0), 254);
+  }
+  const uint32_t wa = 0x01010101u * (uint32_t)ea, wb = 0x01010101u * (uint32_t)eb;
+  uint4* pa = reinterpret_cast<uint4*>(sf);
+  uint4* pb = reinterpret_cast<uint4*>(sf + 1024);
+  pa[lane] = make_uint4(wa, wa, wa, wa);
+  pa[lane + 32] = make_uint4(wa, wa, wa, wa);
+  pb[lane] = make_uint4(wb, wb, wb, wb);
+  pb[lane + 32] = make_uint4(wb, wb, wb, wb);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    mbar_arrive_expect_tx(full_s, (uint32_t)(TcLayout<BN, KIND_F8>::a_stage + TcLayout<BN, KIND_F8>::b_stage));
+    tma_load_2d(a, tmX, xk, xm, full_s);
+    tma_load_2d(b, tmY, xk, yn, full_s);
+  }
+  return true;
+}
+
+template <int BN, int KIND>
 __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXl,
                                              const CUtensorMap* tmYl, double* __restrict__ C, int ldc, int m, int n,
-                                             int k, int lower, double scale, unsigned* __restrict__ err) {
-  using Lay = TcLayout<BN, SPLIT>;
+                                             int k, int lower, double scale, unsigned* __restrict__ err,
+                                             F8Scales f8 = F8Scales{}) {
+  using Lay = TcLayout<BN, KIND>;
   constexpr int STAGES = Lay::stages;
-  constexpr int BK = TcElem<SPLIT>::BK;
+  constexpr int BK = TcElem<KIND>::BK;
+  constexpr uint32_t TMEM_COLS = tmem_cols_pow2(Lay::acc_cols + Lay::sf_cols);
   extern __shared__ unsigned char smem_raw[];
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
   if (lower && m0 + TC_BM - 1 < n0) return;          // tile strictly above the diagonal
@@ -180,7 +283,8 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + STAGES * Lay::a_stage;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Lay::b_stage);
+  uint8_t* sSF = sB + STAGES * Lay::b_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sSF + STAGES * Lay::sf_stage);
   uint64_t* empty = full + STAGES;
   uint64_t* accum = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
@@ -199,7 +303,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(Lay::acc_cols) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -208,7 +312,22 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
+    if constexpr (KIND == KIND_F8) {
+      if (lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmX)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmY)) : "memory");
+      }
+      int ea = 0, eb = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if ((kb & 31) == 0) f8_exponents(f8, blockIdx.x, n0 / TC_BM, kb, nk, ea, eb);
+        if (!f8_produce<BN>(ea, eb, kb, sSF + s * Lay::sf_stage, &empty[s], (kb / STAGES) & 1, &full[s],
+                            sA + s * Lay::a_stage, sB + s * Lay::b_stage, tmX, tmY, kb * BK, m0, n0, err)) {
+          if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+          break;
+        }
+      }
+    } else if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmX)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmY)) : "memory");
       for (int kb = 0; kb < nk; ++kb) {
@@ -218,7 +337,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
         mbar_arrive_expect_tx(&full[s], (uint32_t)(Lay::a_stage + Lay::b_stage));
         tma_load_2d(sA + s * Lay::a_stage, tmX, kb * BK, m0, &full[s]);
         tma_load_2d(sB + s * Lay::b_stage, tmY, kb * BK, n0, &full[s]);
-        if constexpr (SPLIT) {
+        if constexpr (KIND == KIND_TF32X3) {
           tma_load_2d(sA + s * Lay::a_stage + Lay::a_tile, tmXl, kb * BK, m0, &full[s]);
           tma_load_2d(sB + s * Lay::b_stage + Lay::b_tile, tmYl, kb * BK, n0, &full[s]);
         }
@@ -232,7 +351,8 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
         const uint32_t ph = (kb / STAGES) & 1;
         if (!mbar_wait(&full[s], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
         tc_fence_after();
-        mma_slice<BN, SPLIT>(tmem, sA + s * Lay::a_stage, sB + s * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0);
+        mma_slice<BN, KIND>(tmem, sA + s * Lay::a_stage, sB + s * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0,
+                            sSF + s * Lay::sf_stage, tmem + Lay::acc_cols + (uint32_t)(8 * s));
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(accum);
@@ -250,8 +370,8 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
         uint32_t r[32];
         tmem_ld32(taddr, r);
-        uint32_t r2[SPLIT ? 32 : 1];
-        if constexpr (SPLIT) tmem_ld32(taddr + BN, r2);
+        uint32_t r2[KIND == KIND_TF32X3 ? 32 : 1];
+        if constexpr (KIND == KIND_TF32X3) tmem_ld32(taddr + BN, r2);
         if (row < m) {
           // all 32 loads first (independent, in flight together), then the 32 stores
           double* base_p = C + (size_t)(n0 + c0) * ldc + row;
@@ -265,7 +385,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
             double v = (double)__uint_as_float(r[j]);
-            if constexpr (SPLIT) v += (double)__uint_as_float(r2[j]);
+            if constexpr (KIND == KIND_TF32X3) v += (double)__uint_as_float(r2[j]);
             if (col < n && (!lower || row >= col)) __stcs(base_p + (size_t)j * ldc, cv[j] - scale * v);
           }
         }
@@ -276,7 +396,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* tmX, const CUten
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::acc_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -287,7 +407,7 @@ gemm_f16_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constan
                    unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
-  gemm_tc_tile<BN, false>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, err);
+  gemm_tc_tile<BN, KIND_F16>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, err);
 }
 
 template <int BN>
@@ -297,7 +417,17 @@ gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_cons
                       double* __restrict__ C, int ldc, int m, int n, int k, int lower, unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
-  gemm_tc_tile<BN, true>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, err);
+  gemm_tc_tile<BN, KIND_TF32X3>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, err);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, BN <= 64 ? 2 : 1)
+gemm_f8_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                  double* __restrict__ C, int ldc, int m, int n, int k, int lower, F8Scales f8,
+                  unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tile<BN, KIND_F8>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, 1.0, err, f8);
 }
 
 // Persistent variant for products with more tiles than SMs: each CTA walks the active
@@ -324,19 +454,22 @@ __device__ __forceinline__ bool tile_of(int idx, int gm, int gn, bool lower, int
   return false;
 }
 
-template <int BN, bool SPLIT>
+template <int BN, int KIND>
 __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUtensorMap* tmY, const CUtensorMap* tmXl,
                                               const CUtensorMap* tmYl, double* __restrict__ C, int ldc, int m, int n,
-                                              int k, int lower, double scale, int ntiles, unsigned* __restrict__ err) {
-  using Lay = TcLayout<BN, SPLIT>;
+                                              int k, int lower, double scale, int ntiles, unsigned* __restrict__ err,
+                                              F8Scales f8 = F8Scales{}) {
+  using Lay = TcLayout<BN, KIND>;
   constexpr int STAGES = Lay::stages;
-  constexpr int BK = TcElem<SPLIT>::BK;
+  constexpr int BK = TcElem<KIND>::BK;
   constexpr uint32_t ACC = Lay::acc_cols;
+  constexpr uint32_t TMEM_COLS = tmem_cols_pow2(2 * ACC + Lay::sf_cols);
   extern __shared__ unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + STAGES * Lay::a_stage;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Lay::b_stage);
+  uint8_t* sSF = sB + STAGES * Lay::b_stage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sSF + STAGES * Lay::sf_stage);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;             // [2]
   uint64_t* acc_empty = acc_full + 2;              // [2]
@@ -362,7 +495,7 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(2 * ACC) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -375,21 +508,45 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmX)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmY)) : "memory");
+    }
+    if (KIND == KIND_F8 || lane == 0) {
       long long kb_all = 0;
-      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // E4M3: all 32 lanes run this loop, so the abort decision is lane 0's, broadcast
+        int stop = *abort_flag;
+        if constexpr (KIND == KIND_F8) stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop) break;
         int mt, nt;
         if (!tile_of<BN>(t, gm, gn, lower != 0, mt, nt)) break;
+        bool ok = true;
+        int ea = 0, eb = 0;
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
           const int q = (int)(kb_all % STAGES);
           const uint32_t ph = (uint32_t)((kb_all / STAGES) & 1);
-          if (!mbar_wait(&empty[q], ph ^ 1)) { atomicOr(err, DEV_ERR_TIMEOUT); *abort_flag = 1; break; }
-          mbar_arrive_expect_tx(&full[q], (uint32_t)(Lay::a_stage + Lay::b_stage));
-          tma_load_2d(sA + q * Lay::a_stage, tmX, kb * BK, mt * TC_BM, &full[q]);
-          tma_load_2d(sB + q * Lay::b_stage, tmY, kb * BK, nt * BN, &full[q]);
-          if constexpr (SPLIT) {
-            tma_load_2d(sA + q * Lay::a_stage + Lay::a_tile, tmXl, kb * BK, mt * TC_BM, &full[q]);
-            tma_load_2d(sB + q * Lay::b_stage + Lay::b_tile, tmYl, kb * BK, nt * BN, &full[q]);
+          if constexpr (KIND == KIND_F8) {
+            if ((kb & 31) == 0) f8_exponents(f8, mt, (nt * BN) / TC_BM, kb, nk, ea, eb);
+            if (!f8_produce<BN>(ea, eb, kb, sSF + q * Lay::sf_stage, &empty[q], ph, &full[q], sA + q * Lay::a_stage,
+                                sB + q * Lay::b_stage, tmX, tmY, kb * BK, mt * TC_BM, nt * BN, err)) {
+              ok = false;
+              break;
+            }
+          } else {
+            if (!mbar_wait(&empty[q], ph ^ 1)) { ok = false; break; }
+            mbar_arrive_expect_tx(&full[q], (uint32_t)(Lay::a_stage + Lay::b_stage));
+            tma_load_2d(sA + q * Lay::a_stage, tmX, kb * BK, mt * TC_BM, &full[q]);
+            tma_load_2d(sB + q * Lay::b_stage, tmY, kb * BK, nt * BN, &full[q]);
+            if constexpr (KIND == KIND_TF32X3) {
+              tma_load_2d(sA + q * Lay::a_stage + Lay::a_tile, tmXl, kb * BK, mt * TC_BM, &full[q]);
+              tma_load_2d(sB + q * Lay::b_stage + Lay::b_tile, tmYl, kb * BK, nt * BN, &full[q]);
+            }
           }
+        }
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            *abort_flag = 1;
+          }
+          break;
         }
       }
     }
@@ -412,7 +569,8 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
           const uint32_t ph = (uint32_t)((kb_all / STAGES) & 1);
           if (!mbar_wait(&full[q], ph)) { atomicOr(err, DEV_ERR_TIMEOUT); ok = false; break; }
           tc_fence_after();
-          mma_slice<BN, SPLIT>(acc, sA + q * Lay::a_stage, sB + q * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0);
+          mma_slice<BN, KIND>(acc, sA + q * Lay::a_stage, sB + q * Lay::b_stage, Lay::a_tile, Lay::b_tile, kb == 0,
+                              sSF + q * Lay::sf_stage, tmem + 2 * ACC + (uint32_t)(8 * q));
           mma_commit(&empty[q]);
         }
         if (!ok) { *abort_flag = 1; break; }
@@ -437,8 +595,8 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
         const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)b * ACC + (uint32_t)c0;
         uint32_t r[32];
         tmem_ld32(taddr, r);
-        uint32_t r2[SPLIT ? 32 : 1];
-        if constexpr (SPLIT) tmem_ld32(taddr + BN, r2);
+        uint32_t r2[KIND == KIND_TF32X3 ? 32 : 1];
+        if constexpr (KIND == KIND_TF32X3) tmem_ld32(taddr + BN, r2);
         if (row < m) {
           double* base_p = C + (size_t)(n0 + c0) * ldc + row;
           double cv[32];
@@ -451,7 +609,7 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
             double v = (double)__uint_as_float(r[j]);
-            if constexpr (SPLIT) v += (double)__uint_as_float(r2[j]);
+            if constexpr (KIND == KIND_TF32X3) v += (double)__uint_as_float(r2[j]);
             if (col < n && (!lower || row >= col)) __stcs(base_p + (size_t)j * ldc, cv[j] - scale * v);
           }
         }
@@ -466,7 +624,7 @@ __device__ __forceinline__ void gemm_tc_tiles(const CUtensorMap* tmX, const CUte
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -477,7 +635,7 @@ gemm_f16_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_con
                        int ntiles, unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
-  gemm_tc_tiles<BN, false>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, ntiles, err);
+  gemm_tc_tiles<BN, KIND_F16>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, scale, ntiles, err);
 }
 
 template <int BN>
@@ -488,7 +646,17 @@ gemm_tf32x3_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_
                           unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
-  gemm_tc_tiles<BN, true>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, ntiles, err);
+  gemm_tc_tiles<BN, KIND_TF32X3>(&tmX, &tmY, &tmXl, &tmYl, C, ldc, m, n, k, lower, 1.0, ntiles, err);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gemm_f8_tc_persistent(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                      double* __restrict__ C, int ldc, int m, int n, int k, int lower, int ntiles, F8Scales f8,
+                      unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  gemm_tc_tiles<BN, KIND_F8>(&tmX, &tmY, nullptr, nullptr, C, ldc, m, n, k, lower, 1.0, ntiles, err, f8);
 }
 
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -509,18 +677,20 @@ PFN_encodeTiled_t get_encode() {
   return fn;
 }
 
-// 2-D map over a rows x cols block of a row-major fp16 or fp32 matrix (leading dimension ld
-// elements), box = box_rows x 128 bytes of K, 128B swizzle, zero fill outside the block.
+// 2-D map over a rows x cols block of a row-major e4m3 (bytes), fp16 or fp32 matrix (leading
+// dimension ld elements), box = box_rows x 128 bytes of K, 128B swizzle, zero fill outside.
 template <typename T>
 bool make_map(CUtensorMap* map, const T* base, int rows, int cols, int ld, int box_rows) {
-  static_assert(sizeof(T) == 2 || sizeof(T) == 4, "fp16 or fp32 operands");
+  static_assert(sizeof(T) == 1 || sizeof(T) == 2 || sizeof(T) == 4, "e4m3, fp16 or fp32 operands");
   PFN_encodeTiled_t enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
   cuuint32_t box[2] = {(cuuint32_t)(TC_ROW_BYTES / sizeof(T)), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  const CUtensorMapDataType dt = sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = sizeof(T) == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : sizeof(T) == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = enc(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -602,6 +772,39 @@ cudaError_t launch_split(double* C, int ldc, const float* H, const float* Lo, in
   return cudaGetLastError();
 }
 
+// E4M3 codes (row-major bytes, ld lds) with per-tile exponents: block-scaled FP8 MMAs
+template <int BN>
+cudaError_t launch_f8(double* C, int ldc, const uint8_t* S, int lds, int xr0, int yr0, int k0, int m, int n, int k,
+                      bool lower, const int* tile_exp, int ntile_ld, long long ntiles, int sms, bool persistent,
+                      unsigned* dev_err, cudaStream_t s) {
+  CUtensorMap mx, my;
+  if (!make_map(&mx, S + (size_t)xr0 * lds + k0, m, k, lds, TC_BM) || !make_map(&my, S + (size_t)yr0 * lds + k0, n, k, lds, BN))
+    return cudaErrorInvalidValue;
+  const F8Scales f8{tile_exp, ntile_ld, xr0 / TC_BM, yr0 / TC_BM, k0 / TC_BM};
+  using Lay = TcLayout<BN, KIND_F8>;
+  static unsigned long long attr_mask[2] = {0, 0};
+  const unsigned long long attr_bit = dev_bit();
+  if (!(attr_mask[persistent] & attr_bit)) {
+    cudaError_t e = persistent ? cudaFuncSetAttribute(gemm_f8_tc_persistent<BN>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes)
+                               : cudaFuncSetAttribute(gemm_f8_tc_kernel<BN>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+    if (e != cudaSuccess) return e;
+    attr_mask[persistent] |= attr_bit;
+  }
+  if (persistent) {
+    const int cap = launch_ctx().max_ctas > 0 ? std::min(sms, launch_ctx().max_ctas) : sms;
+    const int grid = (int)std::min<long long>(ntiles, cap);
+    (void)launch_pdl(gemm_f8_tc_persistent<BN>, dim3(grid), dim3(TC_THREADS), Lay::bytes, s, mx, my, C, ldc, m, n, k,
+                     lower ? 1 : 0, (int)ntiles, f8, dev_err);
+  } else {
+    dim3 grid((m + TC_BM - 1) / TC_BM, (n + BN - 1) / BN);
+    (void)launch_pdl(gemm_f8_tc_kernel<BN>, grid, dim3(TC_THREADS), Lay::bytes, s, mx, my, C, ldc, m, n, k,
+                     lower ? 1 : 0, f8, dev_err);
+  }
+  return cudaGetLastError();
+}
+
 // tiles of a BN-wide grid that hold work (tiles wholly above the diagonal are skipped)
 long long active_tiles(int m, int n, bool lower, int bn) {
   const int gm = (m + TC_BM - 1) / TC_BM, gn = (n + bn - 1) / bn;
@@ -626,6 +829,25 @@ int pick_bn(int m, int n, bool lower, int occ) {
 }  // namespace
 
 bool tc_gemm_supported() { return get_encode() != nullptr; }
+
+cudaError_t launch_gemm_f8_tc(double* C, int ldc, const uint8_t* S, int lds, int xr0, int yr0, int k0, int m, int n,
+                              int k, bool lower, const int* tile_exp, int ntile_ld, unsigned* dev_err, cudaStream_t s,
+                              int occupancy) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if ((xr0 % TC_BM) || (yr0 % TC_BM) || (k0 % TC_BM) || (lds % 16) || (reinterpret_cast<uintptr_t>(S) & 15))
+    return cudaErrorInvalidValue;
+  // a column tile must lie within one 128-row scale tile: at most 128 wide
+  int bn = pick_bn(m, n, lower, occupancy);
+  if (bn > 128) bn = 128;
+  const int sms = device_sm_count();
+  const long long nt = active_tiles(m, n, lower, bn);
+  const bool persistent = bn == 128 && nt > sms;
+  if (bn == 128)
+    return launch_f8<128>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, tile_exp, ntile_ld, nt, sms, persistent, dev_err, s);
+  if (bn == 64)
+    return launch_f8<64>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, tile_exp, ntile_ld, nt, sms, false, dev_err, s);
+  return launch_f8<32>(C, ldc, S, lds, xr0, yr0, k0, m, n, k, lower, tile_exp, ntile_ld, nt, sms, false, dev_err, s);
+}
 
 cudaError_t launch_gemm_tf32x3_tc(double* C, int ldc, const float* H, const float* Lo, int ldh, int xr0, int yr0,
                                   int k0, int m, int n, int k, bool lower, unsigned* dev_err, cudaStream_t s,

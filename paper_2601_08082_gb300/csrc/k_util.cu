@@ -558,6 +558,40 @@ __device__ __forceinline__ unsigned short quant_e4m3_h(double x, int sig, int G)
   return (unsigned short)(h | sign);
 }
 
+// E4M3FN code (sign, 4 exponent bits with bias 7, 3 mantissa bits; 0x7F = NaN) of
+// e4m3(x 2^-sig), rounded exactly as quant_e4m3_h rounds (nearest even, saturating at 448).
+__device__ __forceinline__ unsigned char quant_e4m3_code(double x, int sig) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = (hi >> 31) << 7;
+  const int E = (int)((hi >> 20) & 0x7ff);
+  if (E == 0) return (unsigned char)sign;
+  if (E == 0x7ff) {
+    if ((hi & 0xfffffu) | lo) return (unsigned char)(sign | 0x7fu);
+    return (unsigned char)(sign | 0x7eu);                    // infinity saturates to 448
+  }
+  const unsigned S = (hi & 0xfffffu) | 0x100000u;
+  const int ey = E - 1023 - sig;
+  int qe = ey >= -6 ? ey - 3 : -9;
+  const int sh = 52 - (ey - qe);
+  if (sh > 54) return (unsigned char)sign;
+  const int s32 = sh - 32;
+  unsigned r = S >> s32;
+  const unsigned halfbit = (S >> (s32 - 1)) & 1u;
+  const unsigned sticky = (S & ((1u << (s32 - 1)) - 1u)) | lo;
+  r += halfbit & ((sticky != 0u) | (r & 1u));
+  if (r == 0) return (unsigned char)sign;
+  if (ey > 8 || (ey == 8 && r > 14u)) {
+    r = 14u;
+    qe = 5;
+  }
+  // value = r 2^qe, 1 <= r <= 16: subnormal code r (qe = -9, r < 8), else 1.m 2^(pw + qe)
+  if (qe == -9 && r < 8u) return (unsigned char)(sign | r);
+  const int pw = 31 - __clz((int)r);
+  const unsigned mant = (r - (1u << pw)) << (3 - pw);           // pw <= 3, or r = 16 (mant 0)
+  return (unsigned char)(sign | ((unsigned)(pw + qe + 7) << 3) | (pw == 4 ? 0u : mant));
+}
+
 constexpr int kQT = 128;     // tile edge (rows and columns)
 constexpr int kQLD = 129;    // row stride (doubles) of the staged tile
 constexpr int kQThreads = 1024;
@@ -567,8 +601,9 @@ constexpr int kQThreads = 1024;
 // shared memory, its amax gives the power-of-two scale s = 2^sig = 2^ceil(log2(amax / 448)),
 // and the FP16 shadow is written row by row (coalesced along columns).
 __device__ __forceinline__ void quant_tile(const double* __restrict__ A, int ld, int R0, int rows, int c0,
-                                           __half* __restrict__ S8, int lds, int* __restrict__ tile_exp,
-                                           int ntile_ld, int G, unsigned* __restrict__ err, double* tileq) {
+                                           __half* __restrict__ S8, unsigned char* __restrict__ B8, int lds,
+                                           int* __restrict__ tile_exp, int ntile_ld, int G,
+                                           unsigned* __restrict__ err, double* tileq) {
   __shared__ unsigned long long red[kQThreads / 32];
   __shared__ int s_sig;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -607,35 +642,55 @@ __device__ __forceinline__ void quant_tile(const double* __restrict__ A, int ld,
       sig = (f == 0.5) ? ex - 1 : ex;              // ceil(log2(amax / 448))
     }
     tile_exp[(size_t)(R0 / kQT) * ntile_ld + c0 / kQT] = sig;
-    const bool fits = !(amax > 0.0) || (ldexp(amax, G) <= 65504.0 && sig - 9 + G >= -24);
-    if (!fits) atomicOr(err, DEV_ERR_RANGE);
+    // FP16 storage: 2^G amax and the smallest E4M3 step 2^(sig - 9 + G) inside FP16's range;
+    // E4M3 codes: the scale 2^sig a UE8M0 code (127 + sig in 0 .. 254)
+    const bool fits16 = !(amax > 0.0) || (ldexp(amax, G) <= 65504.0 && sig - 9 + G >= -24);
+    const bool fits8 = sig >= -127 && sig <= 127;
+    if ((S8 != nullptr && !fits16) || (B8 != nullptr && !fits8)) atomicOr(err, DEV_ERR_RANGE);
     s_sig = sig;
   }
   __syncthreads();
   const int sig = s_sig;
+  if (S8 != nullptr) {
 #pragma unroll 4
-  for (int idx = tid; idx < kQT * kQT; idx += kQThreads) {
-    const int j = idx & (kQT - 1), i = idx >> 7;   // consecutive threads: consecutive columns
-    if (i < rows) S8[(size_t)(R0 + i) * lds + c0 + j] = __ushort_as_half(quant_e4m3_h(tileq[i * kQLD + j], sig, G));
+    for (int idx = tid; idx < kQT * kQT; idx += kQThreads) {
+      const int j = idx & (kQT - 1), i = idx >> 7;   // consecutive threads: consecutive columns
+      if (i < rows) S8[(size_t)(R0 + i) * lds + c0 + j] = __ushort_as_half(quant_e4m3_h(tileq[i * kQLD + j], sig, G));
+    }
+  }
+  if (B8 != nullptr) {
+    // four codes per thread, one 32-bit store: 128 rows x 32 words
+    for (int idx = tid; idx < kQT * (kQT / 4); idx += kQThreads) {
+      const int w = idx & (kQT / 4 - 1), i = idx >> 5;
+      if (i < rows) {
+        const double* q = tileq + i * kQLD + 4 * w;
+        const unsigned word = (unsigned)quant_e4m3_code(q[0], sig) | ((unsigned)quant_e4m3_code(q[1], sig) << 8) |
+                              ((unsigned)quant_e4m3_code(q[2], sig) << 16) |
+                              ((unsigned)quant_e4m3_code(q[3], sig) << 24);
+        *reinterpret_cast<unsigned*>(B8 + (size_t)(R0 + i) * lds + c0 + 4 * w) = word;
+      }
+    }
   }
 }
 
 // The panel rows r0 .. r0 + m - 1, columns c0 .. c0 + 127: one CTA per row tile.
 __global__ void __launch_bounds__(kQThreads)
 quant_e4m3_kernel(const double* __restrict__ A, int ld, int r0, int m, int c0, __half* __restrict__ S8,
-                  int lds, int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+                  unsigned char* __restrict__ B8, int lds, int* __restrict__ tile_exp, int ntile_ld, int G,
+                  unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ double tileq[];                  // [128][kQLD]
   const int R0 = r0 + blockIdx.x * kQT;
-  quant_tile(A, ld, R0, min(kQT, r0 + m - R0), c0, S8, lds, tile_exp, ntile_ld, G, err, tileq);
+  quant_tile(A, ld, R0, min(kQT, r0 + m - R0), c0, S8, B8, lds, tile_exp, ntile_ld, G, err, tileq);
 }
 
 // Every tile strictly below the diagonal tiles of the block A[off:off+nb, off:off+nb]: CTA e
 // takes tile (I, J), e = I (I - 1) / 2 + J, 0 <= J < I.
 __global__ void __launch_bounds__(kQThreads)
-quant_e4m3_lower_kernel(const double* __restrict__ A, int ld, int off, int nb, __half* __restrict__ S8, int lds,
-                        int* __restrict__ tile_exp, int ntile_ld, int G, unsigned* __restrict__ err) {
+quant_e4m3_lower_kernel(const double* __restrict__ A, int ld, int off, int nb, __half* __restrict__ S8,
+                        unsigned char* __restrict__ B8, int lds, int* __restrict__ tile_exp, int ntile_ld, int G,
+                        unsigned* __restrict__ err) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ double tileq[];                  // [128][kQLD]
@@ -645,13 +700,13 @@ quant_e4m3_lower_kernel(const double* __restrict__ A, int ld, int off, int nb, _
   while ((I + 1) * I / 2 <= e) ++I;
   const int J = e - I * (I - 1) / 2;
   const int R0 = off + I * kQT;
-  quant_tile(A, ld, R0, min(kQT, off + nb - R0), off + J * kQT, S8, lds, tile_exp, ntile_ld, G, err, tileq);
+  quant_tile(A, ld, R0, min(kQT, off + nb - R0), off + J * kQT, S8, B8, lds, tile_exp, ntile_ld, G, err, tileq);
 }
 
 }  // namespace
 
-cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, int lds,
-                              int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s) {
+cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, int nc, __half* S8, unsigned char* B8,
+                              int lds, int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if ((r0 % 128) || (c0 % 128) || nc != 128) return cudaErrorInvalidValue;
   const size_t smem = (size_t)128 * kQLD * sizeof(double);
@@ -662,12 +717,13 @@ cudaError_t launch_quant_e4m3(const double* A, int ld, int r0, int m, int c0, in
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  (void)launch_pdl(quant_e4m3_kernel, dim3((m + 127) / 128), dim3(kQThreads), smem, s, A, ld, r0, m, c0, S8, lds, tile_exp, ntile_ld, G, err);
+  (void)launch_pdl(quant_e4m3_kernel, dim3((m + 127) / 128), dim3(kQThreads), smem, s, A, ld, r0, m, c0, S8, B8, lds,
+                   tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, int lds, int* tile_exp,
-                                    int ntile_ld, int G, unsigned* err, cudaStream_t s) {
+cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __half* S8, unsigned char* B8, int lds,
+                                    int* tile_exp, int ntile_ld, int G, unsigned* err, cudaStream_t s) {
   const int nt = (nb + kQT - 1) / kQT;
   if (nt < 2) return cudaSuccess;
   if (off % kQT) return cudaErrorInvalidValue;
@@ -680,8 +736,8 @@ cudaError_t launch_quant_e4m3_lower(const double* A, int ld, int off, int nb, __
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  (void)launch_pdl(quant_e4m3_lower_kernel, dim3(nt * (nt - 1) / 2), dim3(kQThreads), smem, s, A, ld, off, nb, S8, lds, tile_exp, ntile_ld, G,
-                                                                    err);
+  (void)launch_pdl(quant_e4m3_lower_kernel, dim3(nt * (nt - 1) / 2), dim3(kQThreads), smem, s, A, ld, off, nb, S8, B8,
+                   lds, tile_exp, ntile_ld, G, err);
   return cudaGetLastError();
 }
 

@@ -351,6 +351,34 @@ def test_fp8_levels_reproduce_emulator_rounding(hrp_mod, handle, spec):
     assert f_gpu <= 0.02 * f_emu, (f_gpu, f_emu)
 
 
+@pytest.mark.parametrize("spec,n", [("[F8,F16,F32|F64@128]", 2048), ("[F8,F32|F64@128]", 1024),
+                                    ("[F8,F16,F16,F32|F64@128]", 4096)])
+def test_fp8_block_scaled_equals_fp16_storage(hrp_mod, handle, spec, n):
+    """The block-scaled E4M3 MMAs (UE8M0 scale per tile) and the FP16-stored E4M3 values on the
+    FP16 GEMM form the same exact products of the same quantized operands; only the FP32
+    accumulation inside the tensor core may differ, and with it, rarely, a later rounding
+    decision of the quantizer."""
+    A = dominant_spd(n, 2.0, seed_for(3, 300 + n))
+    L8, info8 = _factor_mode(hrp_mod, A, spec, fp16_storage=False)
+    L16, info16 = _factor_mode(hrp_mod, A, spec, fp16_storage=True)
+    assert info8 == info16 == 0
+    scale = np.max(np.abs(L16))
+    d = np.abs(np.tril(L8 - L16)) / scale
+    assert np.median(d[np.tril_indices(n)]) <= 1e-8 and d.max() <= 1e-4, (np.median(d), d.max())
+
+
+def _factor_mode(hrp_mod, A, spec, fp16_storage):
+    h = hrp_mod.Handle(0)
+    try:
+        h.set_f8_gemm(fp16_storage)
+        At = hrp_mod.colmajor(A).cuda()
+        info = h.potrf(hrp_mod.tree_parse(spec, leaf=128), At)
+        assert h.check() == 0
+        return np.tril(hrp_mod.from_colmajor(At)), info
+    finally:
+        h.close()
+
+
 def test_fp8_requires_power_of_two_blocks(hrp_mod, handle):
     A = dominant_spd(1000, 2.0, seed_for(3, 5))
     At = hrp_mod.colmajor(A).cuda()
