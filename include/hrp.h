@@ -152,6 +152,24 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * Diagonal tiles of the FP64 leaves (Alg. 1 base case).  The 128 x 128 FP64 leaf is factored
+ * by 16 x 16 tiles; each diagonal tile's Cholesky is a chain of 16 dependent pivots, the
+ * critical path of the whole factorization on a GPU whose FP64 operations take ~64 cycles.
+ *   mode 1: that tile's Cholesky runs in double-float arithmetic (pairs of binary32, Dekker
+ *     1971; about 48 significant bits, relative error of each operation a few units of
+ *     2^-48) on the FP32 pipe.  The tile is scaled by a power of two and converted exactly
+ *     (hi) and to 2^-48 (lo) from FP64, and the factor is rounded back to FP64.  A tile with
+ *     an entry that is not finite, or a pivot that is not positive or falls below 2^-36 times
+ *     its largest diagonal entry, runs the FP64 chain instead (which also reports a failing
+ *     column).  Every other operation of the leaf (its TRSM and update tiles, the panel
+ *     exchange) stays in FP64.
+ *   mode 0: the chain in FP64.
+ *   mode -1 (default): mode 1 for trees with a level below FP64, mode 0 for all-FP64 trees.
+ * Applies to hrp_potrf, hrp_potrf_async, hrp_posv and the stream-pool batched calls.
+ */
+hrp_status hrp_set_leaf_chain(hrp_handle* h, int mode);
+
+/*
  * F8 levels (E4M3 with one power-of-two scale 2^e per 128 x 128 tile of L).  mode 0 (default):
  * the F8-level GEMMs are block-scaled E4M3 tensor-core products (kind::mxf8f6f4, one UE8M0
  * scale 127 + e per row and 32 K elements, constant over each tile), at the FP8 rate.  mode 1:

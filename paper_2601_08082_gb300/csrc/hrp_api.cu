@@ -105,6 +105,9 @@ struct hrp_handle_s {
   size_t scale_exp_cap = 0;
   // FP32-level GEMMs: 0 = SIMT FP32 (default), 1 = error-corrected TF32 split on tcgen05
   int fp32_split = 0;
+  // FP64 leaves' 16 x 16 diagonal-tile Cholesky: 1 = double-float on the FP32 pipe, 0 = FP64,
+  // -1 (default) = double-float when the tree has a level below FP64, else FP64
+  int leaf_chain = -1;
   float* split32 = nullptr;    // hi then lo, row-major (see Fact::h32)
   size_t split32_cap = 0;
   // batched factorization: 0 = one stream per system (default), 1 = one persistent launch
@@ -287,6 +290,8 @@ struct Fact {
     lc.pdl = !(w != waited.end() && w->second);
     if (w != waited.end()) w->second = false;
     lc.max_ctas = (la && s != main_s) ? side_ctas : 0;
+    lc.leaf_df = h->leaf_chain == 1 ||
+                 (h->leaf_chain < 0 && (tree_has(t, HRP_F32) || tree_has(t, HRP_F16) || tree_has(t, HRP_F8E4M3)));
     if (h->timing) {
       cudaEvent_t e = event(ev_next);
       began = e && cudaEventRecord(e, s) == cudaSuccess;
@@ -1294,6 +1299,14 @@ hrp_status hrp_set_refinement(hrp_handle* h, int mode, int restart, double inner
 }
 
 long long hrp_last_inner_iterations(const hrp_handle* h) { return h ? h->inner_steps : 0; }
+
+hrp_status hrp_set_leaf_chain(hrp_handle* h, int mode) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (mode < -1 || mode > 1) return bad_arg(h, 2, "mode must be -1 (by tree), 0 (FP64) or 1 (double-float)");
+  h->leaf_chain = mode;
+  return HRP_OK;
+}
 
 hrp_status hrp_set_f8_gemm(hrp_handle* h, int mode) {
   if (!h) return HRP_ERR_INVALID_ARG;

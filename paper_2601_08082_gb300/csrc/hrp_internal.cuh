@@ -45,6 +45,7 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 struct LaunchCtx {
   bool pdl = true;
   int max_ctas = 0;
+  bool leaf_df = false;   // FP64 leaves: 16 x 16 pivot chains in double-float (k_leaf_cluster.cu)
 };
 inline LaunchCtx& launch_ctx() {
   thread_local LaunchCtx c;

@@ -62,6 +62,9 @@ struct ClusterLeafSmem {
   float wcol[8][kTileD];                // W phase: W_KJ of this CTA's column block
   float tmp[kTileD];                    // W phase: sum_K L_IK W_KJ
   const float* gsrc[kMaxGather];        // W phase: where each gathered tile comes from
+  float2 dcol[2][kTS];                  // double-float chain: column k (after the updates of columns < k)
+  float2 drs[kTS];                      // double-float chain: d_k^{-1/2}
+  float2 ddg[kTS];                      // double-float chain: pivots d_k
   int fail;                             // read by the cluster: the last diagonal tile here failed
   int cfail;                            // pivot chain: column of the failed pivot, or -1
   signed char slot[8][8];               // slot of tile (I, J) in its owner's `own`
@@ -264,6 +267,213 @@ __device__ __forceinline__ int potrf16_chain(double* __restrict__ T, ClusterLeaf
   return potrf16_chain_t<kChainWarps, kChainSeg>(T, sm, tid);
 }
 
+// ---------------------------------------------------------------------------------------
+// The same 16 x 16 Cholesky with the whole LDL^T recurrence in double-float arithmetic on
+// the FP32 pipe.  A double-float value is the unevaluated sum hi + lo of two binary32 numbers
+// (Dekker 1971), about 48 significant bits: sums by Knuth's error-free TwoSum, products by the
+// FMA-based exact product, in the accurate pair forms whose relative errors Joldes, Muller and
+// Popescu (2017) bound by a few units of 2^-48.  FP32 operations take a few cycles where an
+// FP64 one takes ~64 on this GPU (~128 while other sub-partitions issue FP64), so a column
+// step (the pivot's reciprocal, one product, one update) costs ~150 cycles instead of ~850.
+//   - The tile is scaled by 2^-2s (2s the largest even integer not above the largest
+//     diagonal exponent) while it is converted, exactly in hi and rounded in lo, by integer
+//     operations on the bit fields; the factor is scaled back by 2^s, d_k by 2^2s and
+//     1 / L_kk by 2^-s.  Scaled entries below 2^-60 become zero (2^-12 below the pairs'
+//     unit roundoff relative to the tile's largest entry).
+//   - Threads 0..119 hold the entries (i, j), i >= j >= 1, in registers; column 0 and, after
+//     each step, the next column are published in a double-buffered column array: one CTA
+//     barrier per column.  Every thread forms 1 / d_k itself from the published pivot, so
+//     every thread sees the same pivot and takes the same exit.
+//   - A tile with an entry that is not finite or beyond 8 times the largest diagonal entry,
+//     or a pivot that is not positive or falls below 2^-36 times the largest diagonal entry
+//     (where the pairs' error terms would leave binary32's normal range), returns -2 with T
+//     untouched; the caller then runs the FP64 chain, which also reports a failing column.
+// ---------------------------------------------------------------------------------------
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);                  // x.hi y.hi = p + e exactly
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  const dfloat t = df_two_sum(x.lo, y.lo);
+  s = df_fast_two_sum(s.hi, s.lo + t.hi);
+  return df_fast_two_sum(s.hi, s.lo + t.lo);
+}
+// 1/d for d > 0: single-precision seed x0, e = 1 - d x0 as a pair (1 - fl(d.hi x0) is exact by
+// Sterbenz's lemma), then the third-order step x0 (1 + e + e^2); |e| < 2^-21
+__device__ __forceinline__ dfloat df_recip(dfloat d) {
+  float x0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x0) : "f"(d.hi));
+  const float p = d.hi * x0;
+  float pe = fmaf(d.hi, x0, -p);
+  pe = fmaf(d.lo, x0, pe);
+  const dfloat e = df_two_sum(1.0f - p, -pe);
+  const float p2 = x0 * e.hi;
+  float q = fmaf(x0, e.hi, -p2);
+  q = fmaf(x0, e.lo, q);
+  q = fmaf(p2, e.hi, q);
+  const dfloat r = df_fast_two_sum(x0, p2);
+  return df_fast_two_sum(r.hi, r.lo + q);
+}
+// d^{-1/2} for d > 0: seed r0, e = 1 - d r0^2 as a pair, then r0 (1 + e/2 + 3 e^2 / 8)
+__device__ __forceinline__ dfloat df_rsqrt(dfloat d) {
+  const float r0 = rsqrtf(d.hi);
+  const float y = r0 * r0;
+  const dfloat t = df_mul(d, dfloat{y, fmaf(r0, r0, -y)});
+  const dfloat e = df_two_sum(1.0f - t.hi, -t.lo);
+  const float h = 0.5f * e.hi;
+  const float c = fmaf(0.375f * e.hi, e.hi, 0.5f * e.lo);
+  const float p2 = r0 * h;
+  float q = fmaf(r0, h, -p2);
+  q = fmaf(r0, c, q);
+  const dfloat r = df_fast_two_sum(r0, p2);
+  return df_fast_two_sum(r.hi, r.lo + q);
+}
+// unbiased binary32 exponent of a positive normal float
+__device__ __forceinline__ int f32_exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xff) - 127; }
+
+// x 2^-s2 as a pair, by integer operations: hi = x's sign and leading 24 significand bits
+// (truncated) at the scaled exponent e, lo = the remaining 29 bits rounded to binary32 at
+// 2^(e - 52), then renormalized.  Returns 0 (converted), 1 (zero, subnormal, or e < -60: out
+// = 0) or 2 (not finite or e > 3).
+__device__ __forceinline__ int df_split_scaled(double x, int s2, dfloat& out) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0x7ff) return 2;
+  const int e = E - 1023 - s2;
+  if (E == 0 || e < -60) {
+    out = {0.0f, 0.0f};
+    return 1;
+  }
+  if (e > 3) return 2;
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const float hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  const float ulo = __uint2float_rn((unsigned)(m & 0x1fffffffu)) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
+  out = df_fast_two_sum(hi, __uint_as_float(__float_as_uint(ulo) | sgn));
+  return 0;
+}
+// f 2^off widened to double by integer operations (exact); zero and subnormal f give 0
+__device__ __forceinline__ double df_widen_scaled(float f, int off) {
+  const unsigned u = __float_as_uint(f);
+  const int E = (int)((u >> 23) & 0xff);
+  if (E == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(E - 127 + 1023 + off) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double df_to_double_scaled(dfloat x, int off) {
+  return df_widen_scaled(x.hi, off) + df_widen_scaled(x.lo, off);
+}
+
+// Returns as potrf16_chain, or -2 (T untouched; the caller then runs the FP64 chain).
+__device__ int potrf16_df(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+  // 1. the scale from the diagonal: every thread reads all 16 entries and takes the same
+  //    decision (no barrier)
+  int emax = 0, emin = 0x7ff;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < kTS; ++k) {
+    const long long b = __double_as_longlong(T[k * kTLD + k]);
+    const int E = (int)(b >> 52);                 // negative for a negative entry
+    ok = ok && E > 0 && E < 0x7ff;
+    emax = max(emax, E);
+    emin = min(emin, E);
+  }
+  const int s2 = ((emax - 1023) >> 1) * 2;        // floor((emax - 1023) / 2) * 2
+  if (!ok || emin - 1023 - s2 < -36) return -2;
+  const int sc = s2 / 2;
+  // 2. entries (i, j), j >= 1: thread t < 120 takes entry t of the 15 x 15 triangle, offset
+  //    by one; threads 0..15 also hold column 0 and publish it
+  const bool act = tid < kLowT - kTS;
+  int i = 0, j = 0;
+  if (act) {
+    lower_entry(tid, i, j);
+    ++i;
+    ++j;
+  }
+  dfloat a{0.0f, 0.0f}, c0{0.0f, 0.0f};
+  int out = 0;
+  if (act) out |= df_split_scaled(T[i * kTLD + j], s2, a) >> 1;
+  if (tid < kTS) {
+    out |= df_split_scaled(T[tid * kTLD], s2, c0) >> 1;
+    sm.dcol[0][tid] = make_float2(c0.hi, c0.lo);
+  }
+  if (__syncthreads_or(out)) return -2;
+  // 3. columns k = 0 .. 14: a_ij -= (a_ik a_jk) / d_k for i >= j > k
+  int res = -1;
+  for (int k = 0; k + 1 < kTS; ++k) {
+    const float2* col = sm.dcol[k & 1];
+    const float2 dk = col[k];
+    if (!(dk.x > 0.0f) || f32_exponent(dk.x) < -36) {   // the same in every thread
+      res = -2;
+      break;
+    }
+    const dfloat sk = df_recip(dfloat{dk.x, dk.y});
+    if (act && j > k) {
+      const float2 ai = col[i], aj = col[j];
+      const dfloat u = df_mul(df_mul(dfloat{ai.x, ai.y}, dfloat{aj.x, aj.y}), sk);
+      a = df_add(a, dfloat{-u.hi, -u.lo});
+      if (j == k + 1) sm.dcol[(k + 1) & 1][i] = make_float2(a.hi, a.lo);
+    }
+    __syncthreads();
+  }
+  if (res == -1) {
+    const float2 d = sm.dcol[(kTS - 1) & 1][kTS - 1];
+    if (!(d.x > 0.0f) || f32_exponent(d.x) < -36) res = -2;
+  }
+  if (res != -1) return res;
+  // 4. r_j = d_j^{-1/2} by the holder of (j, j); l_ij = a_ij r_j (l_jj = d_j r_j); back to
+  //    FP64 at the tile's scale
+  if (act && i == j) {
+    const dfloat r = df_rsqrt(a);
+    sm.drs[j] = make_float2(r.hi, r.lo);
+    sm.ddg[j] = make_float2(a.hi, a.lo);
+  }
+  if (tid == 0) {
+    const dfloat r = df_rsqrt(c0);
+    sm.drs[0] = make_float2(r.hi, r.lo);
+    sm.ddg[0] = make_float2(c0.hi, c0.lo);
+  }
+  __syncthreads();
+  if (act) {
+    const float2 r = sm.drs[j];
+    T[i * kTLD + j] = df_to_double_scaled(df_mul(a, dfloat{r.x, r.y}), sc);
+  }
+  if (tid < kTS) {
+    const float2 r0 = sm.drs[0], r = sm.drs[tid], d = sm.ddg[tid];
+    T[tid * kTLD] = df_to_double_scaled(df_mul(c0, dfloat{r0.x, r0.y}), sc);
+    sm.rinv[tid] = df_to_double_scaled(dfloat{r.x, r.y}, -sc);
+    sm.dk[tid] = df_to_double_scaled(dfloat{d.x, d.y}, s2);
+  }
+  return -1;
+}
+
+// the diagonal tile's Cholesky: the double-float recurrence when asked for and in range,
+// else (or when it leaves the range) the FP64 one
+__device__ __forceinline__ int potrf16_diag(double* __restrict__ T, ClusterLeafSmem& sm, int tid, int df_chain) {
+  if (df_chain) {
+    const int r = potrf16_df(T, sm, tid);
+    if (r != -2) return r;
+    __syncthreads();
+  }
+  return potrf16_chain(T, sm, tid);
+}
+
 // X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
 // threads, in unit-diagonal form: with L = Lt diag(L_kk) (Lt_jk = L_jk / L_kk, formed here in
 // Lt) and Y = X diag(L_kk), Y Lt^T = A is a substitution without scaling, y_ij = a_ij -
@@ -341,7 +551,7 @@ __device__ __forceinline__ unsigned consumers(int I, int p, int NT) {
 
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kCThreads, 1)
 potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
-                          int* __restrict__ info) {
+                          int* __restrict__ info, int df_chain) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -407,7 +617,7 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
         tile_update_diag(T, sm.pan[prev][p], tid);
         __syncthreads();
       }
-      const int bad = potrf16_chain(T, sm, tid);
+      const int bad = potrf16_diag(T, sm, tid, df_chain);
       if (bad >= 0) {
         if (tid == 0) {
           atomicMin(info, col0 + kTS * p + bad + 1);
@@ -585,7 +795,8 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(ClusterLeafSmem), s, A, ld, n, col0, W32, ldw, info);
+  (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(ClusterLeafSmem), s, A, ld, n, col0,
+                   W32, ldw, info, launch_ctx().leaf_df ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
     "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
     "hrp_last_inner_iterations", "hrp_autotune_orders", "hrp_set_batched_mode", "hrp_set_scaling",
-    "hrp_set_fp32_split", "hrp_set_f8_gemm",
+    "hrp_set_fp32_split", "hrp_set_f8_gemm", "hrp_set_leaf_chain",
 ]
 
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
     L.hrp_set_scaling.argtypes = [vp, c_int]
     L.hrp_set_fp32_split.argtypes = [vp, c_int]
     L.hrp_set_f8_gemm.argtypes = [vp, c_int]
+    L.hrp_set_leaf_chain.argtypes = [vp, c_int]
     L.hrp_set_refinement.argtypes = [vp, c_int, c_int, c_double]
     L.hrp_last_inner_iterations.argtypes = [vp]
     L.hrp_last_inner_iterations.restype = ctypes.c_longlong
@@ -220,6 +221,11 @@ class Handle:
     def set_scaling(self, dynamic: bool) -> None:
         """hrp_set_scaling: two-sided power-of-two diagonal scaling before the recursion."""
         self._check(self._lib.hrp_set_scaling(self._h, 1 if dynamic else 0))
+
+    def set_leaf_chain(self, double_float: bool) -> None:
+        """hrp_set_leaf_chain: FP64 leaves' 16 x 16 pivot chains in double-float (True, default)
+        or in FP64 (False)."""
+        self._check(self._lib.hrp_set_leaf_chain(self._h, 1 if double_float else 0))
 
     def set_f8_gemm(self, fp16_storage: bool) -> None:
         """hrp_set_f8_gemm: F8 levels by block-scaled E4M3 MMAs (False, default) or through
