@@ -152,18 +152,17 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
- * Diagonal tiles of the FP64 leaves (Alg. 1 base case).  The 128 x 128 FP64 leaf is factored
- * by 16 x 16 tiles; each diagonal tile's Cholesky is a chain of 16 dependent pivots, the
- * critical path of the whole factorization on a GPU whose FP64 operations take ~64 cycles.
- *   mode 1: that tile's Cholesky runs in double-float arithmetic (pairs of binary32, Dekker
- *     1971; about 48 significant bits, relative error of each operation a few units of
- *     2^-48) on the FP32 pipe.  The tile is scaled by a power of two and converted exactly
- *     (hi) and to 2^-48 (lo) from FP64, and the factor is rounded back to FP64.  A tile with
- *     an entry that is not finite, or a pivot that is not positive or falls below 2^-36 times
- *     its largest diagonal entry, runs the FP64 chain instead (which also reports a failing
- *     column).  Every other operation of the leaf (its TRSM and update tiles, the panel
- *     exchange) stays in FP64.
- *   mode 0: the chain in FP64.
+ * Arithmetic of the FP64 leaves (Alg. 1 base case, the 128 x 128 leaf on an 8-CTA cluster).
+ * The leaf's pivot chains, TRSM substitutions and rank-16 updates lie on the critical path of
+ * the whole factorization, and FP64 operations take ~64 cycles on this GPU.
+ *   mode 1: the leaf runs in double-float arithmetic (pairs of binary32, Dekker 1971; about
+ *     48 significant bits, relative error of each operation a few units of 2^-48) on the FP32
+ *     pipe.  The leaf is scaled by a power of two and converted exactly (hi) and to 2^-48
+ *     (lo) from FP64 on load, and L is rounded back to FP64 on store.  A leaf with an entry
+ *     that is not finite, or a diagonal entry or pivot that is not positive or falls below
+ *     2^-36 times its largest diagonal entry, is factored again by the FP64 schedule in the
+ *     same launch (bitwise the mode-0 result; a failing column is reported as in mode 0).
+ *   mode 0: the leaf in FP64.
  *   mode -1 (default): mode 1 for trees with a level below FP64, mode 0 for all-FP64 trees.
  * Applies to hrp_potrf, hrp_potrf_async, hrp_posv and the stream-pool batched calls.
  */

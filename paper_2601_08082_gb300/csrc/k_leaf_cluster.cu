@@ -1,4 +1,5 @@
-// Leaf POTRF (Alg. 1 base case) in FP64 spread over a cluster of 8 CTAs.
+// Leaf POTRF (Alg. 1 base case) spread over a cluster of 8 CTAs, in FP64 or in
+// double-float arithmetic on the FP32 pipe.
 //
 // FP64 on this GPU: each SM sub-partition issues one FP64 warp instruction per ~64
 // cycles (also the dependent latency), the SM as a whole about one per 19 cycles
@@ -24,8 +25,28 @@
 // after the same barrier).  The FP32 inverse W = L^{-1} for the FP32 leaf TRSM (when
 // requested) is built at the end by column blocks, one CTA per block:
 // W_JJ = L_JJ^{-1}, W_IJ = -L_II^{-1} sum_{K=J}^{I-1} L_IK W_KJ.
+//
+// Double-float mode (df = 1).  The same schedule with every tile held as a pair of binary32
+// numbers hi + lo (Dekker 1971; about 48 significant bits): sums by Knuth's error-free TwoSum,
+// products by the FMA-based exact product, in the accurate pair forms whose relative errors
+// Joldes, Muller and Popescu (2017) bound by a few units of 2^-48, and dot products
+// accumulated as in Ogita, Rump and Oishi's Dot2 (2005).  FP32 operations take a few cycles of
+// latency where FP64 ones take ~64 (~128 while other sub-partitions issue FP64), and the FP32
+// pipe has ~40x the FP64 issue rate, so the pivot chains, the TRSM substitutions and the
+// rank-16 updates all run several times faster.
+//   - The leaf is scaled by 2^-2s (2s the largest even integer not above the largest
+//     diagonal exponent) while it is loaded and converted, exactly in hi and to 2^-48 in lo,
+//     by integer operations on the bit fields; L is stored back times 2^s, rounded to FP64.
+//     Scaled entries below 2^-60 are read as zero (2^-12 below the pairs' unit roundoff
+//     relative to the largest diagonal entry).
+//   - A leaf with an entry that is not finite or above 8 times the largest diagonal entry, or
+//     with a diagonal entry or pivot that is not positive or falls below 2^-36 times the
+//     largest diagonal entry (where the pairs' error terms would leave binary32's normal
+//     range), is factored again from the untouched input by the FP64 schedule in the same
+//     launch; that also reports the column of a failing pivot exactly as FP64 does.
 #include <climits>
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "hrp_internal.cuh"
 
@@ -44,31 +65,43 @@ constexpr int kLowT = kTS * (kTS + 1) / 2;   // entries of a lower 16 x 16 trian
 constexpr int kMaxGather = 36;               // W phase: tiles one CTA reads (28 of L, 8 inverses)
 constexpr int kChainWarps = 3;               // worker warps of the 16 x 16 pivot chain
 constexpr int kChainSeg = 2;                 // entries of one row per worker thread
+constexpr int kFallback = 1;                 // leaf_body's result: factor again in FP64
 
-struct ClusterLeafSmem {
-  double own[kMaxOwn][kTileD];          // owned tiles, row-major (row i at i * kTLD)
-  double pan[2][8][kTileD];             // pan[p & 1][I] = L_{I,p} (I > p) or L_pp (I = p)
-  double cv[kTS][kTS];                  // pivot chain: cv[k][i] = a_ik after the updates of columns < k
-  double dpr[kTS + 2];                  // pivot chain: a_kk after the updates of columns < k - 1
-  double usq[kTS + 2];                  // pivot chain: a_{k,k-1}^2 after the updates of columns < k - 1
+// a double-float value hi + lo, |lo| <= ulp(hi) / 2 (8-byte aligned: one 64-bit access)
+struct __align__(8) dfloat {
+  float hi, lo;
+};
+
+// E = double (FP64 mode) or dfloat (double-float mode); both are 8 bytes, so the two layouts
+// coincide and one dynamic shared-memory size serves both
+template <class E>
+struct LeafSmem {
+  E own[kMaxOwn][kTileD];               // owned tiles, row-major (row i at i * kTLD)
+  E pan[2][8][kTileD];                  // pan[p & 1][I] = L_{I,p} (I > p) or L_pp (I = p)
+  double cv[kTS][kTS];                  // FP64 pivot chain: cv[k][i] = a_ik after the updates of columns < k
+  double dpr[kTS + 2];                  // FP64 pivot chain: a_kk after the updates of columns < k - 1
+  double usq[kTS + 2];                  // FP64 pivot chain: a_{k,k-1}^2 after the updates of columns < k - 1
   double dk[kTS];                       // pivots d_k
   double sk[kTS];                       // 1 / d_k
-  double rinv[kTS];                     // 1 / L_kk = d_k^{-1/2} of the diagonal tile factored last here
-  double rin_copy[kTS];                 // rinv of the diagonal tile the TRSM here uses
-  double lt[kTileD];                    // TRSM: unit lower Lt = L diag(rinv) of that tile
+  E rinv[kTS];                          // 1 / L_kk = d_k^{-1/2} of the diagonal tile factored last here
+  E rin_copy[kTS];                      // rinv of the diagonal tile the TRSM here uses
+  E lt[kTileD];                         // TRSM: unit lower Lt = L diag(rinv) of that tile
+  float rinvf[kTS];                     // FP32 rounding of 1 / L_kk (unscaled) for the FP32 inverse
   float ownf[kMaxOwn][kTileD];          // FP32 copies of the finished owned tiles
   float winv[2][kTileD];                // FP32 inverses of the (up to 2) diagonal tiles owned
   float gat[kMaxGather][kTileD];        // W phase: gathered FP32 tiles
   float wcol[8][kTileD];                // W phase: W_KJ of this CTA's column block
   float tmp[kTileD];                    // W phase: sum_K L_IK W_KJ
   const float* gsrc[kMaxGather];        // W phase: where each gathered tile comes from
-  float2 dcol[2][kTS];                  // double-float chain: column k (after the updates of columns < k)
-  float2 drs[kTS];                      // double-float chain: d_k^{-1/2}
-  float2 ddg[kTS];                      // double-float chain: pivots d_k
-  int fail;                             // read by the cluster: the last diagonal tile here failed
+  dfloat dcol[2][kTS];                  // double-float chain: column k (after the updates of columns < k)
+  dfloat drs[kTS];                      // double-float chain: d_k^{-1/2}
+  int dred[2][4];                       // double-float load: per-warp largest / smallest diagonal exponent
+  int lflag;                            // double-float load: an entry here is out of range
+  int fail;                             // read by the cluster: 1 a pivot failed (FP64), 2 fall back
   int cfail;                            // pivot chain: column of the failed pivot, or -1
   signed char slot[8][8];               // slot of tile (I, J) in its owner's `own`
 };
+static_assert(sizeof(LeafSmem<double>) == sizeof(LeafSmem<dfloat>), "one shared-memory size for both modes");
 
 __device__ __forceinline__ int owner_of(int I, int J) { return (I + J) & (kCL - 1); }
 
@@ -185,7 +218,7 @@ __device__ __forceinline__ void tile_update_diag(double* __restrict__ C, const d
 // of columns < j), r_j = d_j^{-1/2}, also stored in sm.rinv.  Returns the 0-based column of
 // the first pivot that is not positive and finite, or -1 (the same in every thread).
 template <int NW, int SEG>
-__device__ int potrf16_chain_t(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+__device__ int potrf16_chain_t(double* __restrict__ T, LeafSmem<double>& sm, int tid) {
   const int warp = tid >> 5;
   int wi = -1, wj0 = 0, wcnt = 0;
   double a[SEG];
@@ -263,35 +296,14 @@ __device__ int potrf16_chain_t(double* __restrict__ T, ClusterLeafSmem& sm, int 
   return -1;
 }
 
-__device__ __forceinline__ int potrf16_chain(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
+__device__ __forceinline__ int potrf16_chain(double* __restrict__ T, LeafSmem<double>& sm, int tid) {
   return potrf16_chain_t<kChainWarps, kChainSeg>(T, sm, tid);
 }
 
+
 // ---------------------------------------------------------------------------------------
-// The same 16 x 16 Cholesky with the whole LDL^T recurrence in double-float arithmetic on
-// the FP32 pipe.  A double-float value is the unevaluated sum hi + lo of two binary32 numbers
-// (Dekker 1971), about 48 significant bits: sums by Knuth's error-free TwoSum, products by the
-// FMA-based exact product, in the accurate pair forms whose relative errors Joldes, Muller and
-// Popescu (2017) bound by a few units of 2^-48.  FP32 operations take a few cycles where an
-// FP64 one takes ~64 on this GPU (~128 while other sub-partitions issue FP64), so a column
-// step (the pivot's reciprocal, one product, one update) costs ~150 cycles instead of ~850.
-//   - The tile is scaled by 2^-2s (2s the largest even integer not above the largest
-//     diagonal exponent) while it is converted, exactly in hi and rounded in lo, by integer
-//     operations on the bit fields; the factor is scaled back by 2^s, d_k by 2^2s and
-//     1 / L_kk by 2^-s.  Scaled entries below 2^-60 become zero (2^-12 below the pairs'
-//     unit roundoff relative to the tile's largest entry).
-//   - Threads 0..119 hold the entries (i, j), i >= j >= 1, in registers; column 0 and, after
-//     each step, the next column are published in a double-buffered column array: one CTA
-//     barrier per column.  Every thread forms 1 / d_k itself from the published pivot, so
-//     every thread sees the same pivot and takes the same exit.
-//   - A tile with an entry that is not finite or beyond 8 times the largest diagonal entry,
-//     or a pivot that is not positive or falls below 2^-36 times the largest diagonal entry
-//     (where the pairs' error terms would leave binary32's normal range), returns -2 with T
-//     untouched; the caller then runs the FP64 chain, which also reports a failing column.
+// Double-float arithmetic (see the file comment)
 // ---------------------------------------------------------------------------------------
-struct dfloat {
-  float hi, lo;
-};
 __device__ __forceinline__ dfloat df_two_sum(float a, float b) {
   const float s = a + b, bb = s - a;
   return {s, (a - (s - bb)) + (b - bb)};
@@ -313,6 +325,7 @@ __device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
   s = df_fast_two_sum(s.hi, s.lo + t.hi);
   return df_fast_two_sum(s.hi, s.lo + t.lo);
 }
+__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
 // 1/d for d > 0: single-precision seed x0, e = 1 - d x0 as a pair (1 - fl(d.hi x0) is exact by
 // Sterbenz's lemma), then the third-order step x0 (1 + e + e^2); |e| < 2^-21
 __device__ __forceinline__ dfloat df_recip(dfloat d) {
@@ -343,8 +356,26 @@ __device__ __forceinline__ dfloat df_rsqrt(dfloat d) {
   const dfloat r = df_fast_two_sum(r0, p2);
   return df_fast_two_sum(r.hi, r.lo + q);
 }
-// unbiased binary32 exponent of a positive normal float
+// unbiased binary32 exponent (-127 for zero and subnormals)
 __device__ __forceinline__ int f32_exponent(float x) { return (int)((__float_as_uint(x) >> 23) & 0xff) - 127; }
+
+// Dot2 accumulator: the running sum s (binary32, carried on by error-free TwoSum) and c, which
+// collects TwoSum's rounding errors and the low-order parts of the products
+struct df_acc {
+  float s, c;
+};
+__device__ __forceinline__ df_acc acc_of(dfloat x) { return {x.hi, x.lo}; }
+// a -= x y
+__device__ __forceinline__ void acc_sub_prod(df_acc& a, dfloat x, dfloat y) {
+  const float p = -x.hi * y.hi;
+  float e = fmaf(-x.hi, y.hi, -p);                 // -x.hi y.hi = p + e exactly
+  e = fmaf(-x.hi, y.lo, e);
+  e = fmaf(-x.lo, y.hi, e);
+  const float s = a.s + p, bb = s - a.s;
+  a.c += ((a.s - (s - bb)) + (p - bb)) + e;
+  a.s = s;
+}
+__device__ __forceinline__ dfloat acc_value(df_acc a) { return df_two_sum(a.s, a.c); }
 
 // x 2^-s2 as a pair, by integer operations: hi = x's sign and leading 24 significand bits
 // (truncated) at the scaled exponent e, lo = the remaining 29 bits rounded to binary32 at
@@ -380,25 +411,77 @@ __device__ __forceinline__ double df_to_double_scaled(dfloat x, int off) {
   return df_widen_scaled(x.hi, off) + df_widen_scaled(x.lo, off);
 }
 
-// Returns as potrf16_chain, or -2 (T untouched; the caller then runs the FP64 chain).
-__device__ int potrf16_df(double* __restrict__ T, ClusterLeafSmem& sm, int tid) {
-  // 1. the scale from the diagonal: every thread reads all 16 entries and takes the same
-  //    decision (no barrier)
-  int emax = 0, emin = 0x7ff;
-  bool ok = true;
+// ---------------------------------------------------------------------------------------
+// Tile operations in double-float (the FP64 ones above, same thread layout)
+// ---------------------------------------------------------------------------------------
+// C -= LI * LJ^T for an off-diagonal 16 x 16 tile
+__device__ __forceinline__ void tile_update(dfloat* __restrict__ C, const dfloat* __restrict__ LI,
+                                            const dfloat* __restrict__ LJ, int tid) {
+  const int i = tid >> 3, j0 = 2 * (tid & 7);
+  df_acc c0 = acc_of(C[i * kTLD + j0]), c1 = acc_of(C[i * kTLD + j0 + 1]);
 #pragma unroll
   for (int k = 0; k < kTS; ++k) {
-    const long long b = __double_as_longlong(T[k * kTLD + k]);
-    const int E = (int)(b >> 52);                 // negative for a negative entry
-    ok = ok && E > 0 && E < 0x7ff;
-    emax = max(emax, E);
-    emin = min(emin, E);
+    const dfloat a = LI[i * kTLD + k];
+    acc_sub_prod(c0, a, LJ[j0 * kTLD + k]);
+    acc_sub_prod(c1, a, LJ[(j0 + 1) * kTLD + k]);
   }
-  const int s2 = ((emax - 1023) >> 1) * 2;        // floor((emax - 1023) / 2) * 2
-  if (!ok || emin - 1023 - s2 < -36) return -2;
-  const int sc = s2 / 2;
-  // 2. entries (i, j), j >= 1: thread t < 120 takes entry t of the 15 x 15 triangle, offset
-  //    by one; threads 0..15 also hold column 0 and publish it
+  C[i * kTLD + j0] = acc_value(c0);
+  C[i * kTLD + j0 + 1] = acc_value(c1);
+}
+
+// C -= LI * LI^T on the lower triangle of a diagonal tile: entry t (t < 128) by thread t in
+// two interleaved accumulators; the last 8 entries (row 15, columns 8..15) one term per thread
+// of a half-warp, reduced by shuffles
+__device__ __forceinline__ void tile_update_diag(dfloat* __restrict__ C, const dfloat* __restrict__ LI, int tid) {
+  int i, j;
+  lower_entry(tid, i, j);
+  df_acc c0 = acc_of(C[i * kTLD + j]), c1{0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < kTS; k += 2) {
+    acc_sub_prod(c0, LI[i * kTLD + k], LI[j * kTLD + k]);
+    acc_sub_prod(c1, LI[i * kTLD + k + 1], LI[j * kTLD + k + 1]);
+  }
+  const int jx = 8 + (tid >> 4), kx = tid & 15;            // entry (15, jx), term kx
+  dfloat x = df_mul(LI[15 * kTLD + kx], LI[jx * kTLD + kx]);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1)
+    x = df_add(x, dfloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)});
+  C[i * kTLD + j] = df_add(acc_value(c0), acc_value(c1));
+  if (kx == 0) C[15 * kTLD + jx] = df_add(C[15 * kTLD + jx], df_neg(x));
+}
+
+// X L^T = A in place, unit-diagonal form as the FP64 trsm16: Lt = L diag(rinv), Y Lt^T = A by
+// substitution (each y_ij accumulated as a Dot2 sum), X = Y diag(rinv)
+__device__ __forceinline__ void trsm16(dfloat* __restrict__ A, const dfloat* __restrict__ L,
+                                       const dfloat* __restrict__ rinv, dfloat* __restrict__ Lt, int tid) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + kCThreads * h, j = e >> 4, k = e & 15;
+    if (k < j) Lt[j * kTLD + k] = df_mul(L[j * kTLD + k], rinv[k]);
+  }
+  __syncthreads();
+  const int i = tid >> 3, cp = tid & 7, lane = tid & 31, j0 = 2 * cp;
+  df_acc c0 = acc_of(A[i * kTLD + j0]), c1 = acc_of(A[i * kTLD + j0 + 1]);
+#pragma unroll
+  for (int k = 0; k < kTS; ++k) {
+    const dfloat v = acc_value((k & 1) ? c1 : c0);
+    const int src = (lane & ~7) | (k >> 1);
+    const dfloat y{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+    if (j0 > k) acc_sub_prod(c0, y, Lt[j0 * kTLD + k]);
+    if (j0 + 1 > k) acc_sub_prod(c1, y, Lt[(j0 + 1) * kTLD + k]);
+  }
+  A[i * kTLD + j0] = df_mul(acc_value(c0), rinv[j0]);
+  A[i * kTLD + j0 + 1] = df_mul(acc_value(c1), rinv[j0 + 1]);
+}
+
+// Cholesky of the 16 x 16 tile T (lower part) in double-float, LDL^T form: a_ij -= (a_ik a_jk)
+// / d_k for i >= j > k.  Threads 0..119 hold the entries (i, j), i >= j >= 1, in registers;
+// column 0 and, after each step, the next column are published in a double-buffered column
+// array, one CTA barrier per column.  Every thread forms 1 / d_k itself from the published
+// pivot, so every thread sees the same pivot and takes the same exit.  At the end l_ij =
+// a_ij r_j, l_jj = d_j r_j, r_j = d_j^{-1/2} (also in sm.rinv).  Returns -1, or -2 when a pivot
+// is not positive or falls below 2^-36 (the leaf is then factored again in FP64).
+__device__ int potrf16(dfloat* __restrict__ T, LeafSmem<dfloat>& sm, int tid) {
   const bool act = tid < kLowT - kTS;
   int i = 0, j = 0;
   if (act) {
@@ -407,72 +490,84 @@ __device__ int potrf16_df(double* __restrict__ T, ClusterLeafSmem& sm, int tid) 
     ++j;
   }
   dfloat a{0.0f, 0.0f}, c0{0.0f, 0.0f};
-  int out = 0;
-  if (act) out |= df_split_scaled(T[i * kTLD + j], s2, a) >> 1;
+  if (act) a = T[i * kTLD + j];
   if (tid < kTS) {
-    out |= df_split_scaled(T[tid * kTLD], s2, c0) >> 1;
-    sm.dcol[0][tid] = make_float2(c0.hi, c0.lo);
+    c0 = T[tid * kTLD];
+    sm.dcol[0][tid] = c0;
   }
-  if (__syncthreads_or(out)) return -2;
-  // 3. columns k = 0 .. 14: a_ij -= (a_ik a_jk) / d_k for i >= j > k
+  __syncthreads();
   int res = -1;
   for (int k = 0; k + 1 < kTS; ++k) {
-    const float2* col = sm.dcol[k & 1];
-    const float2 dk = col[k];
-    if (!(dk.x > 0.0f) || f32_exponent(dk.x) < -36) {   // the same in every thread
+    const dfloat* col = sm.dcol[k & 1];
+    const dfloat dk = col[k];
+    if (!(dk.hi > 0.0f) || f32_exponent(dk.hi) < -36) {   // the same in every thread
       res = -2;
       break;
     }
-    const dfloat sk = df_recip(dfloat{dk.x, dk.y});
+    const dfloat sk = df_recip(dk);
     if (act && j > k) {
-      const float2 ai = col[i], aj = col[j];
-      const dfloat u = df_mul(df_mul(dfloat{ai.x, ai.y}, dfloat{aj.x, aj.y}), sk);
-      a = df_add(a, dfloat{-u.hi, -u.lo});
-      if (j == k + 1) sm.dcol[(k + 1) & 1][i] = make_float2(a.hi, a.lo);
+      a = df_add(a, df_neg(df_mul(df_mul(col[i], col[j]), sk)));
+      if (j == k + 1) sm.dcol[(k + 1) & 1][i] = a;
     }
     __syncthreads();
   }
   if (res == -1) {
-    const float2 d = sm.dcol[(kTS - 1) & 1][kTS - 1];
-    if (!(d.x > 0.0f) || f32_exponent(d.x) < -36) res = -2;
+    const dfloat d = sm.dcol[(kTS - 1) & 1][kTS - 1];
+    if (!(d.hi > 0.0f) || f32_exponent(d.hi) < -36) res = -2;
   }
   if (res != -1) return res;
-  // 4. r_j = d_j^{-1/2} by the holder of (j, j); l_ij = a_ij r_j (l_jj = d_j r_j); back to
-  //    FP64 at the tile's scale
-  if (act && i == j) {
-    const dfloat r = df_rsqrt(a);
-    sm.drs[j] = make_float2(r.hi, r.lo);
-    sm.ddg[j] = make_float2(a.hi, a.lo);
-  }
-  if (tid == 0) {
-    const dfloat r = df_rsqrt(c0);
-    sm.drs[0] = make_float2(r.hi, r.lo);
-    sm.ddg[0] = make_float2(c0.hi, c0.lo);
-  }
+  if (act && i == j) sm.drs[j] = df_rsqrt(a);
+  if (tid == 0) sm.drs[0] = df_rsqrt(c0);
   __syncthreads();
-  if (act) {
-    const float2 r = sm.drs[j];
-    T[i * kTLD + j] = df_to_double_scaled(df_mul(a, dfloat{r.x, r.y}), sc);
-  }
+  if (act) T[i * kTLD + j] = df_mul(a, sm.drs[j]);
   if (tid < kTS) {
-    const float2 r0 = sm.drs[0], r = sm.drs[tid], d = sm.ddg[tid];
-    T[tid * kTLD] = df_to_double_scaled(df_mul(c0, dfloat{r0.x, r0.y}), sc);
-    sm.rinv[tid] = df_to_double_scaled(dfloat{r.x, r.y}, -sc);
-    sm.dk[tid] = df_to_double_scaled(dfloat{d.x, d.y}, s2);
+    T[tid * kTLD] = df_mul(c0, sm.drs[0]);
+    sm.rinv[tid] = sm.drs[tid];
   }
   return -1;
 }
-
-// the diagonal tile's Cholesky: the double-float recurrence when asked for and in range,
-// else (or when it leaves the range) the FP64 one
-__device__ __forceinline__ int potrf16_diag(double* __restrict__ T, ClusterLeafSmem& sm, int tid, int df_chain) {
-  if (df_chain) {
-    const int r = potrf16_df(T, sm, tid);
-    if (r != -2) return r;
-    __syncthreads();
-  }
+__device__ __forceinline__ int potrf16(double* __restrict__ T, LeafSmem<double>& sm, int tid) {
   return potrf16_chain(T, sm, tid);
 }
+
+// conversions at the leaf's boundary (s2 = 2s, sc = s: see the file comment)
+__device__ __forceinline__ int load_conv(double x, int, double& out) {
+  out = x;
+  return 0;
+}
+__device__ __forceinline__ int load_conv(double x, int s2, dfloat& out) { return df_split_scaled(x, s2, out); }
+__device__ __forceinline__ void set_small(double& out, int v) { out = (double)v; }
+__device__ __forceinline__ void set_small(dfloat& out, int v) { out = {(float)v, 0.0f}; }
+__device__ __forceinline__ double store_conv(double x, int) { return x; }
+__device__ __forceinline__ double store_conv(dfloat x, int sc) { return df_to_double_scaled(x, sc); }
+__device__ __forceinline__ float f32_of(double x, int) { return (float)x; }
+__device__ __forceinline__ float f32_of(dfloat x, int sc) { return ldexpf(x.hi, sc); }
+
+// 2s for the double-float leaf (the largest even integer not above the largest diagonal
+// exponent), or INT_MIN when a diagonal entry is not positive and finite or lies 2^36 or more
+// below the largest; the same in every CTA (each reads the whole diagonal)
+__device__ int leaf_scale(const double* __restrict__ A, int ld, int n, LeafSmem<dfloat>& sm, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  int emax = 0, emin = 0x7ff, bad = 0;
+  if (tid < n) {
+    const int E = (int)(__double_as_longlong(A[(size_t)tid * ld + tid]) >> 52);   // < 0 for x < 0
+    if (E <= 0 || E >= 0x7ff) bad = 1;
+    else emax = emin = E;
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  emin = __reduce_min_sync(0xffffffffu, emin);
+  if (lane == 0) {
+    sm.dred[0][warp] = emax;
+    sm.dred[1][warp] = emin;
+  }
+  if (__syncthreads_or(bad)) return INT_MIN;
+  emax = max(max(sm.dred[0][0], sm.dred[0][1]), max(sm.dred[0][2], sm.dred[0][3]));
+  emin = min(min(sm.dred[1][0], sm.dred[1][1]), min(sm.dred[1][2], sm.dred[1][3]));
+  const int s2 = ((emax - 1023) >> 1) * 2;
+  return (emin - 1023 - s2 < -36) ? INT_MIN : s2;
+}
+__device__ __forceinline__ int leaf_scale(const double*, int, int, LeafSmem<double>&, int) { return 0; }
+
 
 // X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
 // threads, in unit-diagonal form: with L = Lt diag(L_kk) (Lt_jk = L_jk / L_kk, formed here in
@@ -501,31 +596,33 @@ __device__ __forceinline__ void trsm16(double* __restrict__ A, const double* __r
 }
 
 // Store the 16 x 16 tile T into slot `dst` of the shared memory of every CTA in `mask`.
-__device__ __forceinline__ void push_tile(cg::cluster_group& cluster, const double* __restrict__ T, double* dst,
-                                          unsigned mask, int tid) {
+template <class E>
+__device__ __forceinline__ void push_tile(cg::cluster_group& cluster, const E* __restrict__ T, E* dst, unsigned mask,
+                                          int tid) {
   const int e0 = tid, e1 = tid + kCThreads;
   const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
-  const double v0 = T[o0], v1 = T[o1];
+  const E v0 = T[o0], v1 = T[o1];
   for (int r = 0; r < kCL; ++r)
     if (mask & (1u << r)) {
-      double* d = cluster.map_shared_rank(dst, r);
+      E* d = cluster.map_shared_rank(dst, r);
       d[o0] = v0;
       d[o1] = v1;
     }
 }
 
-// FP32 copy of the 16 x 16 tile
-__device__ __forceinline__ void to_f32(const double* __restrict__ T, float* __restrict__ F, int tid) {
+// FP32 copy of the 16 x 16 tile (unscaled: sc is the double-float leaf's scale)
+template <class E>
+__device__ __forceinline__ void to_f32(const E* __restrict__ T, float* __restrict__ F, int tid, int sc) {
   const int e0 = tid, e1 = tid + kCThreads;
   const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
-  F[o0] = (float)T[o0];
-  F[o1] = (float)T[o1];
+  F[o0] = f32_of(T[o0], sc);
+  F[o1] = f32_of(T[o1], sc);
 }
 
 // FP32 inverse of the lower 16 x 16 tile Lf (FP32, row-major kTLD) into Wv, by lanes
 // 0..15 of one warp: lane c forms column c by forward substitution, dividing by L_rr as a
-// product with the FP32 rounding of rinv[r] = 1/L_rr.
-__device__ __forceinline__ void trtri16_f32(const float* __restrict__ Lf, const double* __restrict__ rinv,
+// product with rinvf[r], the FP32 rounding of 1/L_rr.
+__device__ __forceinline__ void trtri16_f32(const float* __restrict__ Lf, const float* __restrict__ rinvf,
                                             float* __restrict__ Wv, int lane) {
   if (lane >= kTS) return;
   const int c = lane;
@@ -535,7 +632,7 @@ __device__ __forceinline__ void trtri16_f32(const float* __restrict__ Lf, const 
     float s = (r == c) ? 1.f : 0.f;
 #pragma unroll
     for (int q = 0; q < r; ++q) s = fmaf(-Lf[r * kTLD + q], w[q], s);
-    w[r] = (r >= c) ? s * (float)rinv[r] : 0.f;
+    w[r] = (r >= c) ? s * rinvf[r] : 0.f;
   }
 #pragma unroll
   for (int r = 0; r < kTS; ++r) Wv[r * kTLD + c] = w[r];
@@ -549,13 +646,18 @@ __device__ __forceinline__ unsigned consumers(int I, int p, int NT) {
   return m;
 }
 
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kCThreads, 1)
-potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
-                          int* __restrict__ info, int df_chain) {
-  pdl_wait();
-  pdl_trigger();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ClusterLeafSmem& sm = *reinterpret_cast<ClusterLeafSmem*>(smem_raw);
+
+__device__ __forceinline__ float rinv_f32(double r, int) { return (float)r; }
+__device__ __forceinline__ float rinv_f32(dfloat r, int sc) { return ldexpf(r.hi, -sc); }
+
+// One factorization of the leaf in arithmetic E (see the file comment).  Returns kFallback
+// (the same in every CTA of the cluster, before any write to A, W32 or info) when the
+// double-float leaf must be factored again in FP64, else 0.
+template <class E>
+__device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
+                         int* __restrict__ info, unsigned char* smem_raw) {
+  constexpr bool kDF = std::is_same<E, dfloat>::value;
+  LeafSmem<E>& sm = *reinterpret_cast<LeafSmem<E>*>(smem_raw);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -569,11 +671,17 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
     for (int J = 0; J < 8; ++J)
       for (int I = 0; I < 8; ++I) sm.slot[I][J] = (I >= J && I < NT) ? (signed char)(cnt[owner_of(I, J)]++) : -1;
     sm.fail = 0;
+    sm.lflag = 0;
   }
   __syncthreads();
-  // load the owned tiles (all loads issued before the first store); rows / columns past n
-  // are the identity
+  int s2 = 0;
   if (!skip) {
+    if (kDF) {
+      s2 = leaf_scale(A, ld, n, sm, tid);
+      if (s2 == INT_MIN) return kFallback;     // every CTA read the same diagonal
+    }
+    // load the owned tiles (all loads issued before the first store); rows / columns past n
+    // are the identity
     // NT <= 8, so this CTA owns at most one tile per block column J: row (rank - J) mod 8
     double v[kCL][2];
 #pragma unroll
@@ -592,6 +700,7 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
         v[J][h] = x;
       }
     }
+    int lbad = 0;
 #pragma unroll
     for (int J = 0; J < kCL; ++J) {
       const int I = (rank - J) & 7;
@@ -599,12 +708,26 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int e = tid + kCThreads * h;
-          sm.own[sm.slot[I][J]][(e & 15) * kTLD + (e >> 4)] = v[J][h];
+          const int jj = e >> 4, ii = e & 15;
+          E x;
+          if (kTS * I + ii < n && kTS * J + jj < n) lbad |= load_conv(v[J][h], s2, x) >> 1;
+          else set_small(x, kTS * I + ii == kTS * J + jj ? 1 : 0);
+          sm.own[sm.slot[I][J]][ii * kTLD + jj] = x;
         }
+    }
+    if (kDF) {
+      lbad = __syncthreads_or(lbad);
+      if (tid == 0) sm.lflag = lbad;
     }
   }
   cluster.sync();
-  if (skip) return;
+  if (skip) return 0;
+  if (kDF) {
+    int any = 0;
+    for (int r = 0; r < kCL; ++r) any |= *(volatile int*)cluster.map_shared_rank(&sm.lflag, r);
+    if (any) return kFallback;
+  }
+  const int sc = s2 / 2;
 
   bool failed = false;
   for (int p = 0; p < NT; ++p) {
@@ -612,16 +735,16 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
     const int cur = p & 1, prev = cur ^ 1;
     // ---- A ----
     if (rank == D) {
-      double* T = sm.own[sm.slot[p][p]];
+      E* T = sm.own[sm.slot[p][p]];
       if (p > 0) {
         tile_update_diag(T, sm.pan[prev][p], tid);
         __syncthreads();
       }
-      const int bad = potrf16_diag(T, sm, tid, df_chain);
-      if (bad >= 0) {
+      const int bad = potrf16(T, sm, tid);
+      if (bad != -1) {
         if (tid == 0) {
-          atomicMin(info, col0 + kTS * p + bad + 1);
-          sm.fail = 1;
+          if (bad >= 0) atomicMin(info, col0 + kTS * p + bad + 1);
+          sm.fail = bad >= 0 ? 1 : 2;
         }
       } else {
         __syncthreads();                                       // L_pp and rinv complete
@@ -640,46 +763,53 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
         for (int J = p; J < NT; ++J)
           for (int I = J; I < NT; ++I)
             if (owner_of(I, J) == rank) {
-              double* C = sm.own[sm.slot[I][J]];
+              E* C = sm.own[sm.slot[I][J]];
               if (I == J) tile_update_diag(C, sm.pan[cur][I], tid);
               else tile_update(C, sm.pan[cur][I], sm.pan[cur][J], tid);
             }
       }
       if (W32 && p >= 1 && rank == owner_of(p - 1, p - 1)) {
         float* F = sm.ownf[sm.slot[p - 1][p - 1]];
-        to_f32(sm.own[sm.slot[p - 1][p - 1]], F, tid);
+        to_f32(sm.own[sm.slot[p - 1][p - 1]], F, tid, sc);
+        if (tid < kTS) sm.rinvf[tid] = rinv_f32(sm.rinv[tid], sc);
         __syncthreads();
-        if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p - 1 >= 4 ? 1 : 0], lane);
+        if (warp == 0) trtri16_f32(F, sm.rinvf, sm.winv[p - 1 >= 4 ? 1 : 0], lane);
       }
       if (p > 0)
         for (int J = p; J < NT; ++J)
           for (int I = J; I < NT; ++I)
             if (owner_of(I, J) == rank) {
-              double* C = sm.own[sm.slot[I][J]];
+              E* C = sm.own[sm.slot[I][J]];
               if (I == J) tile_update_diag(C, sm.pan[prev][I], tid);
               else tile_update(C, sm.pan[prev][I], sm.pan[prev][J], tid);
             }
     }
     cluster.sync();                                              // S1
-    if (*(volatile int*)cluster.map_shared_rank(&sm.fail, D)) { failed = true; break; }
+    const int f = *(volatile int*)cluster.map_shared_rank(&sm.fail, D);
+    if (f == 2) return kFallback;
+    if (f) {
+      failed = true;
+      break;
+    }
     // ---- B ----
     int mine = -1;
     for (int I = p + 1; I < NT; ++I)
       if (owner_of(I, p) == rank) mine = I;
     if (mine >= 0) {
-      double* X = sm.own[sm.slot[mine][p]];
+      E* X = sm.own[sm.slot[mine][p]];
       trsm16(X, sm.pan[cur][p], sm.rin_copy, sm.lt, tid);
       __syncthreads();
       push_tile(cluster, X, sm.pan[cur][mine], consumers(mine, p, NT), tid);
-      if (W32) to_f32(X, sm.ownf[sm.slot[mine][p]], tid);
+      if (W32) to_f32(X, sm.ownf[sm.slot[mine][p]], tid, sc);
     }
     // D's other tiles and the FP32 inverse of (p, p) wait for phase A of panel p + 1 (done
     // there while D(p+1) factors), except after the last panel
     if (rank == D && W32 && p + 1 == NT) {
       float* F = sm.ownf[sm.slot[p][p]];
-      to_f32(sm.own[sm.slot[p][p]], F, tid);
+      to_f32(sm.own[sm.slot[p][p]], F, tid, sc);
+      if (tid < kTS) sm.rinvf[tid] = rinv_f32(sm.rinv[tid], sc);
       __syncthreads();
-      if (warp == 0) trtri16_f32(F, sm.rinv, sm.winv[p >= 4 ? 1 : 0], lane);
+      if (warp == 0) trtri16_f32(F, sm.rinvf, sm.winv[p >= 4 ? 1 : 0], lane);
     }
     cluster.sync();                                              // S2
   }
@@ -688,11 +818,11 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
     for (int J = 0; J < NT; ++J)
       for (int I = J; I < NT; ++I) {
         if (owner_of(I, J) != rank) continue;
-        const double* T = sm.own[sm.slot[I][J]];
+        const E* T = sm.own[sm.slot[I][J]];
         for (int e = tid; e < kTS * kTS; e += kCThreads) {
           const int jj = e >> 4, ii = e & 15;
           const int gi = kTS * I + ii, gj = kTS * J + jj;
-          if (gi < n && gj < n && gi >= gj) A[(size_t)gj * ld + gi] = T[ii * kTLD + jj];
+          if (gi < n && gj < n && gi >= gj) A[(size_t)gj * ld + gi] = store_conv(T[ii * kTLD + jj], sc);
         }
       }
     // FP32 inverse, column block J = rank: gather L_IK (J <= K < I) and W_II (I >= J)
@@ -779,6 +909,20 @@ potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float
     }
   }
   cluster.sync();                       // no CTA leaves while others may read its tiles
+  return 0;
+}
+
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kCThreads, 1)
+potrf_leaf_cluster_kernel(double* __restrict__ A, int ld, int n, int col0, float* __restrict__ W32, int ldw,
+                          int* __restrict__ info, int df) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (df) {
+    if (leaf_body<dfloat>(A, ld, n, col0, W32, ldw, info, smem_raw) != kFallback) return;
+    cg::this_cluster().sync();          // every CTA has left the double-float attempt
+  }
+  (void)leaf_body<double>(A, ld, n, col0, W32, ldw, info, smem_raw);
 }
 
 }  // namespace
@@ -791,11 +935,11 @@ cudaError_t launch_potrf_leaf_cluster(double* A, int ld, int n, int col0, float*
   const unsigned long long attr_bit = dev_bit();
   if (!(attr_mask & attr_bit)) {
     cudaError_t e = cudaFuncSetAttribute(potrf_leaf_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(ClusterLeafSmem));
+                                         (int)sizeof(LeafSmem<double>));
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(ClusterLeafSmem), s, A, ld, n, col0,
+  (void)launch_pdl(potrf_leaf_cluster_kernel, dim3(kCL), dim3(kCThreads), sizeof(LeafSmem<double>), s, A, ld, n, col0,
                    W32, ldw, info, launch_ctx().leaf_df ? 1 : 0);
   return cudaGetLastError();
 }

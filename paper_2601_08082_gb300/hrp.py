@@ -222,10 +222,10 @@ class Handle:
         """hrp_set_scaling: two-sided power-of-two diagonal scaling before the recursion."""
         self._check(self._lib.hrp_set_scaling(self._h, 1 if dynamic else 0))
 
-    def set_leaf_chain(self, double_float: bool) -> None:
-        """hrp_set_leaf_chain: FP64 leaves' 16 x 16 pivot chains in double-float (True, default)
-        or in FP64 (False)."""
-        self._check(self._lib.hrp_set_leaf_chain(self._h, 1 if double_float else 0))
+    def set_leaf_chain(self, mode: int) -> None:
+        """hrp_set_leaf_chain: FP64 leaves in double-float arithmetic (1), in FP64 (0), or by
+        tree (-1, default: double-float when the tree has a level below FP64)."""
+        self._check(self._lib.hrp_set_leaf_chain(self._h, int(mode)))
 
     def set_f8_gemm(self, fp16_storage: bool) -> None:
         """hrp_set_f8_gemm: F8 levels by block-scaled E4M3 MMAs (False, default) or through
