@@ -60,7 +60,9 @@ constexpr int kTS = 16;                 // tile edge
 constexpr int kTLD = 17;                // padded row length of a tile (elements)
 constexpr int kTileD = kTS * kTLD;      // elements per tile slot
 constexpr int kMaxOwn = 5;              // tiles per CTA for 8 x 8 tiles owned by (I + J) mod 8
-constexpr int kCThreads = 128;
+constexpr int kCThreads = 256;              // threads per CTA: one per entry of a 16 x 16 tile
+constexpr int kFT = 128;                    // threads that work in the FP64 tile operations
+static_assert(kCThreads == kTS * kTS, "one thread per tile entry");
 constexpr int kLowT = kTS * (kTS + 1) / 2;   // entries of a lower 16 x 16 triangle
 constexpr int kMaxGather = 36;               // W phase: tiles one CTA reads (28 of L, 8 inverses)
 constexpr int kChainWarps = 3;               // worker warps of the 16 x 16 pivot chain
@@ -95,9 +97,9 @@ struct LeafSmem {
   const float* gsrc[kMaxGather];        // W phase: where each gathered tile comes from
   dfloat dcol[2][kTS];                  // double-float chain: column k (after the updates of columns < k)
   dfloat drs[kTS];                      // double-float chain: d_k^{-1/2}
-  int dred[2][4];                       // double-float load: per-warp largest / smallest diagonal exponent
+  int dred[2][kCThreads / 32];          // double-float load: per-warp largest / smallest diagonal exponent
   int lflag;                            // double-float load: an entry here is out of range
-  int fail;                             // read by the cluster: 1 a pivot failed (FP64), 2 fall back
+  int fail;                             // written into every CTA by D: 1 a pivot failed (FP64), 2 fall back
   int cfail;                            // pivot chain: column of the failed pivot, or -1
   signed char slot[8][8];               // slot of tile (I, J) in its owner's `own`
 };
@@ -169,10 +171,12 @@ __device__ __forceinline__ double rsqrt_third_order(double d) {
   return fma(r * e, t, r);
 }
 
-// C -= LI * LJ^T for an off-diagonal 16 x 16 tile, by the 128 threads:
+// C -= LI * LJ^T for an off-diagonal 16 x 16 tile, by threads 0..127 (one FP64 warp
+// instruction costs the same however many lanes it has, so two entries per thread):
 // thread (i, cp) = (tid / 8, tid % 8) owns C[i][2cp], C[i][2cp + 1].
 __device__ __forceinline__ void tile_update(double* __restrict__ C, const double* __restrict__ LI,
                                             const double* __restrict__ LJ, int tid) {
+  if (tid >= kFT) return;
   const int i = tid >> 3, j0 = 2 * (tid & 7);
   double c0 = C[i * kTLD + j0], c1 = C[i * kTLD + j0 + 1];
 #pragma unroll
@@ -186,10 +190,11 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
 }
 
 // C -= LI * LI^T on the lower triangle of a diagonal tile (136 entries x 16 terms), spread
-// evenly over the 128 threads: entry t (t < 128) is summed by thread t, and each of the last
+// evenly over threads 0..127: entry t (t < 128) is summed by thread t, and each of the last
 // 8 entries (row 15, columns 8..15) is split over the 16 threads of a half-warp, one term
 // each, and reduced by shuffles; every thread issues 17 FMAs.
 __device__ __forceinline__ void tile_update_diag(double* __restrict__ C, const double* __restrict__ LI, int tid) {
+  if (tid >= kFT) return;                                  // whole warps
   int i, j;
   lower_entry(tid, i, j);
   double c0 = 0.0, c1 = 0.0;
@@ -412,27 +417,26 @@ __device__ __forceinline__ double df_to_double_scaled(dfloat x, int off) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Tile operations in double-float (the FP64 ones above, same thread layout)
+// Tile operations in double-float: one entry per thread (the FP32 pipe is not issue-bound here,
+// so the more independent chains in flight the better)
 // ---------------------------------------------------------------------------------------
-// C -= LI * LJ^T for an off-diagonal 16 x 16 tile
+// C -= LI * LJ^T for an off-diagonal 16 x 16 tile: thread (i, j) = (tid / 16, tid % 16), its
+// 16 terms in two Dot2 sums (even and odd k)
 __device__ __forceinline__ void tile_update(dfloat* __restrict__ C, const dfloat* __restrict__ LI,
                                             const dfloat* __restrict__ LJ, int tid) {
-  const int i = tid >> 3, j0 = 2 * (tid & 7);
-  df_acc c0 = acc_of(C[i * kTLD + j0]), c1 = acc_of(C[i * kTLD + j0 + 1]);
+  const int i = tid >> 4, j = tid & 15;
+  df_acc c0 = acc_of(C[i * kTLD + j]), c1{0.0f, 0.0f};
 #pragma unroll
-  for (int k = 0; k < kTS; ++k) {
-    const dfloat a = LI[i * kTLD + k];
-    acc_sub_prod(c0, a, LJ[j0 * kTLD + k]);
-    acc_sub_prod(c1, a, LJ[(j0 + 1) * kTLD + k]);
+  for (int k = 0; k < kTS; k += 2) {
+    acc_sub_prod(c0, LI[i * kTLD + k], LJ[j * kTLD + k]);
+    acc_sub_prod(c1, LI[i * kTLD + k + 1], LJ[j * kTLD + k + 1]);
   }
-  C[i * kTLD + j0] = acc_value(c0);
-  C[i * kTLD + j0 + 1] = acc_value(c1);
+  C[i * kTLD + j] = df_add(acc_value(c0), acc_value(c1));
 }
 
-// C -= LI * LI^T on the lower triangle of a diagonal tile: entry t (t < 128) by thread t in
-// two interleaved accumulators; the last 8 entries (row 15, columns 8..15) one term per thread
-// of a half-warp, reduced by shuffles
+// C -= LI * LI^T on the lower triangle of a diagonal tile: entry t (t < 136) by thread t
 __device__ __forceinline__ void tile_update_diag(dfloat* __restrict__ C, const dfloat* __restrict__ LI, int tid) {
+  if (tid >= kLowT) return;
   int i, j;
   lower_entry(tid, i, j);
   df_acc c0 = acc_of(C[i * kTLD + j]), c1{0.0f, 0.0f};
@@ -441,37 +445,26 @@ __device__ __forceinline__ void tile_update_diag(dfloat* __restrict__ C, const d
     acc_sub_prod(c0, LI[i * kTLD + k], LI[j * kTLD + k]);
     acc_sub_prod(c1, LI[i * kTLD + k + 1], LI[j * kTLD + k + 1]);
   }
-  const int jx = 8 + (tid >> 4), kx = tid & 15;            // entry (15, jx), term kx
-  dfloat x = df_mul(LI[15 * kTLD + kx], LI[jx * kTLD + kx]);
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1)
-    x = df_add(x, dfloat{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)});
   C[i * kTLD + j] = df_add(acc_value(c0), acc_value(c1));
-  if (kx == 0) C[15 * kTLD + jx] = df_add(C[15 * kTLD + jx], df_neg(x));
 }
 
 // X L^T = A in place, unit-diagonal form as the FP64 trsm16: Lt = L diag(rinv), Y Lt^T = A by
-// substitution (each y_ij accumulated as a Dot2 sum), X = Y diag(rinv)
+// substitution, X = Y diag(rinv).  Thread (i, j) = (tid / 16, tid % 16) accumulates y_ij as a
+// Dot2 sum; y_ik is passed along the row's 16 threads (one half-warp) by shuffles.
 __device__ __forceinline__ void trsm16(dfloat* __restrict__ A, const dfloat* __restrict__ L,
                                        const dfloat* __restrict__ rinv, dfloat* __restrict__ Lt, int tid) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int e = tid + kCThreads * h, j = e >> 4, k = e & 15;
-    if (k < j) Lt[j * kTLD + k] = df_mul(L[j * kTLD + k], rinv[k]);
-  }
+  const int i = tid >> 4, j = tid & 15, lane = tid & 31;
+  if (j < i) Lt[i * kTLD + j] = df_mul(L[i * kTLD + j], rinv[j]);
   __syncthreads();
-  const int i = tid >> 3, cp = tid & 7, lane = tid & 31, j0 = 2 * cp;
-  df_acc c0 = acc_of(A[i * kTLD + j0]), c1 = acc_of(A[i * kTLD + j0 + 1]);
+  df_acc c = acc_of(A[i * kTLD + j]);
 #pragma unroll
-  for (int k = 0; k < kTS; ++k) {
-    const dfloat v = acc_value((k & 1) ? c1 : c0);
-    const int src = (lane & ~7) | (k >> 1);
+  for (int k = 0; k + 1 < kTS; ++k) {
+    const dfloat v = acc_value(c);                       // y_ik in thread (i, k)
+    const int src = (lane & 16) | k;
     const dfloat y{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
-    if (j0 > k) acc_sub_prod(c0, y, Lt[j0 * kTLD + k]);
-    if (j0 + 1 > k) acc_sub_prod(c1, y, Lt[(j0 + 1) * kTLD + k]);
+    if (j > k) acc_sub_prod(c, y, Lt[j * kTLD + k]);
   }
-  A[i * kTLD + j0] = df_mul(acc_value(c0), rinv[j0]);
-  A[i * kTLD + j0 + 1] = df_mul(acc_value(c1), rinv[j0 + 1]);
+  A[i * kTLD + j] = df_mul(acc_value(c), rinv[j]);
 }
 
 // Cholesky of the 16 x 16 tile T (lower part) in double-float, LDL^T form: a_ij -= (a_ik a_jk)
@@ -504,9 +497,8 @@ __device__ int potrf16(dfloat* __restrict__ T, LeafSmem<dfloat>& sm, int tid) {
       res = -2;
       break;
     }
-    const dfloat sk = df_recip(dk);
     if (act && j > k) {
-      a = df_add(a, df_neg(df_mul(df_mul(col[i], col[j]), sk)));
+      a = df_add(a, df_neg(df_mul(df_mul(col[i], col[j]), df_recip(dk))));
       if (j == k + 1) sm.dcol[(k + 1) & 1][i] = a;
     }
     __syncthreads();
@@ -561,28 +553,31 @@ __device__ int leaf_scale(const double* __restrict__ A, int ld, int n, LeafSmem<
     sm.dred[1][warp] = emin;
   }
   if (__syncthreads_or(bad)) return INT_MIN;
-  emax = max(max(sm.dred[0][0], sm.dred[0][1]), max(sm.dred[0][2], sm.dred[0][3]));
-  emin = min(min(sm.dred[1][0], sm.dred[1][1]), min(sm.dred[1][2], sm.dred[1][3]));
+#pragma unroll
+  for (int w = 0; w < kCThreads / 32; ++w) {
+    emax = max(emax, sm.dred[0][w]);
+    emin = min(emin, sm.dred[1][w]);
+  }
   const int s2 = ((emax - 1023) >> 1) * 2;
   return (emin - 1023 - s2 < -36) ? INT_MIN : s2;
 }
 __device__ __forceinline__ int leaf_scale(const double*, int, int, LeafSmem<double>&, int) { return 0; }
 
 
-// X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by the 128
-// threads, in unit-diagonal form: with L = Lt diag(L_kk) (Lt_jk = L_jk / L_kk, formed here in
+// X L^T = A for the 16 x 16 tile A (in place), L lower with 1/L_kk in rinv, by threads
+// 0..127, in unit-diagonal form: with L = Lt diag(L_kk) (Lt_jk = L_jk / L_kk, formed here in
 // Lt) and Y = X diag(L_kk), Y Lt^T = A is a substitution without scaling, y_ij = a_ij -
 // sum_{k<j} y_ik Lt_jk, and X = Y diag(rinv) at the end; no multiply sits between one
 // column's broadcast and the next.  Thread (i, cp) = (tid / 8, tid % 8) holds A[i][2cp],
 // A[i][2cp + 1]; y_ik is passed along the row's 8 threads by a shuffle.
 __device__ __forceinline__ void trsm16(double* __restrict__ A, const double* __restrict__ L,
                                        const double* __restrict__ rinv, double* __restrict__ Lt, int tid) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int e = tid + kCThreads * h, j = e >> 4, k = e & 15;
+  {
+    const int j = tid >> 4, k = tid & 15;
     if (k < j) Lt[j * kTLD + k] = L[j * kTLD + k] * rinv[k];
   }
   __syncthreads();
+  if (tid >= kFT) return;                                  // whole warps
   const int i = tid >> 3, cp = tid & 7, lane = tid & 31, j0 = 2 * cp;
   double c0 = A[i * kTLD + j0], c1 = A[i * kTLD + j0 + 1];
 #pragma unroll
@@ -599,24 +594,17 @@ __device__ __forceinline__ void trsm16(double* __restrict__ A, const double* __r
 template <class E>
 __device__ __forceinline__ void push_tile(cg::cluster_group& cluster, const E* __restrict__ T, E* dst, unsigned mask,
                                           int tid) {
-  const int e0 = tid, e1 = tid + kCThreads;
-  const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
-  const E v0 = T[o0], v1 = T[o1];
+  const int o = (tid >> 4) * kTLD + (tid & 15);
+  const E v = T[o];
   for (int r = 0; r < kCL; ++r)
-    if (mask & (1u << r)) {
-      E* d = cluster.map_shared_rank(dst, r);
-      d[o0] = v0;
-      d[o1] = v1;
-    }
+    if (mask & (1u << r)) cluster.map_shared_rank(dst, r)[o] = v;
 }
 
 // FP32 copy of the 16 x 16 tile (unscaled: sc is the double-float leaf's scale)
 template <class E>
 __device__ __forceinline__ void to_f32(const E* __restrict__ T, float* __restrict__ F, int tid, int sc) {
-  const int e0 = tid, e1 = tid + kCThreads;
-  const int o0 = (e0 >> 4) * kTLD + (e0 & 15), o1 = (e1 >> 4) * kTLD + (e1 & 15);
-  F[o0] = f32_of(T[o0], sc);
-  F[o1] = f32_of(T[o1], sc);
+  const int o = (tid >> 4) * kTLD + (tid & 15);
+  F[o] = f32_of(T[o], sc);
 }
 
 // FP32 inverse of the lower 16 x 16 tile Lf (FP32, row-major kTLD) into Wv, by lanes
@@ -683,37 +671,30 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
     // load the owned tiles (all loads issued before the first store); rows / columns past n
     // are the identity
     // NT <= 8, so this CTA owns at most one tile per block column J: row (rank - J) mod 8
-    double v[kCL][2];
+    // one entry of each owned tile per thread: (ii, jj) = (tid % 16, tid / 16)
+    const int jj = tid >> 4, ii = tid & 15;          // column-major walk: coalesced reads
+    double v[kCL];
 #pragma unroll
     for (int J = 0; J < kCL; ++J) {
       const int I = (rank - J) & 7;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e = tid + kCThreads * h;
-        const int jj = e >> 4, ii = e & 15;          // column-major walk: coalesced reads
-        double x = 0.0;
-        if (J < NT && I >= J && I < NT) {
-          const int gi = kTS * I + ii, gj = kTS * J + jj;
-          if (gi < n && gj < n) x = (gi >= gj) ? A[(size_t)gj * ld + gi] : 0.0;
-          else x = (gi == gj) ? 1.0 : 0.0;
-        }
-        v[J][h] = x;
+      double x = 0.0;
+      if (J < NT && I >= J && I < NT) {
+        const int gi = kTS * I + ii, gj = kTS * J + jj;
+        if (gi < n && gj < n) x = (gi >= gj) ? A[(size_t)gj * ld + gi] : 0.0;
+        else x = (gi == gj) ? 1.0 : 0.0;
       }
+      v[J] = x;
     }
     int lbad = 0;
 #pragma unroll
     for (int J = 0; J < kCL; ++J) {
       const int I = (rank - J) & 7;
-      if (J < NT && I >= J && I < NT)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int e = tid + kCThreads * h;
-          const int jj = e >> 4, ii = e & 15;
-          E x;
-          if (kTS * I + ii < n && kTS * J + jj < n) lbad |= load_conv(v[J][h], s2, x) >> 1;
-          else set_small(x, kTS * I + ii == kTS * J + jj ? 1 : 0);
-          sm.own[sm.slot[I][J]][ii * kTLD + jj] = x;
-        }
+      if (J < NT && I >= J && I < NT) {
+        E x;
+        if (kTS * I + ii < n && kTS * J + jj < n) lbad |= load_conv(v[J], s2, x) >> 1;
+        else set_small(x, kTS * I + ii == kTS * J + jj ? 1 : 0);
+        sm.own[sm.slot[I][J]][ii * kTLD + jj] = x;
+      }
     }
     if (kDF) {
       lbad = __syncthreads_or(lbad);
@@ -744,7 +725,7 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
       if (bad != -1) {
         if (tid == 0) {
           if (bad >= 0) atomicMin(info, col0 + kTS * p + bad + 1);
-          sm.fail = bad >= 0 ? 1 : 2;
+          for (int r = 0; r < kCL; ++r) *cluster.map_shared_rank(&sm.fail, r) = bad >= 0 ? 1 : 2;
         }
       } else {
         __syncthreads();                                       // L_pp and rinv complete
@@ -785,7 +766,7 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
             }
     }
     cluster.sync();                                              // S1
-    const int f = *(volatile int*)cluster.map_shared_rank(&sm.fail, D);
+    const int f = *(volatile int*)&sm.fail;
     if (f == 2) return kFallback;
     if (f) {
       failed = true;
@@ -867,32 +848,22 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
       // gathered index of L_IK: row I starts at (I-J-1)(I-J)/2; W_II follows the nl L tiles
       for (int e = tid; e < kTileD; e += kCThreads) sm.wcol[J][e] = sm.gat[nl][e];
       __syncthreads();
-      const int r = tid >> 3, q0 = (tid & 7) * 2;
+      const int r = tid >> 4, q = tid & 15;
       for (int I = J + 1; I < NT; ++I) {
-        // tmp = sum_K L_IK W_KJ ; thread: row r, columns q0, q0 + 1
-        float s0 = 0.f, s1 = 0.f;
+        // tmp = sum_K L_IK W_KJ ; thread: row r, column q
+        float s0 = 0.f;
         for (int K = J; K < I; ++K) {
           const float* L = sm.gat[(I - J - 1) * (I - J) / 2 + (K - J)];
 #pragma unroll
-          for (int k = 0; k < kTS; ++k) {
-            const float l = L[r * kTLD + k];
-            s0 = fmaf(l, sm.wcol[K][k * kTLD + q0], s0);
-            s1 = fmaf(l, sm.wcol[K][k * kTLD + q0 + 1], s1);
-          }
+          for (int k = 0; k < kTS; ++k) s0 = fmaf(L[r * kTLD + k], sm.wcol[K][k * kTLD + q], s0);
         }
-        sm.tmp[r * kTLD + q0] = s0;
-        sm.tmp[r * kTLD + q0 + 1] = s1;
+        sm.tmp[r * kTLD + q] = s0;
         __syncthreads();
         const float* Wi = sm.gat[nl + (I - J)];
-        float o0 = 0.f, o1 = 0.f;
+        float o0 = 0.f;
 #pragma unroll
-        for (int mm = 0; mm < kTS; ++mm) {
-          const float wv = Wi[r * kTLD + mm];
-          o0 = fmaf(-wv, sm.tmp[mm * kTLD + q0], o0);
-          o1 = fmaf(-wv, sm.tmp[mm * kTLD + q0 + 1], o1);
-        }
-        sm.wcol[I][r * kTLD + q0] = o0;
-        sm.wcol[I][r * kTLD + q0 + 1] = o1;
+        for (int mm = 0; mm < kTS; ++mm) o0 = fmaf(-Wi[r * kTLD + mm], sm.tmp[mm * kTLD + q], o0);
+        sm.wcol[I][r * kTLD + q] = o0;
         __syncthreads();
       }
       // write column block J of W (column-major, zeros above the diagonal)
