@@ -41,8 +41,12 @@ FP64_MEASURED_TFLOPS = 1.20
 FP32_MEASURED_TFLOPS = 75.2
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture, reported
 # while the kernel's device code is the code captured: the source up to its launcher, hashed.
-LEAF_TRAFFIC = {"bytes": 150528, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "e8bffda6d025138e101779f672700ffe9a98bf8e"}
+LEAF_TRAFFIC = {"bytes": 163584, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "a8293fce89abc3f0cf9a49ee3ecae6243a8463ea"}
+# The leaves of trees with a level below FP64 run in double-float arithmetic on the FP32 pipe:
+# one double-float multiply-add (the Dot2 accumulation step of the tile updates) is 12 FP32
+# instructions, so FP64-class work done that way peaks at the FP32 rate / 12.
+DF_OPS_PER_FMA = 12
 
 
 def device_code_sha1(path, until):
@@ -718,6 +722,10 @@ def main():
         achieved = per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
         if name == "gemm_f16_tcgen05":
             peak, bound, src = pk["bf16_tflops"], "tensor", f"{pk['src']} bf16 dense burst (FP16 same rate)"
+        elif name in ("leaf_potrf_fp64",) and TREE != FP64_TREE:
+            peak, bound = FP32_MEASURED_TFLOPS / DF_OPS_PER_FMA, "alu"
+            src = (f"double-float on the FP32 pipe: FP32 {FP32_MEASURED_TFLOPS} TFLOP/s (FFMA microbenchmark, this "
+                   f"pool) / {DF_OPS_PER_FMA} FP32 instructions per double-float multiply-add")
         elif name in ("leaf_potrf_fp64",):
             peak, bound, src = FP64_MEASURED_TFLOPS, "alu", "FP64 1.20 TFLOP/s (DFMA microbenchmark, this pool)"
         else:
