@@ -126,7 +126,7 @@ potrs_diag_inverse_kernel(const double* __restrict__ L, int ldl, int n, T* __res
 
 // ---- 2/3. sweeps ----
 template <typename T, bool FWD>
-__global__ void __launch_bounds__(PT)
+__global__ void __launch_bounds__(PT, 1)
 potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ W, double* __restrict__ B, int ldb,
                    int n, int nrhs, int* __restrict__ ticket, int* __restrict__ flags, const int* __restrict__ ctr,
                    int ne, int q, unsigned* __restrict__ err, unsigned long long limit_ns) {
@@ -149,6 +149,15 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
 #pragma unroll
   for (int c = 0; c < MAX_RHS; ++c) acc[c] = (T)0;
 
+  // this block's right-hand side does not depend on other blocks either: its DRAM latency
+  // stays off the block-to-block chain (thread tid holds entries tid + PT u)
+  constexpr int kBU = MAX_RHS * PB / PT;
+  T bpre[kBU];
+#pragma unroll
+  for (int u = 0; u < kBU; ++u) {
+    const int idx = tid + PT * u, ii = idx % PB, c = idx / PB;
+    bpre[u] = (c < nrhs && ii < rows) ? (T)B[(size_t)c * ldb + R0 + ii] : (T)0;
+  }
   // W_r does not depend on other blocks: fetch this thread's 16 entries now
   const T* Wr = W + (size_t)r * PB * PB;      // column-major, ld 64
   T wv[16];
@@ -208,10 +217,10 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
   for (int c = 0; c < MAX_RHS; ++c)
     if (c < nrhs) part[ch][c][i] = acc[c];
   __syncthreads();
-  for (int idx = tid; idx < nrhs * PB; idx += PT) {
-    const int ii = idx % PB, c = idx / PB;
-    const T b = (ii < rows) ? (T)B[(size_t)c * ldb + R0 + ii] : (T)0;
-    accS[c][ii] = b - ((part[0][c][ii] + part[1][c][ii]) + (part[2][c][ii] + part[3][c][ii]));
+#pragma unroll
+  for (int u = 0; u < kBU; ++u) {
+    const int idx = tid + PT * u, ii = idx % PB, c = idx / PB;
+    if (c < nrhs) accS[c][ii] = bpre[u] - ((part[0][c][ii] + part[1][c][ii]) + (part[2][c][ii] + part[3][c][ii]));
   }
   __syncthreads();
   // y_r = W_r acc (forward) or x_r = W_r^T acc (backward): row i, chunk ch of 16 columns
