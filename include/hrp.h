@@ -152,6 +152,23 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
                     int* iters, double* resid, int* info, int* used_fallback, void* stream);
 
 /*
+ * Alg. 1 on a matrix in HOST memory: hrp_potrf_async with the transfer overlapped.  The lower
+ * triangle of hA (column-major, leading dimension ldha) is copied into dA (lda) in blocks of
+ * 128 columns, block b holding rows [128 b, n) of columns [128 b, 128 b + 128), on a copy
+ * stream of the handle, in column order; each node of the recursion waits only for the
+ * blocks it reads, so the leading blocks are factored while the rest is in flight, and half
+ * of the matrix is transferred.  The copies start after the work queued on `stream` before
+ * the call; every copy has completed before the work this call queues on `stream` does.
+ * Entries of dA above the 128 x 128 diagonal blocks are not written.  hA should be
+ * page-locked (cudaHostAlloc or cudaHostRegister): from pageable memory the copies are staged
+ * through the driver and overlap nothing.  hA must stay unchanged until the copies are done
+ * (synchronize `stream`).  Otherwise as hrp_potrf_async: *d_info (device) as in hrp_potrf,
+ * no synchronization.
+ */
+hrp_status hrp_potrf_host(hrp_handle* h, const hrp_tree* tree, int n, const double* hA, int ldha, double* dA,
+                          int lda, int* d_info, void* stream);
+
+/*
  * Arithmetic of the FP64 leaves (Alg. 1 base case, the 128 x 128 leaf on an 8-CTA cluster).
  * The leaf's pivot chains, TRSM substitutions and rank-16 updates lie on the critical path of
  * the whole factorization, and FP64 operations take ~64 cycles on this GPU.

@@ -91,6 +91,9 @@ struct hrp_handle_s {
   bool lookahead = true;
   std::vector<cudaStream_t> lstreams;
   std::vector<cudaEvent_t> levents;
+  // hrp_potrf_host: the copy stream and one event per 128-column block of the copied matrix
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> col_events;
   // refinement of hrp_posv: 0 = classical (POTRS corrections), 1 = GMRES-IR
   int refine_mode = 0;
   int gmres_restart = 20;
@@ -265,6 +268,10 @@ struct Fact {
   int side_ctas = 0;
   // record mode (persistent batched launch): operations are appended here, nothing is launched
   std::vector<BatchOp>* rec = nullptr;
+  // host input (hrp_potrf_host): event of the copy of each 128-column block (rows from the
+  // block's diagonal down), and the last block each stream has waited for
+  const std::vector<cudaEvent_t>* col_ev = nullptr;
+  std::map<cudaStream_t, int> col_waited;
   // timing mode: an event pair around every launch, tagged with its class and flops
   struct Rec { int cls; size_t ev; double flops; };
   std::vector<Rec> recs;
@@ -464,6 +471,17 @@ struct Fact {
     waited[on] = true;
   }
 
+  // host input: the next launch on s reads columns < col_end (rows from their diagonal down)
+  static constexpr int kColBlock = 128;
+  void need(int col_end) {
+    if (!col_ev || col_ev->empty() || col_end <= 0) return;
+    const int b = std::min((int)col_ev->size() - 1, (col_end - 1) / kColBlock);
+    int& w = col_waited.emplace(s, -1).first->second;
+    if (w >= b) return;
+    wait(s, (*col_ev)[b]);
+    w = b;
+  }
+
   // Alg. 1.  `rest`: when non-null, the event after which everything of this node outside
   // its A11 block is up to date (A11 itself is up to date now, on the critical stream).
   //
@@ -478,6 +496,7 @@ struct Fact {
     int p = node_prec(t, depth, nb);
     if (nb <= t->leaf) {
       wait(s, rest);
+      need(off + nb);
       leaf_potrf(off, nb, p);
       return;
     }
@@ -487,7 +506,8 @@ struct Fact {
     if (p == HRP_F8E4M3) quant8_lower(off, n1);
     const int m1 = n2 > t->leaf ? split(n2) : n2;
     if (!la || m1 >= n2 || depth + 1 >= (int)side->size()) {
-      trsm(off + n1, n2, off, n1, p);
+      trsm(off + n1, n2, off, n1, p);              // A21 lies in the columns of A11: copied
+      need(off + nb);
       syrk(off + n1, n2, off, n1, p);
       potrf(off + n1, n2, depth + 1);
       return;
@@ -497,11 +517,14 @@ struct Fact {
     wait(ss, record(s));                         // L11 (and its FP32 inverses) are final
     trsm(r0, m1, off, n1, p, n2);                // top rows of A21: critical
     cudaEvent_t top = record(s);
+    need(r0 + m1);
     syrk(r0, m1, off, n1, p);                    // A22[0:m1, 0:m1] -= A21_top A21_top^T
     s = ss;                                      // side: the rest of Alg. 2 and Alg. 3
     trsm(rb, mb, off, n1, p, n2);
     wait(ss, top);
+    need(r0 + m1);
     gemm(p, rb, mb, r0, m1, off, n1, false);     // A22[m1:, 0:m1] -= A21_bot A21_top^T
+    need(off + nb);
     syrk(rb, mb, off, n1, p);                    // A22[m1:, m1:] (lower) -= A21_bot A21_bot^T
     cudaEvent_t done = record(ss);
     s = main_s;
@@ -551,7 +574,8 @@ hrp_status lookahead_streams(hrp_handle* h) {
   return HRP_OK;
 }
 
-hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s) {
+hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, int lda, int* d_info, cudaStream_t s,
+                         const std::vector<cudaEvent_t>* col_ev = nullptr) {
   hrp_status st;
   const bool has8 = tree_has(t, HRP_F8E4M3);
   if (has8) {
@@ -622,8 +646,10 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
   }
   const bool scaled = h->scaling == 1 && n > 0;
   if (scaled && (st = ensure(h, &h->scale_exp, &h->scale_exp_cap, (size_t)n)) != HRP_OK) return st;
+  f.col_ev = col_ev;
   f.begin(CLS_OTHER, 0.0);
   f.chk(launch_fill_int(d_info, INT_MAX, 1, f.s));
+  if (scaled) f.need(n);                      // the scaling reads the whole matrix
   if (scaled) {                               // A_hat = D^-1 A D^-1, D = diag(2^e_i)
     f.begin(CLS_OTHER, 0.0);
     f.chk(launch_diag_scale(dA, lda, n, h->scale_exp, false, f.s));
@@ -633,6 +659,7 @@ hrp_status potrf_enqueue(hrp_handle* h, const hrp_tree* t, int n, double* dA, in
     f.begin(CLS_OTHER, 0.0);
     f.chk(launch_diag_scale(dA, lda, n, h->scale_exp, true, f.s));
   }
+  f.need(n);                                  // every copy is done when the call's work is
   f.begin(CLS_OTHER, 0.0);
   f.chk(launch_finalize_info(d_info, f.s));
   if (f.la) {
@@ -768,6 +795,8 @@ hrp_status hrp_destroy(hrp_handle* h) {
   for (cudaStream_t st : h->bstreams) cudaStreamDestroy(st);
   for (cudaStream_t st : h->lstreams) cudaStreamDestroy(st);
   for (cudaEvent_t e : h->levents) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->col_events) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   cudaFree(h->bwork);
   cudaFree(h->fwork);
   cudaFree(h->kwork);
@@ -866,6 +895,47 @@ hrp_status hrp_potrf_async(hrp_handle* h, const hrp_tree* tree, int n, double* d
   if (!d_info) return bad_arg(h, 6, "d_info is NULL");
   cudaSetDevice(h->device);
   return potrf_enqueue(h, tree, n, dA, lda, d_info, static_cast<cudaStream_t>(stream));
+}
+
+hrp_status hrp_potrf_host(hrp_handle* h, const hrp_tree* tree, int n, const double* hA, int ldha, double* dA, int lda,
+                          int* d_info, void* stream) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  hrp_status st = validate_tree(h, tree, 2);
+  if (st != HRP_OK) return st;
+  if (n < 0) return bad_arg(h, 3, "n < 0");
+  if (n > 0 && !hA) return bad_arg(h, 4, "hA is NULL");
+  if (ldha < (n > 1 ? n : 1)) return bad_arg(h, 5, "ldha < max(1, n)");
+  if (n > 0 && !dA) return bad_arg(h, 6, "dA is NULL");
+  if (lda < (n > 1 ? n : 1)) return bad_arg(h, 7, "lda < max(1, n)");
+  if (!d_info) return bad_arg(h, 8, "d_info is NULL");
+  cudaSetDevice(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  constexpr int kBlk = 128;                 // Fact::kColBlock
+  const int nblk = (n + kBlk - 1) / kBlk;
+  if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return set_err(h, HRP_ERR_CUDA, "hrp_potrf_host: copy stream");
+  while ((int)h->col_events.size() < nblk + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return set_err(h, HRP_ERR_CUDA, "hrp_potrf_host: events");
+    h->col_events.push_back(e);
+  }
+  // the copies start after the work queued on the caller's stream before this call (it may
+  // still use dA); block b carries rows [128 b, n) of columns [128 b, 128 b + 128)
+  cudaEvent_t fork = h->col_events[nblk];
+  cudaError_t e = cudaEventRecord(fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, fork, 0);
+  for (int b = 0; b < nblk && e == cudaSuccess; ++b) {
+    const int c0 = b * kBlk, nc = std::min(kBlk, n - c0);
+    e = cudaMemcpy2DAsync(dA + (size_t)c0 * lda + c0, (size_t)lda * sizeof(double), hA + (size_t)c0 * ldha + c0,
+                          (size_t)ldha * sizeof(double), (size_t)(n - c0) * sizeof(double), nc, cudaMemcpyHostToDevice,
+                          h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->col_events[b], h->copy_stream);
+  }
+  if (e != cudaSuccess) return cuda_status(h, e, "hrp_potrf_host: copies");
+  const std::vector<cudaEvent_t> ev(h->col_events.begin(), h->col_events.begin() + nblk);
+  return potrf_enqueue(h, tree, n, dA, lda, d_info, s, &ev);
 }
 
 hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda, int* info, void* stream) {

@@ -27,7 +27,7 @@ STATUS = {0: "HRP_OK", 1: "HRP_ERR_INVALID_ARG", 2: "HRP_ERR_NOT_SPD", 3: "HRP_E
 
 EXPORTED = [
     "hrp_create", "hrp_destroy", "hrp_last_arg", "hrp_last_error", "hrp_status_string",
-    "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrs",
+    "hrp_tree_parse", "hrp_tree_format", "hrp_potrf", "hrp_potrf_async", "hrp_potrf_host", "hrp_potrs",
     "hrp_posv", "hrp_backward_error", "hrp_set_timing", "hrp_get_timing", "hrp_last_launch_count",
     "hrp_potrs_noalloc", "hrp_potrf_batched", "hrp_potrs_batched", "hrp_posv_batched",
     "hrp_policy_features", "hrp_mlp_forward", "hrp_mlp_grad", "hrp_mlp_adam", "hrp_mlp_param_count",
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.hrp_tree_format.argtypes = [tp, ctypes.c_char_p, ctypes.c_size_t]
     L.hrp_potrf.argtypes = [vp, tp, c_int, vp, c_int, ip, vp]
     L.hrp_potrf_async.argtypes = [vp, tp, c_int, vp, c_int, vp, vp]
+    L.hrp_potrf_host.argtypes = [vp, tp, c_int, vp, c_int, vp, c_int, vp, vp]
     L.hrp_potrs.argtypes = [vp, c_int, c_int, vp, c_int, vp, c_int, vp]
     L.hrp_posv.argtypes = [vp, tp, c_int, c_int, vp, c_int, vp, c_int, vp, c_int, c_int, c_double, ip, dp, ip, ip, vp]
     L.hrp_backward_error.argtypes = [vp, c_int, vp, c_int, vp, c_int, dp, vp]
@@ -256,6 +257,14 @@ class Handle:
         n = A.shape[0] if n is None else n
         st = self._lib.hrp_potrf_async(self._h, ctypes.byref(tree), n, _ptr(A), A.shape[1], _ptr(d_info),
                                        _stream(stream))
+        self._check(st)
+
+    def potrf_host(self, tree: Tree, hA, A, d_info, n: int | None = None, stream=None) -> None:
+        """hrp_potrf_host: hA a column-major (n, ldha) float64 CPU tensor (page-locked for the
+        overlap), A the column-major (n, lda) CUDA tensor that receives its lower triangle and L."""
+        n = A.shape[0] if n is None else n
+        st = self._lib.hrp_potrf_host(self._h, ctypes.byref(tree), n, _ptr(hA), hA.shape[1], _ptr(A), A.shape[1],
+                                      _ptr(d_info), _stream(stream))
         self._check(st)
 
     # hrp_potrs: L (n, ldl) column-major factor, B (nrhs, ldb) column-major, overwritten with X

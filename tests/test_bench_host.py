@@ -6,6 +6,7 @@ import os
 import sys
 import time
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -130,3 +131,10 @@ def test_leaf_traffic_is_keyed_to_the_kernel_code(tmp_path):
     assert bench.device_code_sha1(str(src), "cudaError_t launch_k(") == a
     src.write_text("__global__ void k() { int x; }\n\ncudaError_t launch_k() { return 1; }\n")
     assert bench.device_code_sha1(str(src), "cudaError_t launch_k(") != a
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 300, 1000])
+def test_host_lower_bytes_counts_the_transferred_entries(n):
+    # hrp_potrf_host transfers entry (i, j) when i >= 128 floor(j / 128)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    assert bench.host_lower_bytes(n) == 8 * int(np.count_nonzero(i >= 128 * (j // 128)))
