@@ -254,6 +254,15 @@ hrp_status hrp_set_timing(hrp_handle* h, int enable);
 int hrp_get_timing(hrp_handle* h, double* out, int n);
 
 /*
+ * The launches of the last factorization in timing mode, in enqueue order, four doubles each:
+ * kernel class (as hrp_get_timing), stream (0: the critical stream, d: the lookahead side
+ * stream of recursion depth d), start and end in milliseconds from the first launch's start
+ * event.  Returns the number of doubles written (a multiple of 4, <= n).  The events around
+ * every launch add a few microseconds each, so gaps read from it are upper bounds.
+ */
+int hrp_get_timeline(hrp_handle* h, double* out, int n);
+
+/*
  * Lookahead (on by default): after a node's A11 is factored, the rows of its A21 that the
  * next diagonal block needs, and that block's share of the SYRK, run on the handle's
  * critical stream (highest priority); the remaining TRSM rows and SYRK blocks run on a side

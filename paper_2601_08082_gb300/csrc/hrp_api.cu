@@ -68,6 +68,7 @@ struct hrp_handle_s {
   bool timing = false;
   // per-kernel-class timing of the last factorization (timing mode only)
   double cls_ms[hrp::kNumClasses] = {0};
+  std::vector<double> timeline;   // timing mode: class, stream, start ms, end ms per launch
   double cls_launches[hrp::kNumClasses] = {0};
   double cls_flops[hrp::kNumClasses] = {0};
   std::vector<cudaEvent_t> events;
@@ -273,7 +274,7 @@ struct Fact {
   const std::vector<cudaEvent_t>* col_ev = nullptr;
   std::map<cudaStream_t, int> col_waited;
   // timing mode: an event pair around every launch, tagged with its class and flops
-  struct Rec { int cls; size_t ev; double flops; };
+  struct Rec { int cls; size_t ev; double flops; int sidx; };
   std::vector<Rec> recs;
   int cur_cls = CLS_OTHER;
   double cur_flops = 0.0;
@@ -310,7 +311,11 @@ struct Fact {
     if (h->timing && began) {
       cudaEvent_t e1 = event(ev_next + 1);
       if (e1 && cudaEventRecord(e1, s) == cudaSuccess) {
-        recs.push_back({cur_cls, ev_next, cur_flops});
+        int sidx = 0;
+        if (la && side)
+          for (size_t q = 0; q < side->size(); ++q)
+            if ((*side)[q] == s) sidx = (int)q;
+        recs.push_back({cur_cls, ev_next, cur_flops, sidx});
         ev_next += 2;
       }
     }
@@ -540,7 +545,16 @@ hrp_status cuda_status(hrp_handle* h, cudaError_t e, const char* where) {
 
 void collect_timing(hrp_handle* h, const Fact& f) {
   for (int c = 0; c < kNumClasses; ++c) h->cls_ms[c] = h->cls_launches[c] = h->cls_flops[c] = 0.0;
+  h->timeline.clear();
   for (const auto& r : f.recs) {
+    float t0 = 0.f, t1 = 0.f;
+    if (cudaEventElapsedTime(&t0, h->events[f.recs[0].ev], h->events[r.ev]) == cudaSuccess &&
+        cudaEventElapsedTime(&t1, h->events[f.recs[0].ev], h->events[r.ev + 1]) == cudaSuccess) {
+      h->timeline.push_back(r.cls);
+      h->timeline.push_back(r.sidx);
+      h->timeline.push_back(t0);
+      h->timeline.push_back(t1);
+    }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->events[r.ev], h->events[r.ev + 1]) == cudaSuccess) h->cls_ms[r.cls] += ms;
     h->cls_launches[r.cls] += 1.0;
@@ -1424,6 +1438,13 @@ int hrp_get_timing(hrp_handle* h, double* out, int n) {
     out[w++] = h->cls_launches[c];
     out[w++] = h->cls_flops[c];
   }
+  return w;
+}
+
+int hrp_get_timeline(hrp_handle* h, double* out, int n) {
+  if (!h || !out) return 0;
+  const int w = std::min(n - n % 4, (int)h->timeline.size());
+  for (int i = 0; i < w; ++i) out[i] = h->timeline[i];
   return w;
 }
 

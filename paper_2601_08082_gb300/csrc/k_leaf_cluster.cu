@@ -848,22 +848,40 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
       // gathered index of L_IK: row I starts at (I-J-1)(I-J)/2; W_II follows the nl L tiles
       for (int e = tid; e < kTileD; e += kCThreads) sm.wcol[J][e] = sm.gat[nl][e];
       __syncthreads();
+      // right-looking: once W_KJ is final, every later row block I adds L_IK W_KJ to its sum
+      // tmp_I (slot I - J - 1 of acc; the terms arrive in the order K = J, J + 1, .., as a
+      // left-looking sum would take them), and W_{K+1,J} = -W_{K+1,K+1} tmp_{K+1}: a step
+      // costs one tile product on the chain instead of I - J of them
       const int r = tid >> 4, q = tid & 15;
-      for (int I = J + 1; I < NT; ++I) {
-        // tmp = sum_K L_IK W_KJ ; thread: row r, column q
-        float s0 = 0.f;
-        for (int K = J; K < I; ++K) {
-          const float* L = sm.gat[(I - J - 1) * (I - J) / 2 + (K - J)];
+      float acc[kCL - 1];
 #pragma unroll
-          for (int k = 0; k < kTS; ++k) s0 = fmaf(L[r * kTLD + k], sm.wcol[K][k * kTLD + q], s0);
+      for (int t = 0; t < kCL - 1; ++t) acc[t] = 0.f;
+      for (int K = J; K + 1 < NT; ++K) {
+        float wk[kTS];                                   // column q of W_KJ, read once per step
+#pragma unroll
+        for (int k = 0; k < kTS; ++k) wk[k] = sm.wcol[K][k * kTLD + q];
+#pragma unroll
+        for (int t = 0; t < kCL - 1; ++t) {
+          const int I = J + 1 + t;
+          if (I > K && I < NT) {
+            const float* L = sm.gat[(I - J - 1) * (I - J) / 2 + (K - J)];
+#pragma unroll
+            for (int k = 0; k < kTS; ++k) acc[t] = fmaf(L[r * kTLD + k], wk[k], acc[t]);
+            if (I == K + 1) sm.tmp[r * kTLD + q] = acc[t];
+          }
         }
-        sm.tmp[r * kTLD + q] = s0;
         __syncthreads();
-        const float* Wi = sm.gat[nl + (I - J)];
+        const float* Wi = sm.gat[nl + (K + 1 - J)];
+        float wi[kTS], tq[kTS];
+#pragma unroll
+        for (int mm = 0; mm < kTS; ++mm) {
+          wi[mm] = Wi[r * kTLD + mm];
+          tq[mm] = sm.tmp[mm * kTLD + q];
+        }
         float o0 = 0.f;
 #pragma unroll
-        for (int mm = 0; mm < kTS; ++mm) o0 = fmaf(-Wi[r * kTLD + mm], sm.tmp[mm * kTLD + q], o0);
-        sm.wcol[I][r * kTLD + q] = o0;
+        for (int mm = 0; mm < kTS; ++mm) o0 = fmaf(-wi[mm], tq[mm], o0);
+        sm.wcol[K + 1][r * kTLD + q] = o0;
         __syncthreads();
       }
       // write column block J of W (column-major, zeros above the diagonal)

@@ -35,7 +35,7 @@ EXPORTED = [
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
     "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
     "hrp_last_inner_iterations", "hrp_autotune_orders", "hrp_set_batched_mode", "hrp_set_scaling",
-    "hrp_set_fp32_split", "hrp_set_f8_gemm", "hrp_set_leaf_chain",
+    "hrp_set_fp32_split", "hrp_set_f8_gemm", "hrp_set_leaf_chain", "hrp_get_timeline",
 ]
 
 
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.hrp_set_fp32_split.argtypes = [vp, c_int]
     L.hrp_set_f8_gemm.argtypes = [vp, c_int]
     L.hrp_set_leaf_chain.argtypes = [vp, c_int]
+    L.hrp_get_timeline.argtypes = [vp, vp, c_int]
     L.hrp_set_refinement.argtypes = [vp, c_int, c_int, c_double]
     L.hrp_last_inner_iterations.argtypes = [vp]
     L.hrp_last_inner_iterations.restype = ctypes.c_longlong
@@ -339,6 +340,13 @@ class Handle:
             self._lib.hrp_set_timing(self._h, 0)
         return {name: {"ms": buf[3 * c], "launches": int(buf[3 * c + 1]), "flops": buf[3 * c + 2]}
                 for c, name in enumerate(self.TIMING_CLASSES)}
+
+    def timeline(self) -> np.ndarray:
+        """hrp_get_timeline after timing(): one row per launch (class, stream, start ms, end ms)."""
+        cap = 4 * 200000
+        buf = (ctypes.c_double * cap)()
+        w = self._lib.hrp_get_timeline(self._h, buf, cap)
+        return np.array(buf[:w], dtype=np.float64).reshape(-1, 4)
 
     def policy_features(self, A, lanczos_steps: int = 10, n: int | None = None, stream=None) -> np.ndarray:
         n = A.shape[0] if n is None else n
