@@ -783,7 +783,15 @@ def main():
         hostX = torch.empty_like(hostB).pin_memory()
         dA = torch.empty_like(A0[0])
         dB = torch.empty_like(B[0])
+        # this box's pinned host-to-device rate, one whole-matrix copy (context for e2e)
         torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dA.copy_(hostA[0], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = dA.numel() * 8 / (a.elapsed_time(b) * 1e-3) / 1e9
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -797,7 +805,7 @@ def main():
         ems = a.elapsed_time(b)
         e2e = {"value": world * args.e2e_steps * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(host_lower_bytes(N) + dB.numel() * 8), "d2h_bytes_per_step": int(dB.numel() * 8),
-               "ms_per_step": ems / args.e2e_steps}
+               "ms_per_step": ems / args.e2e_steps, "h2d_gbs_box": h2d_gbs}
 
     barrier()
     if rank == 0:
