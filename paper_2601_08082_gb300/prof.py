@@ -15,6 +15,37 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def print_timeline(tl) -> None:
+    """Leaves on the critical stream (stream 0) and, grouped by their sequence of kernel
+    classes, the launches between consecutive leaves."""
+    import numpy as np
+
+    names = ["leaf", "ltrsm", "tc", "simt", "other"]
+    crit = tl[tl[:, 1] == 0]
+    leaf = crit[crit[:, 0] == 0]
+    print(f"launches {len(tl)} (critical stream {len(crit)}), span {tl[:, 3].max():.3f} ms")
+    print(f"leaves: {len(leaf)}, {np.sum(leaf[:, 3] - leaf[:, 2]):.3f} ms, "
+          f"{np.mean(leaf[:, 3] - leaf[:, 2]) * 1e3:.1f} us each")
+    starts, ends = leaf[:, 2], leaf[:, 3]
+    gaps = starts[1:] - ends[:-1]
+    print(f"between consecutive leaves: {gaps.sum():.3f} ms in {len(gaps)} gaps")
+    groups = {}
+    for k in range(len(gaps)):
+        sel = crit[(crit[:, 2] >= ends[k]) & (crit[:, 3] <= starts[k + 1])]
+        key = " ".join(names[int(c)] for c in sel[:, 0])
+        g = groups.setdefault(key, [0, 0.0, 0.0])
+        g[0] += 1
+        g[1] += gaps[k] * 1e3
+        g[2] += float(np.sum(sel[:, 3] - sel[:, 2])) * 1e3
+    for key, (cnt, gap_us, in_us) in sorted(groups.items(), key=lambda x: len(x[0])):
+        nk = len(key.split()) if key else 0
+        print(f"  {cnt:3d} gaps of {nk:2d} kernels: mean gap {gap_us / cnt:7.1f} us, in kernels {in_us / cnt:7.1f} us")
+    for c in range(5):
+        sel = crit[crit[:, 0] == c]
+        if len(sel):
+            print(f"  critical {names[c]}: {len(sel)} launches, {np.mean(sel[:, 3] - sel[:, 2]) * 1e3:.1f} us each")
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=8192)
@@ -27,6 +58,8 @@ def main() -> int:
                     help="draw the matrix on the device (seeded torch generator) instead of the host generator")
     ap.add_argument("--timing", action="store_true",
                     help="print per-kernel-class device time of the last factorization (event timing mode)")
+    ap.add_argument("--timeline", action="store_true",
+                    help="print the critical stream's leaves and the launches between them (event timing mode)")
     args = ap.parse_args()
 
     import torch
@@ -71,6 +104,9 @@ def main() -> int:
         classes = h.timing(tree, A0.clone())
         print(json.dumps({"n": args.n, "tree": args.tree, "leaf": args.leaf, "ms": e0.elapsed_time(e1),
                           "classes": classes}))
+    if args.timeline:
+        h.timing(tree, A0.clone())
+        print_timeline(h.timeline())
     print(f"{args.reps} factorizations of n={args.n} tree {args.tree}: {h.launch_count()} launches each")
     h.close()
     return 0
