@@ -41,8 +41,8 @@ FP64_MEASURED_TFLOPS = 1.20
 FP32_MEASURED_TFLOPS = 75.2
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture, reported
 # while the kernel's device code is the code captured: the source up to its launcher, hashed.
-LEAF_TRAFFIC = {"bytes": 163584, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "a8293fce89abc3f0cf9a49ee3ecae6243a8463ea"}
+LEAF_TRAFFIC = {"bytes": 163072, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "3fcb53634d49a05aa792a80807a6f51416a8e543"}
 # The leaves of trees with a level below FP64 run in double-float arithmetic on the FP32 pipe:
 # one double-float multiply-add (the Dot2 accumulation step of the tile updates) is 12 FP32
 # instructions, so FP64-class work done that way peaks at the FP32 rate / 12.
@@ -590,7 +590,7 @@ def run_fp8posv(args, rank, world):
             "unit": "TFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "e4m3 (in f16 storage) / f16 (fp32 acc) / f32 / f64", "data": "synthetic (device generator)",
+            "dtype": "e4m3 (block-scaled MMA, fp32 acc) / f16 (fp32 acc) / f32 / f64", "data": "synthetic (device generator)",
             "config": {"workload": f"n={n} rho={rho} tree {spec}, factor; posv with {nrhs} RHS to 1e-12",
                        "n": n, "tree": spec, "leaf": 128, "nrhs": nrhs,
                        "l2": "inputs larger than L2 (8.6 GB matrix, fresh copy per step)"},
