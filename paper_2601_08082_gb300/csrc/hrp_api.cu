@@ -257,6 +257,10 @@ struct Fact {
   int ldh = 0;
   bool tc;
   std::map<int, int> leaves;  // leaf offset -> order (blocks with an FP32 inverse)
+  // launches so far on each stream, and for each leaf offset the stream and number of the
+  // launch that wrote its FP32 inverse
+  std::map<cudaStream_t, long long> launch_no;
+  std::map<int, std::pair<cudaStream_t, long long>> inv_by;
   cudaError_t err = cudaSuccess;
   long long launches = 0;
   // lookahead (see potrf): s is the stream of the next launch, main_s the critical stream;
@@ -307,6 +311,7 @@ struct Fact {
   }
   void chk(cudaError_t e) {
     ++launches;
+    ++launch_no[s];
     if (e != cudaSuccess && err == cudaSuccess) err = e;
     if (h->timing && began) {
       cudaEvent_t e1 = event(ev_next + 1);
@@ -334,6 +339,7 @@ struct Fact {
     if (w32) {
       W = w32 + (size_t)off * 128;
       leaves[off] = nb;
+      inv_by[off] = {s, launch_no[s] + 1};
     }
     begin(CLS_POTRF, (double)nb * nb * nb / 3.0);
     chk(launch_potrf_leaf(A + (size_t)off * lda + off, lda, nb, off, p == HRP_F64, p == HRP_F16, W, 128, info, h->d_err, s));
@@ -355,8 +361,13 @@ struct Fact {
     }
     auto it = leaves.find(c0);
     if (w32 && it != leaves.end() && it->second == nc) {
+      // the inverse is complete when this launch starts unless the previous launch on this
+      // stream wrote it (a leaf on another stream was awaited through an event, which starts
+      // the next launch here without programmatic overlap)
+      const auto pr = inv_by.find(c0);
+      const bool w_done = pr != inv_by.end() && (pr->second.first != s || pr->second.second < launch_no[s]);
       chk(launch_trsm_leaf32(Ab, lda, r0, m, c0, nc, w32 + (size_t)c0 * 128, 128, sh, lds, shadow32, ld32, info,
-                             h->d_err, s));
+                             h->d_err, s, w_done));
     } else {
       chk(launch_trsm_leaf32_subst(Ab, lda, r0, m, c0, nc, sh, lds, shadow32, ld32, info, h->d_err, s));
     }

@@ -95,9 +95,11 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
                                cudaStream_t s, const double* Lm = nullptr, int ldl = 0);
 // Same in FP32 using the precomputed FP32 inverse W (nc x nc lower, ldw) of the block:
 // X = fl32(B) * W^T, result stored in FP64.
+// w_done: W was written by a kernel that completed before the previous launch on s started
+// (the kernel may then read it before waiting for that launch)
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
-                               const int* info, unsigned* err, cudaStream_t s);
+                               const int* info, unsigned* err, cudaStream_t s, bool w_done = false);
 // FP32 substitution variant (no inverse), for blocks whose inverse is not available.
 cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, int nc,
                                      __half* shadow16, int lds, float* shadow32, int ld32, const int* info,

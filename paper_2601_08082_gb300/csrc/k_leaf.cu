@@ -338,34 +338,44 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // (1 x gridDim.y) and meet at a cluster barrier after all of them have staged B and before
 // any writes X in place.  Every CTA reaches it: the only early exit reads `info`, which no
 // kernel writes while this one runs, so all CTAs see the same value.
+// w_done: W was written by a kernel that completed before the previous launch on this stream
+// started (the host knows), so it is staged before the wait for that launch, under its tail.
 template <int CPL>
 __global__ void __launch_bounds__(kT32Threads)
 trsm_inv32_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
                   const float* __restrict__ W, int ldw, __half* __restrict__ S, int lds,
-                  float* __restrict__ S32, int ld32, const int* __restrict__ info, unsigned* __restrict__ err) {
-  pdl_wait();
-  pdl_trigger();
+                  float* __restrict__ S32, int ld32, const int* __restrict__ info, unsigned* __restrict__ err,
+                  int w_done) {
   constexpr int C = 32 * CPL;
   constexpr int WLD = C + 4;                               // 16-byte rows
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (*(volatile const int*)info != INT_MAX) return;
   const int jc0 = blockIdx.y * C;                          // < nc: gridDim.y = ceil(nc / C)
   float* Ws = reinterpret_cast<float*>(smem_raw);          // Ws[k * WLD + jj] = W(jc0 + jj, k)
   float* Bs = Ws + 128 * WLD;                              // Bs[r * 132 + k] = B(row0 + r, k); later X
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kT32Rows;
   const bool vecw = (nc == 128) && ((ldw & 3) == 0) && ((reinterpret_cast<uintptr_t>(W) & 15) == 0);
-  if (vecw) {
-    for (int e = tid; e < 128 * (C / 4); e += kT32Threads) {
-      const int k = e / (C / 4), q = e % (C / 4);
-      cp_async16(Ws + k * WLD + 4 * q, W + (size_t)k * ldw + jc0 + 4 * q);
+  auto stage_w = [&]() {
+    if (vecw) {
+      for (int e = tid; e < 128 * (C / 4); e += kT32Threads) {
+        const int k = e / (C / 4), q = e % (C / 4);
+        cp_async16(Ws + k * WLD + 4 * q, W + (size_t)k * ldw + jc0 + 4 * q);
+      }
+    } else {
+      for (int e = tid; e < 128 * C; e += kT32Threads) {
+        const int k = e / C, jj = e % C, j = jc0 + jj;
+        Ws[k * WLD + jj] = (j < nc && k < nc) ? W[(size_t)k * ldw + j] : 0.f;
+      }
     }
-  } else {
-    for (int e = tid; e < 128 * C; e += kT32Threads) {
-      const int k = e / C, jj = e % C, j = jc0 + jj;
-      Ws[k * WLD + jj] = (j < nc && k < nc) ? W[(size_t)k * ldw + j] : 0.f;
-    }
+  };
+  if (w_done) stage_w();
+  pdl_wait();
+  pdl_trigger();
+  if (*(volatile const int*)info != INT_MAX) {
+    cp_async_wait_all();
+    return;
   }
+  if (!w_done) stage_w();
   // B: 8 values per thread, all loads in flight before the conversions
   double bv[8];
 #pragma unroll
@@ -519,7 +529,7 @@ cudaError_t launch_trsm_leaf32_subst(double* A, int ld, int r0, int m, int c0, i
 
 cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
                                const float* W, int ldw, __half* shadow16, int lds, float* shadow32, int ld32,
-                               const int* info, unsigned* err, cudaStream_t s) {
+                               const int* info, unsigned* err, cudaStream_t s, bool w_done) {
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 128) return cudaErrorInvalidValue;
   const int sms = device_sm_count();
@@ -570,13 +580,13 @@ cudaError_t launch_trsm_leaf32(double* A, int ld, int r0, int m, int c0, int nc,
   cudaError_t e;
   if (cpl == 4)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<4>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info, err);
+                           info, err, w_done ? 1 : 0);
   else if (cpl == 2)
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<2>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info, err);
+                           info, err, w_done ? 1 : 0);
   else
     e = cudaLaunchKernelEx(&cfg, trsm_inv32_kernel<1>, A, ld, r0, m, c0, nc, W, ldw, shadow16, lds, shadow32, ld32,
-                           info, err);
+                           info, err, w_done ? 1 : 0);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
