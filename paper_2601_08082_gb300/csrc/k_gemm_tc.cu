@@ -1,8 +1,8 @@
 // FP16 tensor-core GEMM for the low-precision off-diagonal levels (Sec. 3.3):
 // C_master -= scale * X Y^T with X, Y read from the row-major FP16 shadow of L by TMA,
 // multiplied by tcgen05.mma (kind::f16, FP32 accumulation in TMEM) and applied to the
-// FP64 master in the epilogue.  This is the "GemmEx" update of Alg. 2 line "B2 <- B2 -
-// B1 L21^T" and Alg. 3 line "C21 <- beta C21 + alpha A2 A1^T" at an FP16 level; with
+// FP64 master in the epilogue.  This is Alg. 2's GEMM update of B2 by B1 L21^T and Alg. 3's
+// update of C21 by A2 A1^T at an FP16 level; with
 // `lower` it is the leaf SYRK of Alg. 3 (entries above the diagonal are skipped, and
 // tiles entirely above it are never computed).
 //
