@@ -664,12 +664,8 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
   __syncthreads();
   int s2 = 0;
   if (!skip) {
-    if (kDF) {
-      s2 = leaf_scale(A, ld, n, sm, tid);
-      if (s2 == INT_MIN) return kFallback;     // every CTA read the same diagonal
-    }
-    // load the owned tiles (all loads issued before the first store); rows / columns past n
-    // are the identity
+    // load the owned tiles (all loads issued before the first store, and before the leaf's
+    // scale is known: only their conversion needs it); rows / columns past n are the identity
     // NT <= 8, so this CTA owns at most one tile per block column J: row (rank - J) mod 8
     // one entry of each owned tile per thread: (ii, jj) = (tid % 16, tid / 16)
     const int jj = tid >> 4, ii = tid & 15;          // column-major walk: coalesced reads
@@ -684,6 +680,10 @@ __device__ int leaf_body(double* __restrict__ A, int ld, int n, int col0, float*
         else x = (gi == gj) ? 1.0 : 0.0;
       }
       v[J] = x;
+    }
+    if (kDF) {
+      s2 = leaf_scale(A, ld, n, sm, tid);
+      if (s2 == INT_MIN) return kFallback;     // every CTA read the same diagonal
     }
     int lbad = 0;
 #pragma unroll
