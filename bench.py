@@ -41,8 +41,8 @@ FP64_MEASURED_TFLOPS = 1.20
 FP32_MEASURED_TFLOPS = 75.2
 # DRAM bytes (read + write) per launch of the leaf POTRF kernel from one ncu capture, reported
 # while the kernel's device code is the code captured: the source up to its launcher, hashed.
-LEAF_TRAFFIC = {"bytes": 163072, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
-                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "3fcb53634d49a05aa792a80807a6f51416a8e543"}
+LEAF_TRAFFIC = {"bytes": 162176, "source": "paper_2601_08082_gb300/csrc/k_leaf_cluster.cu",
+                "until": "cudaError_t launch_potrf_leaf_cluster(", "sha1": "c1833c238d6246960dce60c58aa7a6d40dfe023a"}
 # The leaves of trees with a level below FP64 run in double-float arithmetic on the FP32 pipe:
 # one double-float multiply-add (the Dot2 accumulation step of the tile updates) is 12 FP32
 # instructions, so FP64-class work done that way peaks at the FP32 rate / 12.

@@ -104,3 +104,31 @@ def test_host_input_argument_errors(hrp_mod):
                               vp(info.data_ptr()), s) == 1
     assert lib.hrp_last_arg(h._h) == -4
     h.close()
+
+
+def test_host_input_with_padded_leading_dimensions(hrp_mod):
+    # ldha and lda larger than n: the copies walk both pitches
+    import torch
+    hrp = hrp_mod
+    n, ldh, ldd = 700, 731, 760
+    A = dominant_spd(n, 1.5, seed_for(0, 952))
+    h = hrp.Handle(0)
+    try:
+        tree = hrp.tree_parse("[F16,F32|F64@128]", leaf=128)
+        info = torch.zeros(2, dtype=torch.int32, device="cuda")
+        hA = torch.zeros((n, ldh), dtype=torch.float64)
+        hA[:, :n] = hrp.colmajor(A)
+        hA = hA.pin_memory()
+        Ah = torch.full((n, ldd), 7.0, dtype=torch.float64, device="cuda")
+        h.potrf_host(tree, hA, Ah, info[1:2], n=n)
+        Ad = torch.zeros((n, ldd), dtype=torch.float64, device="cuda")
+        Ad[:, :n] = hrp.colmajor(A).cuda()
+        h.potrf_async(tree, Ad, info[0:1], n=n)
+        torch.cuda.synchronize()
+        assert [int(v) for v in info.cpu()] == [0, 0]
+        Ld, Lh = hrp.from_colmajor(Ad)[:n, :n], hrp.from_colmajor(Ah)[:n, :n]
+        il = np.tril_indices(n)
+        assert np.array_equal(Lh[il], Ld[il])
+        assert torch.all(Ah[:, n:] == 7.0)                 # padding rows of every column untouched
+    finally:
+        h.close()
