@@ -161,9 +161,9 @@ hrp_status hrp_posv(hrp_handle* h, const hrp_tree* tree, int n, int nrhs,
  * the call; every copy has completed before the work this call queues on `stream` does.
  * Entries of dA above the 128 x 128 diagonal blocks are not written.  hA should be
  * page-locked (cudaHostAlloc or cudaHostRegister): from pageable memory the copies are staged
- * through the driver and overlap nothing.  hA must stay unchanged until the copies are done
- * (synchronize `stream`).  Otherwise as hrp_potrf_async: *d_info (device) as in hrp_potrf,
- * no synchronization.
+ * through the driver and overlap nothing.  hA must stay unchanged until the copies are done:
+ * synchronizing `stream` covers them, also after an error return.  Otherwise as
+ * hrp_potrf_async: *d_info (device) as in hrp_potrf, no synchronization.
  */
 hrp_status hrp_potrf_host(hrp_handle* h, const hrp_tree* tree, int n, const double* hA, int ldha, double* dA,
                           int lda, int* d_info, void* stream);

@@ -960,7 +960,11 @@ hrp_status hrp_potrf_host(hrp_handle* h, const hrp_tree* tree, int n, const doub
   }
   if (e != cudaSuccess) return cuda_status(h, e, "hrp_potrf_host: copies");
   const std::vector<cudaEvent_t> ev(h->col_events.begin(), h->col_events.begin() + nblk);
-  return potrf_enqueue(h, tree, n, dA, lda, d_info, s, &ev);
+  st = potrf_enqueue(h, tree, n, dA, lda, d_info, s, &ev);
+  // on an error the factorization may have enqueued nothing that waits for the copies: the
+  // caller's stream still does, so synchronizing it covers every use of hA and dA
+  if (st != HRP_OK && nblk > 0) cudaStreamWaitEvent(s, ev.back(), 0);
+  return st;
 }
 
 hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int lda, int* info, void* stream) {
