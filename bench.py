@@ -143,6 +143,14 @@ class Replicas:
     def sum(self, x):
         return self._reduce(x, self.dist.ReduceOp.SUM if self.dist is not None else None)
 
+    def gather_objects(self, obj):
+        """Every rank's picklable obj, in rank order (a one-element list on one rank)."""
+        if self.dist is None:
+            return [obj]
+        out = [None] * self.world
+        self.dist.all_gather_object(out, obj)
+        return out
+
     def close(self):
         if self.dist is not None:
             self.dist.destroy_process_group()
@@ -608,6 +616,101 @@ def run_fp8posv(args, rank, world):
     return 0
 
 
+def paired_ratio_ci(t_a, t_b, reps=2000, seed=7):
+    """Mean of t_a / mean of t_b and a 95% bootstrap interval (pairs resampled together)."""
+    import numpy as np
+    a, b = np.asarray(t_a, dtype=np.float64), np.asarray(t_b, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, len(a), size=(reps, len(a)))
+    boot = a[idx].mean(axis=1) / b[idx].mean(axis=1)
+    return float(a.mean() / b.mean()), float(np.quantile(boot, 0.025)), float(np.quantile(boot, 0.975))
+
+
+def run_policy(args, rank, world):
+    """The learned precision-tree policy on held-out matrices of its training distribution
+    (another generator seed): for each matrix, hrp_posv with tree = NULL (the library runs the
+    feature pass, the network and its order gate, then the solve) against hrp_posv with the
+    fixed fallback tree.  Reports the time ratio with a bootstrap interval and the failure rate."""
+    import json as _json
+
+    import numpy as np
+    import torch
+
+    import paper_2601_08082_gb300 as hrp
+    from paper_2601_08082_gb300 import train_policy as tp
+    from synth import rhs, seed_for
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    h = hrp.Handle(local)
+    weights = os.path.join(ROOT, "paper_2601_08082_gb300", "policy_weights.json")
+    h.policy_load(weights)
+    with open(weights) as f:
+        gate = _json.load(f).get("min_n", [0])[0]
+    fb = hrp.policy_tree(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    k = 0
+    rows = []
+    for i in range(args.policy_matrices * world):
+        if i % world != rank:
+            continue
+        A, meta = tp.make_matrix(i, 9999, torch)
+        A = A.contiguous()
+        n = meta["n"]
+        B = hrp.colmajor(rhs(n, 1, seed_for(7, 100 + i))).cuda()
+        res = {}
+        for name, tree in (("policy", None), ("fallback", fb)):
+            X = torch.zeros_like(B)
+            out, t = timed(lambda: h.posv(tree, A, B, X, tol=1e-12))
+            res[name] = (t, int(out["status"]), int(out.get("used_fallback", 0)))
+            if tree is None:
+                k = int(h.last_policy_choice())
+        rows.append({"n": n, "kind": meta["kind"], "pick": k, "t_policy": res["policy"][0],
+                     "t_fallback": res["fallback"][0], "ok_policy": res["policy"][1] == 0,
+                     "ok_fallback": res["fallback"][1] == 0, "policy_refactored": res["policy"][2]})
+        del A
+    gathered = reps.gather_objects(rows)
+    if rank == 0:
+        allr = [r for part in gathered for r in part]
+        t_pol = [r["t_policy"] for r in allr]
+        t_fb = [r["t_fallback"] for r in allr]
+        ratio, lo, hi = paired_ratio_ci(t_pol, t_fb)
+        line = {"metric": "policy POSV time (features + solve) / fixed-fallback POSV time, held-out matrices",
+                "value": ratio, "unit": "ratio", "n_gpus": world, "steps": len(allr), "warmup": 0,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16 / f32 / f64 trees",
+                "data": "synthetic (device generator, held-out seed)",
+                "config": {"workload": "learned policy on the training distribution: Gram G G^T/k + alpha I and "
+                                       "rho-dominant matrices, n in {1024, 2048, 4096, 8192}, 1 RHS, POSV to 1e-12",
+                           "matrices": len(allr)},
+                "ratio_ci95": [lo, hi],
+                "speedup": 1.0 / ratio,
+                "failures_policy": sum(not r["ok_policy"] for r in allr),
+                "failures_fallback": sum(not r["ok_fallback"] for r in allr),
+                "policy_refactored_with_fallback": sum(r["policy_refactored"] != 0 for r in allr),
+                "order_gate": gate,
+                "picks": {str(k): sum(r["pick"] == k for r in allr) for k in range(8)},
+                "by_n": {str(nn): {"matrices": sum(r["n"] == nn for r in allr),
+                                   "ratio": (float(np.mean([r["t_policy"] for r in allr if r["n"] == nn]) /
+                                                   np.mean([r["t_fallback"] for r in allr if r["n"] == nn]))
+                                             if any(r["n"] == nn for r in allr) else None)}
+                         for nn in (1024, 2048, 4096, 8192)}}
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,7 +720,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768", "blas3"])
+    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768", "blas3", "policy"])
+    ap.add_argument("--policy-matrices", type=int, default=48, help="held-out matrices per rank of the policy workload")
     ap.add_argument("--blas3-n", type=int, default=8192, help="order of the blas3 workload")
     ap.add_argument("--n3", type=int, default=32768, help="order of the fp8posv32768 workload")
     ap.add_argument("--batch", type=int, default=512)
@@ -635,6 +739,8 @@ def main():
         return run_fp8posv(args, rank, world)
     if args.workload == "blas3":
         return run_blas3(args, rank, world)
+    if args.workload == "policy":
+        return run_policy(args, rank, world)
 
     import numpy as np
     import torch

@@ -362,8 +362,12 @@ hrp_status hrp_set_batched_mode(hrp_handle* h, int mode);
  *   (mean[12], scale[12]).
  * hrp_policy_load: the same from a file written by train_policy.py (JSON, format
  *   "hrp-policy-v1": "trees" must be this library's 8 candidate trees in order, "params"
- *   5512 numbers, "mean" and "scale" 12 each); HRP_ERR_INVALID_ARG (with hrp_last_error)
- *   when the file is missing or does not match.
+ *   5512 numbers, "mean" and "scale" 12 each, optionally "min_n": [order] as for
+ *   hrp_policy_set_min_order); HRP_ERR_INVALID_ARG (with hrp_last_error) when the file is
+ *   missing or does not match.
+ * hrp_policy_set_min_order: systems of order n < n_min take the fallback tree (index 0) without
+ *   the feature pass, where the pass costs more than the policy saves (0, the default after
+ *   hrp_policy_set: every order asks the policy).
  * hrp_policy_predict: the predicted tree for host feat[12] into *out and its index into
  *   *index (either may be NULL, not both); HRP_ERR_INVALID_ARG when no policy is loaded.
  * hrp_last_policy_choice: the index hrp_posv chose last (-1 if a tree was given).
@@ -379,6 +383,7 @@ hrp_status hrp_mlp_adam(hrp_handle* h, float* d_params, const float* d_grad, flo
 int hrp_mlp_param_count(void);
 hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean, const float* scale);
 hrp_status hrp_policy_load(hrp_handle* h, const char* path);
+hrp_status hrp_policy_set_min_order(hrp_handle* h, int n_min);
 hrp_status hrp_policy_predict(hrp_handle* h, const float* feat, hrp_tree* out, int* index);
 hrp_status hrp_policy_tree(int index, hrp_tree* out);
 int hrp_last_policy_choice(const hrp_handle* h);

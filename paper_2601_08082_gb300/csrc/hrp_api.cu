@@ -84,6 +84,9 @@ struct hrp_handle_s {
   float* pio = nullptr;        // device, 12 inputs + 8 logits
   bool policy_set = false;
   int last_choice = -1;
+  // orders below this take the fallback tree without the feature pass (the pass would cost
+  // more than the policy saves there); 0 = every order asks the policy
+  int policy_min_n = 0;
   // autotuner: tuned tree and its median time by (precision list, inner region, trsm_compute)
   // and order n
   std::map<std::string, std::map<int, std::pair<hrp_tree, float>>> tune_cache;
@@ -730,7 +733,7 @@ hrp_status check_dev_err(hrp_handle* h, cudaStream_t s) {
 hrp_status policy_choose(hrp_handle* h, int n, const double* dA, int lda, bool no_f8, hrp_tree* out, int* idx,
                          void* stream) {
   int k = 0;
-  if (h->policy_set) {
+  if (h->policy_set && n >= h->policy_min_n) {
     float feat[12];
     hrp_status fs = hrp_policy_features(h, n, dA, lda, kPolicyLanczosSteps, feat, stream);
     if (fs != HRP_OK) return fs;
@@ -2063,6 +2066,7 @@ hrp_status hrp_policy_set(hrp_handle* h, const float* params, const float* mean,
   if (cudaMemcpy(h->policy, p.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess)
     return set_err(h, HRP_ERR_CUDA, "hrp_policy_set");
   h->policy_set = true;
+  h->policy_min_n = 0;
   return HRP_OK;
 }
 
@@ -2122,7 +2126,25 @@ hrp_status hrp_policy_load(hrp_handle* h, const char* path) {
     return set_err(h, HRP_ERR_INVALID_ARG, "%s: \"mean\" and \"scale\" must hold 12 numbers each", path);
   for (float v : scale)
     if (!(v > 0.f)) return set_err(h, HRP_ERR_INVALID_ARG, "%s: a scale is not positive", path);
-  return hrp_policy_set(h, params.data(), mean.data(), scale.data());
+  // optional "min_n": [order], the smallest order at which the policy paid for its features
+  std::vector<float> min_n;
+  int gate = 0;
+  if (json_numbers(text, "min_n", min_n)) {
+    if (min_n.size() != 1 || !(min_n[0] >= 0.f) || !(min_n[0] <= 2147483647.f))
+      return set_err(h, HRP_ERR_INVALID_ARG, "%s: \"min_n\" must hold one order >= 0", path);
+    gate = (int)min_n[0];
+  }
+  hrp_status st = hrp_policy_set(h, params.data(), mean.data(), scale.data());
+  if (st == HRP_OK) h->policy_min_n = gate;
+  return st;
+}
+
+hrp_status hrp_policy_set_min_order(hrp_handle* h, int n_min) {
+  if (!h) return HRP_ERR_INVALID_ARG;
+  h->last_arg = 0;
+  if (n_min < 0) return bad_arg(h, 2, "n_min < 0");
+  h->policy_min_n = n_min;
+  return HRP_OK;
 }
 
 int hrp_last_policy_choice(const hrp_handle* h) { return h ? h->last_choice : -1; }

@@ -35,7 +35,7 @@ EXPORTED = [
     "hrp_autotune_candidates", "hrp_autotune", "hrp_policy_load", "hrp_check", "hrp_set_wait_limit",
     "hrp_wait_selftest", "hrp_set_lookahead", "hrp_syrk", "hrp_trsm", "hrp_set_refinement",
     "hrp_last_inner_iterations", "hrp_autotune_orders", "hrp_set_batched_mode", "hrp_set_scaling",
-    "hrp_set_fp32_split", "hrp_set_f8_gemm", "hrp_set_leaf_chain", "hrp_get_timeline",
+    "hrp_set_fp32_split", "hrp_set_f8_gemm", "hrp_set_leaf_chain", "hrp_get_timeline", "hrp_policy_set_min_order",
 ]
 
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.hrp_set_f8_gemm.argtypes = [vp, c_int]
     L.hrp_set_leaf_chain.argtypes = [vp, c_int]
     L.hrp_get_timeline.argtypes = [vp, vp, c_int]
+    L.hrp_policy_set_min_order.argtypes = [vp, c_int]
     L.hrp_set_refinement.argtypes = [vp, c_int, c_int, c_double]
     L.hrp_last_inner_iterations.argtypes = [vp]
     L.hrp_last_inner_iterations.restype = ctypes.c_longlong
@@ -386,6 +387,10 @@ class Handle:
 
     def policy_load(self, path: str) -> None:
         self._check(self._lib.hrp_policy_load(self._h, os.fsencode(path)))
+
+    def policy_set_min_order(self, n_min: int) -> None:
+        """hrp_policy_set_min_order: orders below n_min take the fallback tree, no features."""
+        self._check(self._lib.hrp_policy_set_min_order(self._h, int(n_min)))
 
     def check(self, stream=None) -> int:
         """hrp_check: status of the device-side failures since the last synchronous call."""

@@ -12,8 +12,11 @@ too).  Label = the fastest tree whose solve converged; matrices no tree solves a
 
 Training: 80/10/10 split, inputs standardized with the training split's mean and scale,
 full-batch Adam on the GPU with the library's own kernels (hrp_mlp_grad, hrp_mlp_adam).
-The validation split picks the step with the best validation loss; the test split is
-reported.  Output: JSON with the parameters, the standardization, and the split metrics.
+The validation split picks the step with the best validation loss, and the order gate: the
+smallest order from which, at every order of the grid, the feature pass plus the picked
+tree's solve beat the fallback tree's solve on average ("min_n"; smaller systems take the
+fallback without the feature pass).  The test split is reported with the gate applied.
+Output: JSON with the parameters, the standardization, the gate and the split metrics.
 
     python -m paper_2601_08082_gb300.train_policy --samples 800 --out policy_weights.json
 """
@@ -58,14 +61,22 @@ def make_matrix(i: int, seed0: int, torch):
 
 
 def label_one(h, A, hrp, torch):
-    """features, per-tree posv times (inf where the solve did not converge).
-    A: symmetric (n, n) float64 CUDA tensor (its own transpose, so also column-major)."""
+    """features, per-tree posv times (inf where the solve did not converge), and the time of
+    the feature pass.  A: symmetric (n, n) float64 CUDA tensor (its own transpose, so also
+    column-major)."""
     import numpy as np
 
     from synth import rhs, seed_for
     n = A.shape[0]
     A = A.contiguous()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
     feat = h.policy_features(A, lanczos_steps=10)
+    f1.record()
+    torch.cuda.synchronize()
+    t_feat = f0.elapsed_time(f1)
     B = hrp.colmajor(rhs(n, 1, seed_for(5, 7))).cuda()
     X = torch.zeros_like(B)
     times = np.full(NTREES, np.inf)
@@ -80,7 +91,25 @@ def label_one(h, A, hrp, torch):
         torch.cuda.synchronize()
         if out["status"] == 0:
             times[t] = e0.elapsed_time(e1)
-    return feat, times
+    return feat, times, t_feat
+
+
+def order_gate(ns, t_feat, t_pick, t_fb):
+    """Smallest order from which the policy (feature pass + the picked tree) beats the fixed
+    fallback on average at every order of the grid, from matrices not used for training
+    (numpy arrays over the same matrices); 2^30 when it never does."""
+    import numpy as np
+    grid = sorted(set(int(n) for n in ns))
+    wins = {}
+    for n in grid:
+        sel = ns == n
+        wins[n] = bool(np.mean(t_feat[sel] + t_pick[sel]) < np.mean(t_fb[sel]))
+    gate = 1 << 30
+    for n in reversed(grid):
+        if not wins[n]:
+            break
+        gate = n
+    return gate, wins
 
 
 def train(h, hrp, torch, Xtr, ytr, Xva, yva, steps: int, lr: float, seed: int):
@@ -137,16 +166,19 @@ def main() -> int:
 
     h = hrp.Handle(0)
     t0 = time.time()
-    feats, times, meta = [], [], []
+    feats, times, meta, tfeat = [], [], [], []
     for i in range(args.samples):
         A, m = make_matrix(i, args.seed, torch)
-        f, t = label_one(h, A, hrp, torch)
+        f, t, tf = label_one(h, A, hrp, torch)
         del A
         feats.append(f)
         times.append(t)
         meta.append(m)
+        tfeat.append(tf)
     feats = np.array(feats, dtype=np.float64)
     times = np.array(times)
+    tfeat = np.array(tfeat)
+    orders = np.array([m["n"] for m in meta])
     ok = np.isfinite(times).any(axis=1)
     labels = np.where(ok, np.argmin(times, axis=1), -1)
     idx = np.nonzero(ok)[0]
@@ -160,21 +192,30 @@ def main() -> int:
                        args.lr, args.seed)
     params = best[1].cpu().numpy()
 
-    # held-out evaluation with the GPU forward pass
+    # the order gate from the validation split, then held-out evaluation with the GPU forward pass
     h.policy_set(params, mean, scale)
-    pred = np.array([h.policy_predict(feats[i]) for i in te])
+    pred_va = np.array([h.policy_predict(feats[i]) for i in va])
+    tp_va = np.where(np.isfinite(times[va, pred_va]), times[va, pred_va], 1e9)
+    tf_va = np.where(np.isfinite(times[va, 0]), times[va, 0], 1e9)
+    gate, wins = order_gate(orders[va], tfeat[va], tp_va, tf_va)
+    pred = np.array([h.policy_predict(feats[i]) if orders[i] >= gate else 0 for i in te])
     t_pred = times[te, pred]
     t_fb = times[te, 0]
+    t_total = np.where(orders[te] >= gate, tfeat[te] + t_pred, t_pred)
     result = {
         "format": "hrp-policy-v1",
         "trees": [hrp.tree_format(hrp.policy_tree(t)) for t in range(NTREES)],
         "params": [float(x) for x in params],
         "mean": [float(x) for x in mean],
         "scale": [float(x) for x in scale],
+        "min_n": [int(gate)],
+        "gate": {"validation_wins_by_order": {str(k): v for k, v in wins.items()},
+                 "mean_feature_ms_by_order": {str(n): float(np.mean(tfeat[orders == n])) for n in sorted(set(orders))}},
         "train": {"samples": int(len(tr)), "best_step": int(best[2]), "val_loss": float(best[0]),
                   "history": hist[-10:], "label_counts": np.bincount(labels[tr], minlength=NTREES).tolist()},
         "test": {"samples": int(len(te)), "accuracy": float((pred == labels[te]).mean()),
                  "mean_ms_policy": float(np.mean(np.where(np.isfinite(t_pred), t_pred, np.nan))),
+                 "mean_ms_policy_with_features": float(np.mean(np.where(np.isfinite(t_total), t_total, np.nan))),
                  "mean_ms_fallback": float(np.mean(np.where(np.isfinite(t_fb), t_fb, np.nan))),
                  "policy_failures": int((~np.isfinite(t_pred)).sum()),
                  "fallback_failures": int((~np.isfinite(t_fb)).sum()),

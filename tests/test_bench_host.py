@@ -138,3 +138,13 @@ def test_host_lower_bytes_counts_the_transferred_entries(n):
     # hrp_potrf_host transfers entry (i, j) when i >= 128 floor(j / 128)
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     assert bench.host_lower_bytes(n) == 8 * int(np.count_nonzero(i >= 128 * (j // 128)))
+
+
+def test_paired_ratio_ci_brackets_the_ratio():
+    rng = np.random.default_rng(3)
+    b = rng.uniform(10, 20, 40)
+    a = 0.8 * b * rng.uniform(0.95, 1.05, 40)
+    r, lo, hi = bench.paired_ratio_ci(a, b)
+    assert abs(r - a.mean() / b.mean()) < 1e-15
+    assert lo <= r <= hi and hi - lo < 0.05
+    assert bench.paired_ratio_ci(b, b)[1:] == (1.0, 1.0)     # identical pairs: no spread

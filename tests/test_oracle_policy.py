@@ -63,3 +63,22 @@ def test_features_on_known_matrices():
     G = gram_spd(128, 1e-2, seed_for(5, 3))
     f = policy.features(G)
     assert f[10] > 2.0                    # rank-deficient Gram + small shift: ill-conditioned
+
+
+def test_order_gate_takes_the_smallest_order_from_which_the_policy_always_wins():
+    import numpy as np
+
+    from paper_2601_08082_gb300.train_policy import order_gate
+    ns = np.array([1024] * 3 + [2048] * 3 + [4096] * 3 + [8192] * 3)
+    t_feat = np.full(12, 1.0)
+    t_fb = np.array([3.0] * 3 + [6.0] * 3 + [20.0] * 3 + [60.0] * 3)
+    # the policy saves 0.5, 2, 5, 10 ms: it pays for the 1 ms pass from 2048 on
+    t_pick = t_fb - np.repeat([0.5, 2.0, 5.0, 10.0], 3)
+    gate, wins = order_gate(ns, t_feat, t_pick, t_fb)
+    assert gate == 2048 and wins == {1024: False, 2048: True, 4096: True, 8192: True}
+    # a loss at a larger order moves the gate above it
+    t_pick2 = t_pick.copy()
+    t_pick2[6:9] = t_fb[6:9]
+    assert order_gate(ns, t_feat, t_pick2, t_fb)[0] == 8192
+    # never wins: no order qualifies
+    assert order_gate(ns, t_feat, t_fb.copy(), t_fb)[0] == 1 << 30
