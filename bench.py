@@ -616,6 +616,82 @@ def run_fp8posv(args, rank, world):
     return 0
 
 
+def run_fp64_1024(args, rank, world):
+    """The plain FP64 recursive Cholesky + solve at n = 1024: A = (B + B^T)/2, B iid N(0,1),
+    A_ii = sum_{j!=i} |A_ij| + 1, one N(0,1) right-hand side, tree [F64] with leaf 64 (FP64
+    leaves, FP64 SIMT GEMMs).  A step is hrp_potrf_async + hrp_potrs on a fresh resident copy;
+    the factor and the solution are checked against the CPU oracle (plain Cholesky, two
+    triangular solves) on every matrix, and the oracle itself is timed on the host as the CPU
+    baseline."""
+    import numpy as np
+    import torch
+
+    import paper_2601_08082_gb300 as hrp
+    from oracle import dense
+    from synth import dominant_spd, rhs, seed_for
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reps = Replicas("nccl", device=torch.device("cuda", local))
+    n = 1024
+    mats = [dominant_spd(n, 1.0, seed_for(0, 10 * rank + i), shift=1.0) for i in range(3)]
+    bs = [rhs(n, 1, seed_for(0, 100 + 10 * rank + i)) for i in range(3)]
+    # oracle: factor + solve on the host, its results also the reference of the check
+    t0 = time.perf_counter()
+    ref = []
+    for A, b in zip(mats, bs):
+        L0, info0 = dense.cholesky(A)
+        ref.append((L0, dense.potrs(L0, b)))
+    cpu_s = (time.perf_counter() - t0) / len(mats)
+    h = hrp.Handle(local)
+    tree = hrp.tree_parse("[F64]", leaf=64)
+    A0 = [hrp.colmajor(A).cuda() for A in mats]
+    B0 = [hrp.colmajor(b).cuda() for b in bs]
+    nsteps = args.warmup + args.steps
+    copies = [A0[s % 3].clone() for s in range(nsteps)]
+    Bc = [B0[s % 3].clone() for s in range(nsteps)]
+    d_info = torch.zeros(nsteps, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for s in range(args.warmup):
+        h.potrf_async(tree, copies[s], d_info[s:s + 1], stream=stream)
+        h.potrs(copies[s], Bc[s], stream=stream)
+    torch.cuda.synchronize()
+    reps.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(args.warmup, nsteps):
+        h.potrf_async(tree, copies[s], d_info[s:s + 1], stream=stream)
+        h.potrs(copies[s], Bc[s], stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = reps.max(a.elapsed_time(b))
+    assert int(d_info.max().item()) == 0 and int(d_info.min().item()) == 0
+    err_l, err_x = 0.0, 0.0
+    for s in range(args.warmup, min(nsteps, args.warmup + 3)):
+        L0, x0 = ref[s % 3]
+        L = np.tril(hrp.from_colmajor(copies[s]))
+        x = hrp.from_colmajor(Bc[s])
+        err_l = max(err_l, float(np.max(np.abs(L - L0)) / np.max(np.abs(L0))))
+        err_x = max(err_x, float(np.max(np.abs(x - x0)) / np.max(np.abs(x0))))
+    flops = n ** 3 / 3.0
+    work = reps.sum(args.steps * flops)
+    if rank == 0:
+        line = {"metric": "POTRF TFLOP/s (n^3/3 per s), plain FP64 recursive Cholesky + 1-RHS solve, n=1024",
+                "value": work / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "plain FP64 tree [F64] leaf 64, n=1024, A_ii = sum |A_ij| + 1, 1 RHS",
+                           "n": n, "tree": "[F64]", "leaf": 64,
+                           "l2": "inputs fit in L2 (8 MB each); a fresh resident copy per step"},
+                "max_rel_err_L_vs_oracle": err_l, "max_rel_err_x_vs_oracle": err_x,
+                "cpu_baseline": {"value": flops / cpu_s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": "oracle Cholesky + solve of the 3 workload matrices"}}
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def paired_ratio_ci(t_a, t_b, reps=2000, seed=7):
     """Mean of t_a / mean of t_b and a 95% bootstrap interval (pairs resampled together)."""
     import numpy as np
@@ -720,7 +796,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768", "blas3", "policy"])
+    ap.add_argument("--workload", default="mixed8192", choices=["mixed8192", "batched", "fp8posv32768", "blas3", "policy",
+                                                                  "fp64_1024"])
     ap.add_argument("--policy-matrices", type=int, default=48, help="held-out matrices per rank of the policy workload")
     ap.add_argument("--blas3-n", type=int, default=8192, help="order of the blas3 workload")
     ap.add_argument("--n3", type=int, default=32768, help="order of the fp8posv32768 workload")
@@ -741,6 +818,8 @@ def main():
         return run_blas3(args, rank, world)
     if args.workload == "policy":
         return run_policy(args, rank, world)
+    if args.workload == "fp64_1024":
+        return run_fp64_1024(args, rank, world)
 
     import numpy as np
     import torch
