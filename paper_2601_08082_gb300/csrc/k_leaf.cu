@@ -242,8 +242,9 @@ potrf_leaf_kernel(double* __restrict__ A, int ld, int n, int col0, int round16,
 }
 
 // ---------------------------------------------------------------------------------------
-// Leaf TRSM in FP64 (Alg. 2 base case "B <- TRSM(...; L, B)", right side, lower,
-// transposed): each thread owns one row of B and substitutes column by column,
+// Leaf TRSM by substitution (Alg. 2 base case "B <- TRSM(...; L, B)", right side, lower,
+// transposed), with T the arithmetic type (FP32 here; the FP64 leaf TRSM is the right-looking
+// kernel below): each thread owns one row of B and substitutes column by column,
 // x_j = (b_j - sum_{k<j} x_k l_jk) / l_jj.  B = A[r0.., c0..] and L = Lm[c0.., c0..]
 // (Lm = A inside the factorization, a separate factor for a standalone TRSM).
 // ---------------------------------------------------------------------------------------
@@ -308,6 +309,78 @@ trsm_subst_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc,
     }
     if (__any_sync(0xffffffffu, over16) && (tid & 31) == 0) atomicOr(err, DEV_ERR_RANGE16);
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Leaf TRSM in FP64, right-looking in unit-diagonal form (the FP64 base case of Alg. 2):
+// with Lt = L diag(1/l_kk) and Y = X diag(l_kk), Y Lt^T = B is a substitution without
+// divisions, y_ij = b_ij - sum_{k<j} y_ik Lt_jk, and X = Y diag(1/l_kk) at the end.  A row of
+// B is one half-warp's: lane q holds the row's columns q, q + 16, q + 32, ... (CPT of them);
+// at step k the holder of y_ik passes it along the half-warp by a shuffle and every lane
+// subtracts it from its columns j > k.  One dependent FMA per step sits on the row's chain
+// (the substitution above divides and sums a column's whole row in each step), and 8 rows
+// per CTA spread the FP64 work over many SMs.
+// ---------------------------------------------------------------------------------------
+constexpr int kR64Rows = 8;                        // rows of B per CTA (16 lanes each)
+template <int CPT>
+__global__ void __launch_bounds__(kR64Rows * 16)
+trsm_rl64_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc, const double* __restrict__ Lm,
+                 int ldl, __half* __restrict__ S, int lds, float* __restrict__ S32, int ld32,
+                 const int* __restrict__ info, unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (*(volatile const int*)info != INT_MAX) return;
+  double* Lt = reinterpret_cast<double*>(smem_raw);     // Lt[j * nc + k] = l_jk / l_kk, k < j
+  double* rinv = Lt + (size_t)nc * nc;                   // 1 / l_kk
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int q = tid & 15, rr = tid >> 4;
+  const int row = blockIdx.x * kR64Rows + rr;
+  const bool live = row < m;
+  if (tid < nc) rinv[tid] = 1.0 / Lm[(size_t)(c0 + tid) * ldl + (c0 + tid)];
+  // this lane's entries of B (all loads in flight before the staging of Lt is used)
+  double y[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int j = q + 16 * c;
+    y[c] = (live && j < nc) ? A[(size_t)(c0 + j) * ld + (r0 + row)] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nc * nc; idx += blockDim.x) {
+    const int j = idx / nc, k = idx % nc;
+    if (k < j) Lt[idx] = Lm[(size_t)(c0 + k) * ldl + (c0 + j)] * rinv[k];
+  }
+  __syncthreads();
+  const int base = lane & 16;                            // the half-warp of this row
+  for (int k = 0; k + 1 < nc; ++k) {
+    const int ck = k >> 4;
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (c == ck) v = y[c];
+    v = __shfl_sync(0xffffffffu, v, base | (k & 15));    // y_ik from the lane holding column k
+    const double* Lk = Lt + k;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = q + 16 * c;
+      if (c >= ck && j > k && j < nc) y[c] = fma(-v, Lk[(size_t)j * nc], y[c]);
+    }
+  }
+  bool over16 = false;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int j = q + 16 * c;
+    if (live && j < nc) {
+      const double x = y[c] * rinv[j];
+      A[(size_t)(c0 + j) * ld + (r0 + row)] = x;
+      if (S32 != nullptr) S32[(size_t)(c0 + j) * ld32 + (r0 + row)] = (float)x;
+      if (S != nullptr) {
+        over16 |= fabs(x) > (double)kF16Max;
+        S[(size_t)(r0 + row) * lds + (c0 + j)] = __double2half(x);
+      }
+    }
+  }
+  if (S != nullptr && __any_sync(0xffffffffu, over16) && lane == 0) atomicOr(err, DEV_ERR_RANGE16);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -486,19 +559,27 @@ cudaError_t launch_trsm_leaf64(double* A, int ld, int r0, int m, int c0, int nc,
   }
   if (m <= 0 || nc <= 0) return cudaSuccess;
   if (nc > 144) return cudaErrorInvalidValue;
-  int RT = nc <= 128 ? 64 : 32;
-  size_t smem = ((size_t)nc * nc + (size_t)RT * nc) * sizeof(double);
+  const size_t smem = ((size_t)nc * nc + (size_t)nc) * sizeof(double);
   static unsigned long long attr_mask = 0;
   const unsigned long long attr_bit = dev_bit();
   if (!(attr_mask & attr_bit)) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_subst_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(((size_t)144 * 144 + (size_t)32 * 144) * sizeof(double)));
+    const int mx = (int)(((size_t)144 * 144 + 144) * sizeof(double));
+    cudaError_t e = cudaFuncSetAttribute(trsm_rl64_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(trsm_rl64_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(trsm_rl64_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e != cudaSuccess) return e;
     attr_mask |= attr_bit;
   }
-  int grid = (m + RT - 1) / RT;
-  (void)launch_pdl(trsm_subst_kernel<double>, dim3(grid), dim3(64), smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds,
-                   shadow32, ld32, info, err, RT);
+  const dim3 grid((m + kR64Rows - 1) / kR64Rows), block(kR64Rows * 16);
+  if (nc <= 64)
+    (void)launch_pdl(trsm_rl64_kernel<4>, grid, block, smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds, shadow32,
+                     ld32, info, err);
+  else if (nc <= 128)
+    (void)launch_pdl(trsm_rl64_kernel<8>, grid, block, smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds, shadow32,
+                     ld32, info, err);
+  else
+    (void)launch_pdl(trsm_rl64_kernel<9>, grid, block, smem, s, A, ld, r0, m, c0, nc, Lm, ldl, shadow16, lds, shadow32,
+                     ld32, info, err);
   return cudaGetLastError();
 }
 
