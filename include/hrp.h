@@ -129,7 +129,10 @@ hrp_status hrp_potrf_async(hrp_handle* h, const hrp_tree* tree, int n, double* d
 
 /*
  * Solve A X = B given the factor from hrp_potrf (L in the lower triangle of dL):
- * forward substitution L Y = B, then backward L^T X = Y, both in FP64.
+ * forward substitution L Y = B, then backward L^T X = Y, in 64-row blocks with FP64
+ * storage and sums; each block's 16-term partial products are formed in double-float
+ * (a pair of binary32 values, about 2^-44 relative to the sum of |terms| at worst, against
+ * about 2^-49 for FP64 arithmetic), which moves them off GB300's slow FP64 pipe.
  * dB (n x nrhs, ldb >= max(1,n)) is overwritten with X. Asynchronous.
  */
 hrp_status hrp_potrs(hrp_handle* h, int n, int nrhs, const double* dL, int ldl,
@@ -439,7 +442,7 @@ long long hrp_last_launch_count(const hrp_handle* h);
  *   sweeps), 1 us .. 2 s (the default).  A sweep whose wait expires writes NaN into the
  *   rows it could not solve and publishes them, so dependent rows come out NaN too.
  * hrp_wait_selftest: one device thread waits, through the sweeps' bounded-wait routine,
- *   on a device flag that nothing sets, for `microseconds` (1 .. 2e6); the wait expires,
+ *   on a mailbox entry that nothing fills, for `microseconds` (1 .. 2e6); the wait expires,
  *   the kernel records the timeout and returns, and the call reports HRP_ERR_TIMEOUT with
  *   *waited_us (host, may be NULL) the time the device waited.  The context stays usable.
  *   Synchronous.
@@ -455,13 +458,13 @@ hrp_status hrp_wait_selftest(hrp_handle* h, long long microseconds, double* wait
  * their own pool, loops where cudaMalloc's implicit synchronization is unacceptable, or
  * plugins handed buffers but no allocator.  The paper has no counterpart; this is a
  * property of the library, not of the method.
- *   - Takes no handle and allocates nothing: its scratch (diagonal-block inverses, ready
- *     flags, a ticket) is one fixed device array inside the library, about 4 MiB, which
- *     every GPU that loads the library keeps until the process exits.
+ *   - Takes no handle and allocates nothing: its scratch (diagonal-block inverses, the
+ *     sweeps' mailboxes, a ticket) is one fixed device array inside the library, about
+ *     6 MiB, which every GPU that loads the library keeps until the process exits.
  *   - n must be <= 8192 (the array's size); larger n returns HRP_ERR_INVALID_ARG, as do
  *     negative sizes, NULL buffers and leading dimensions < max(1, n).
  *   - The first call on a device (with that device current) looks up the array's device
- *     address and zeroes its flags with a synchronous cudaMemset; make that first call
+ *     address and zeroes its ticket with a synchronous cudaMemset; make that first call
  *     before any stream capture.  Later calls only enqueue work on `stream`.
  *   - All calls share the one array: calls that overlap on the GPU (different streams,
  *     no ordering between them) race and must not be issued.

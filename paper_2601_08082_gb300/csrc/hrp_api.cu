@@ -36,10 +36,7 @@ struct hrp_handle_s {
   int* d_info = nullptr;       // internal info word
   unsigned* d_err = nullptr;   // device error flags
   int* d_ticket = nullptr;
-  int* d_flags = nullptr;
-  size_t flags_cap = 0;
-  int* d_epoch = nullptr;      // POTRS epoch counter (advanced on the device by every solve)
-  int* d_probe = nullptr;      // a flag nothing sets (hrp_wait_selftest) and the time waited
+  double* d_probe = nullptr;   // a mailbox entry nothing fills (hrp_wait_selftest) and the time waited
   unsigned long long wait_ns = hrp::kWaitTimeoutNs;   // limit of the solves' bounded waits
   __half* shadow = nullptr;
   size_t shadow_cap = 0;       // elements
@@ -783,12 +780,10 @@ hrp_status hrp_create(hrp_handle** out, int device) {
   bool ok = cudaMalloc(&h->d_info, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_err, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&h->d_ticket, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->d_epoch, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_probe, 4 * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&h->d_norms, sizeof(double) * 128) == cudaSuccess &&
             cudaMallocHost(&h->h_norms, sizeof(double) * 128) == cudaSuccess;
   if (!ok || cudaMemset(h->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(h->d_epoch, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(h->d_probe, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     hrp_destroy(h);
     return HRP_ERR_ALLOC;
@@ -804,9 +799,7 @@ hrp_status hrp_destroy(hrp_handle* h) {
   cudaFree(h->d_info);
   cudaFree(h->d_err);
   cudaFree(h->d_ticket);
-  cudaFree(h->d_epoch);
   cudaFree(h->d_probe);
-  cudaFree(h->d_flags);
   cudaFree(h->shadow);
   cudaFree(h->w32);
   cudaFree(h->shadow8);
@@ -996,19 +989,9 @@ hrp_status hrp_potrf(hrp_handle* h, const hrp_tree* tree, int n, double* dA, int
 static hrp_status potrs_impl(hrp_handle* h, int n, int nrhs, const double* dL, int ldl, double* dB, int ldb,
                              bool fp32, cudaStream_t s) {
   hrp_status st;
-  int* old_flags = h->d_flags;
-  size_t old_cap = h->flags_cap;
-  if ((st = ensure(h, &h->d_flags, &h->flags_cap, potrs_flag_count(n))) != HRP_OK) return st;
-  if (h->d_flags != old_flags || h->flags_cap != old_cap) {
-    // fresh flags must not hold a value equal to a future epoch (epochs are >= 1)
-    cudaError_t me = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->flags_cap, s);
-    if (me != cudaSuccess) return cuda_status(h, me, "hrp_potrs");
-  }
   if ((st = ensure(h, &h->pwork, &h->pwork_cap, potrs_workspace_bytes(n))) != HRP_OK) return st;
-  cudaError_t e =
-      launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->pwork, h->d_ticket, h->d_flags, h->d_epoch, h->d_err, s,
-                   h->wait_ns);
-  h->launches += 2 + potrs_epochs(nrhs);
+  cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, fp32, h->pwork, h->d_ticket, h->d_err, s, h->wait_ns);
+  h->launches += 1 + potrs_sweeps(nrhs);
   return cuda_status(h, e, "hrp_potrs");
 }
 
@@ -1490,10 +1473,9 @@ hrp_status hrp_wait_selftest(hrp_handle* h, long long microseconds, double* wait
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   hrp_status st = check_dev_err(h, s);           // report what earlier calls left first
   if (st != HRP_OK) return st;
-  // d_probe[0] (an int that stays 0) is the flag; d_probe[1] receives the time waited
-  unsigned long long* out = reinterpret_cast<unsigned long long*>(h->d_probe) + 1;
-  cudaError_t e = cudaMemsetAsync(h->d_probe, 0, sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = launch_wait_probe(h->d_probe, (unsigned long long)microseconds * 1000ull, h->d_err, out, s);
+  // d_probe[0] is the mailbox entry (emptied by the probe); d_probe[1] receives the time waited
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(h->d_probe + 1);
+  cudaError_t e = launch_wait_probe(h->d_probe, (unsigned long long)microseconds * 1000ull, h->d_err, out, s);
   unsigned long long ns = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, out, sizeof(ns), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1517,7 +1499,7 @@ namespace {
 constexpr int kBatchStreams = 32;
 
 struct SysWork {
-  size_t shadow, w32, pinv, flags, ticket, fact, res;   // byte offsets into h->bwork
+  size_t shadow, w32, pinv, ticket, fact, res;   // byte offsets into h->bwork
   int lds;
 };
 
@@ -1534,7 +1516,6 @@ hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<Sys
     w.shadow = need_factor_ws ? take((size_t)ni * w.lds * sizeof(__half)) : 0;
     w.w32 = need_factor_ws ? take(((size_t)ni * 128 + 128 * 128) * sizeof(float)) : 0;
     w.pinv = take(potrs_workspace_bytes(ni));
-    w.flags = take(sizeof(int) * (potrs_flag_count(ni) + 1));   // flags, then the epoch counter
     w.ticket = take(sizeof(int));
     w.fact = nrhs_ir ? take(sizeof(double) * (size_t)ni * ni) : 0;
     w.res = nrhs_ir ? take(sizeof(double) * (size_t)ni * nrhs_ir + sizeof(double) * 2 * nrhs_ir) : 0;
@@ -1544,7 +1525,7 @@ hrp_status batch_prepare(hrp_handle* h, int batch, const int* n, std::vector<Sys
   hrp_status st = ensure(h, &h->bwork, &h->bwork_cap, off);
   if (st != HRP_OK) return st;
   if (h->bwork != old || h->bwork_cap != old_cap) {
-    // zero flags and epoch counters (and everything else) of the fresh workspace
+    // zero the tickets (and everything else) of the fresh workspace
     if (cudaMemset(h->bwork, 0, h->bwork_cap) != cudaSuccess) return set_err(h, HRP_ERR_CUDA, "batch workspace");
   }
   while ((int)h->bstreams.size() < kBatchStreams) {
@@ -1820,11 +1801,9 @@ hrp_status hrp_potrs_batched(hrp_handle* h, int batch, const int* n, double* con
   for (int i = 0; i < batch; ++i) {
     if (n[i] == 0) continue;
     cudaStream_t si = h->bstreams[which[i]];
-    int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
     cudaError_t e = launch_potrs(dL[i], ldl[i], dB[i], ldb[i], n[i], nrhs, false, h->bwork + ws[i].pinv,
-                                 reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags,
-                                 flags + potrs_flag_count(n[i]), h->d_err, si, h->wait_ns);
-    launches += 2 + potrs_epochs(nrhs);
+                                 reinterpret_cast<int*>(h->bwork + ws[i].ticket), h->d_err, si, h->wait_ns);
+    launches += 1 + potrs_sweeps(nrhs);
     if (e != cudaSuccess && err == cudaSuccess) err = e;
   }
   if ((st = join(h, s)) != HRP_OK) return st;
@@ -2253,19 +2232,15 @@ extern "C" hrp_status hrp_posv_batched(hrp_handle* h, const hrp_tree* const* tre
     for (int i = 0; i < batch; ++i) {
       if (n[i] == 0 || hinfo[i] != 0 || done[i]) continue;
       cudaStream_t si = h->bstreams[which[i]];
-      int* flags = reinterpret_cast<int*>(h->bwork + ws[i].flags);
-      int* ctr = flags + potrs_flag_count(n[i]);
       double* R = res_of(i);
       if (fresh[i]) {
         fresh[i] = 0;
         note(launch_copy_matrix(dX[i], ldx[i], dB[i], ldb[i], n[i], nrhs, si));
         note(launch_potrs(fact_of(i), n[i], dX[i], ldx[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
-                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ctr, h->d_err, si,
-                          h->wait_ns));
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), h->d_err, si, h->wait_ns));
       } else {
         note(launch_potrs(fact_of(i), n[i], R, n[i], n[i], nrhs, true, h->bwork + ws[i].pinv,
-                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), flags, ctr, h->d_err, si,
-                          h->wait_ns));
+                          reinterpret_cast<int*>(h->bwork + ws[i].ticket), h->d_err, si, h->wait_ns));
         note(launch_axpy_matrix(dX[i], ldx[i], R, n[i], n[i], nrhs, si));
         ++its[i];
       }

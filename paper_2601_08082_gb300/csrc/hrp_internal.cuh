@@ -127,24 +127,27 @@ cudaError_t launch_gemm_f16_tc(double* C, int ldc, const __half* S, int lds,
                                double scale, unsigned* dev_err, cudaStream_t s, int occupancy = 0);
 
 // ---------------- POTRS (k_potrs.cu) ----------------
-// B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 or (fp32)
-// in FP32 on FP32-rounded L and B.  ticket: device int scratch; flags: device ints, one per
-// 64-row block (potrs_flag_count(n), zero before first use); epoch_ctr: a device int (zero
-// before first use) that the solve's first kernel advances by potrs_epochs(nrhs), clearing
-// the flags when it would overflow.  work: device scratch of potrs_workspace_bytes(n)
-// (inverses of the 64 x 64 diagonal blocks).  A bounded wait that expires sets
-// DEV_ERR_TIMEOUT in dev_err and leaves NaN in the unsolved rows of B.
+constexpr int kPotrsBlock = 64;     // rows per block of the sweeps
+constexpr int kPotrsMaxRhs = 16;    // right-hand sides per pair of sweeps
+// device scratch of one solve of order n: the inverses of the 64 x 64 diagonal blocks
+// (FP64), then two mailboxes (forward and backward sweep) of kPotrsMaxRhs columns each
+constexpr size_t potrs_workspace_bytes(int n) {
+  return (size_t)((n + kPotrsBlock - 1) / kPotrsBlock) * kPotrsBlock * (kPotrsBlock + 2 * kPotrsMaxRhs) * sizeof(double);
+}
+// B (n x nrhs) <- A^{-1} B with A = L L^T: forward then backward sweep, in FP64 (the products
+// in double-float) or (fp32) in FP32 on FP32-rounded L and B.  ticket: device int scratch.
+// work: device scratch of potrs_workspace_bytes(n), no initial contents needed (the solve
+// empties its mailboxes itself).  A bounded wait that expires sets DEV_ERR_TIMEOUT in dev_err
+// and leaves NaN in the unsolved rows of B.  Launches: one pre-pass plus potrs_sweeps(nrhs).
 cudaError_t launch_potrs(const double* L, int ldl, double* B, int ldb, int n, int nrhs, bool fp32, void* work,
-                         int* ticket, int* flags, int* epoch_ctr, unsigned* dev_err, cudaStream_t s,
+                         int* ticket, unsigned* dev_err, cudaStream_t s,
                          unsigned long long wait_limit_ns = kWaitTimeoutNs);
-// One thread waits, through the sweeps' bounded wait, on *flag reaching 1 (the caller sees
-// that nothing sets it): after wait_limit_ns it sets DEV_ERR_TIMEOUT and writes the time it
-// waited (ns) to *waited_ns (device).
-cudaError_t launch_wait_probe(const int* flag, unsigned long long wait_limit_ns, unsigned* dev_err,
+// One thread empties the mailbox entry *entry (device) and waits on it through the sweeps'
+// bounded wait; nothing fills it, so after wait_limit_ns it sets DEV_ERR_TIMEOUT and writes
+// the time it waited (ns) to *waited_ns (device).
+cudaError_t launch_wait_probe(double* entry, unsigned long long wait_limit_ns, unsigned* dev_err,
                               unsigned long long* waited_ns, cudaStream_t s);
-size_t potrs_workspace_bytes(int n);
-size_t potrs_flag_count(int n);
-int potrs_epochs(int nrhs);
+int potrs_sweeps(int nrhs);
 
 // ---------------- utilities (k_util.cu) ----------------
 // SM count of the current device, queried once per device

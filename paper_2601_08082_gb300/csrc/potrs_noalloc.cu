@@ -9,9 +9,9 @@
 // file-scope device array, reserved in every GPU that loads the library until the
 // process exits.
 //
-// Scratch layout (kScratchBytes, fixed): inverses of the 64 x 64 diagonal blocks
-// (n_max x 64 doubles), one ready flag per 64-row block, the sweep ticket, the epoch
-// counter of the sweeps (advanced on the device by every call) and an error word.
+// Scratch layout (kScratchBytes, fixed): the solve's workspace for n_max (inverses of the
+// 64 x 64 diagonal blocks and the two mailboxes of the sweeps, which every call empties
+// itself), the sweep ticket and an error word.
 // A bounded wait inside a sweep that expires leaves NaN in the rows of B it could not
 // solve (and, through the products, in every row that depends on them): that NaN is
 // how a caller of this entry point sees the failure.
@@ -23,12 +23,9 @@ namespace hrp {
 namespace {
 
 constexpr int kNoAllocMaxN = 8192;                                   // largest order accepted
-constexpr int kNoAllocBlocks = (kNoAllocMaxN + 63) / 64;             // 128 row blocks
-constexpr size_t kInvBytes = (size_t)kNoAllocBlocks * 64 * 64 * sizeof(double);   // 4 MiB
-constexpr size_t kFlagsOffset = kInvBytes;
-constexpr size_t kTicketOffset = kFlagsOffset + sizeof(int) * kNoAllocBlocks;
-constexpr size_t kEpochOffset = kTicketOffset + sizeof(int);
-constexpr size_t kErrOffset = kEpochOffset + sizeof(int);
+constexpr size_t kWorkBytes = potrs_workspace_bytes(kNoAllocMaxN);   // 6 MiB
+constexpr size_t kTicketOffset = kWorkBytes;
+constexpr size_t kErrOffset = kTicketOffset + sizeof(int);
 constexpr size_t kScratchBytes = (kErrOffset + sizeof(unsigned) + 255) / 256 * 256;
 
 static __device__ __align__(256) unsigned char g_potrs_scratch[kScratchBytes];
@@ -64,11 +61,10 @@ extern "C" hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int l
     DeviceScratch& d = g_dev[dev];
     if (!d.ready) {
       // once per device, with that device current: the device address of the array (its
-      // host-side name is only a stand-in), then zeroed flags, ticket, epoch counter and
-      // error word (no flag may equal an epoch, and epochs start at 1)
+      // host-side name is only a stand-in), then a zeroed ticket and error word
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_potrs_scratch) != cudaSuccess) return HRP_ERR_CUDA;
-      if (cudaMemset(static_cast<unsigned char*>(p) + kFlagsOffset, 0, kScratchBytes - kFlagsOffset) != cudaSuccess)
+      if (cudaMemset(static_cast<unsigned char*>(p) + kTicketOffset, 0, kScratchBytes - kTicketOffset) != cudaSuccess)
         return HRP_ERR_CUDA;
       d.base = static_cast<unsigned char*>(p);
       d.ready = true;
@@ -76,7 +72,6 @@ extern "C" hrp_status hrp_potrs_noalloc(int n, int nrhs, const double* dL, int l
     base = d.base;
   }
   cudaError_t e = launch_potrs(dL, ldl, dB, ldb, n, nrhs, false, base, reinterpret_cast<int*>(base + kTicketOffset),
-                               reinterpret_cast<int*>(base + kFlagsOffset), reinterpret_cast<int*>(base + kEpochOffset),
                                reinterpret_cast<unsigned*>(base + kErrOffset), s);
   return e == cudaSuccess ? HRP_OK : HRP_ERR_CUDA;
 }
