@@ -352,18 +352,22 @@ trsm_rl64_kernel(double* __restrict__ A, int ld, int r0, int m, int c0, int nc, 
   }
   __syncthreads();
   const int base = lane & 16;                            // the half-warp of this row
-  for (int k = 0; k + 1 < nc; ++k) {
-    const int ck = k >> 4;
-    double v = 0.0;
+  // column panels of 16: while k runs through panel p only slots c >= p change, and the
+  // panel loop is unrolled so that no FP64 instruction is issued for the others (on this
+  // GPU the SM retires under two FP64 lane-FMAs per clock, predicated-off lanes included)
 #pragma unroll
-    for (int c = 0; c < CPT; ++c)
-      if (c == ck) v = y[c];
-    v = __shfl_sync(0xffffffffu, v, base | (k & 15));    // y_ik from the lane holding column k
-    const double* Lk = Lt + k;
+  for (int p = 0; p < CPT; ++p) {
+    if (16 * p + 1 >= nc) break;
+    const int kend = min(16 * p + 16, nc - 1);
+    for (int k = 16 * p; k < kend; ++k) {
+      const double v = __shfl_sync(0xffffffffu, y[p], base | (k & 15));   // y_ik from the lane holding column k
+      const double* Lk = Lt + k;
+      if (q > k - 16 * p && q + 16 * p < nc) y[p] = fma(-v, Lk[(size_t)(q + 16 * p) * nc], y[p]);
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int j = q + 16 * c;
-      if (c >= ck && j > k && j < nc) y[c] = fma(-v, Lk[(size_t)j * nc], y[c]);
+      for (int c = p + 1; c < CPT; ++c) {
+        const int j = q + 16 * c;
+        if (j < nc) y[c] = fma(-v, Lk[(size_t)j * nc], y[c]);
+      }
     }
   }
   bool over16 = false;
