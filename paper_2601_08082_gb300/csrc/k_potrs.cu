@@ -214,17 +214,18 @@ __device__ __forceinline__ fpair split_chunk(double x, int& s) {
 // With T = double the far products (blocks solved two or more links earlier) stay in FP64,
 // off the chain; the link itself (the newest block's product and the product with W_r) runs
 // in double-float as above.  With T = float (the correction solves of the refinement) every
-// product is binary32.
-template <typename T, bool FWD>
+// product is binary32.  NR (1, 4 or 16) bounds the right-hand sides of one launch, which sizes
+// the accumulators: a 1-RHS solve does not carry 16 of them through the sweep.
+template <typename T, bool FWD, int NR>
 __global__ void __launch_bounds__(PT, 1)
 potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ W, double* __restrict__ B, int ldb,
                    int n, int nrhs, int* __restrict__ ticket, double* __restrict__ mb, double* __restrict__ mb_next,
                    int mbld, unsigned* __restrict__ err, unsigned long long limit_ns) {
   constexpr bool kDF = sizeof(T) == sizeof(double);
-  __shared__ T yS[MAX_RHS][PB];          // solved block of another CTA; later the reduced rhs
-  __shared__ T part[4][MAX_RHS][PB];     // per-chunk partial sums
+  __shared__ T yS[NR][PB];               // solved block of another CTA; later the reduced rhs
+  __shared__ T part[4][NR][PB];          // per-chunk partial sums
   __shared__ int s_r, s_abort;
-  __shared__ int vsc[MAX_RHS][PB / 16];  // double-float: scale of each 16-entry chunk of the staged vector
+  __shared__ int vsc[NR][PB / 16];       // double-float: scale of each 16-entry chunk of the staged vector
   T (*accS)[PB] = yS;
   fpair (*vP)[PB] = reinterpret_cast<fpair (*)[PB]>(&yS[0][0]);   // double-float: the staged vector as pairs
   const int tid = threadIdx.x;
@@ -238,13 +239,13 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
   const int r = s_r, R0 = r * PB, rows = min(PB, n - R0);
   const int i = tid % PB, ch = tid / PB;           // row i, k-chunk ch (16 columns each)
   empty_rows(mb_next, mbld, R0, tid);              // the next sweep's mailbox (no one reads it now)
-  T acc[MAX_RHS];
+  T acc[NR];
 #pragma unroll
-  for (int c = 0; c < MAX_RHS; ++c) acc[c] = (T)0;
+  for (int c = 0; c < NR; ++c) acc[c] = (T)0;
 
   // this block's right-hand side does not depend on other blocks either: its DRAM latency
   // stays off the block-to-block chain (thread tid holds entries tid + PT u)
-  constexpr int kBU = MAX_RHS * PB / PT;
+  constexpr int kBU = (NR * PB + PT - 1) / PT;
   T bpre[kBU];
 #pragma unroll
   for (int u = 0; u < kBU; ++u) {
@@ -447,7 +448,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
       } else if (kd == 1) {
         // reduce the four chunks, subtract from the right-hand side
 #pragma unroll
-        for (int c = 0; c < MAX_RHS; ++c)
+        for (int c = 0; c < NR; ++c)
           if (c < nrhs) part[ch][c][i] = acc[c];
         __syncthreads();
 #pragma unroll
@@ -465,7 +466,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
         if (!await_block(jl)) return;
       }
 #pragma unroll
-      for (int c = 0; c < MAX_RHS; ++c) {
+      for (int c = 0; c < NR; ++c) {
         if (c < nrhs) {
           const double d = dot16_df(ap, sa, &vP[c][ch * 16], vsc[c][ch]);
           if (kd == 0) acc[c] += d;
@@ -500,7 +501,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
       load_l(j, lv);
       if (!await_block(j)) return;
 #pragma unroll
-      for (int c = 0; c < MAX_RHS; ++c) {
+      for (int c = 0; c < NR; ++c) {
         if (c < nrhs) {
           T s = (T)0;
 #pragma unroll
@@ -512,7 +513,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
     }
     // reduce the four chunks, subtract from the right-hand side
 #pragma unroll
-    for (int c = 0; c < MAX_RHS; ++c)
+    for (int c = 0; c < NR; ++c)
       if (c < nrhs) part[ch][c][i] = acc[c];
     __syncthreads();
 #pragma unroll
@@ -523,7 +524,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
     __syncthreads();
     // y_r = W_r acc (forward) or x_r = W_r^T acc (backward): row i, chunk ch of 16 columns
 #pragma unroll
-    for (int c = 0; c < MAX_RHS; ++c) {
+    for (int c = 0; c < NR; ++c) {
       if (c < nrhs) {
         T s = (T)0;
 #pragma unroll
@@ -537,6 +538,25 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
       if (ii < rows) publish(ii, c, (double)((part[0][c][ii] + part[1][c][ii]) + (part[2][c][ii] + part[3][c][ii])));
     }
   }
+}
+
+template <typename T, int NR>
+cudaError_t sweep_smem_attr(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(potrs_sweep_kernel<T, true, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(potrs_sweep_kernel<T, false, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+template <typename T, int NR>
+cudaError_t launch_sweep(bool fwd, int nb, size_t dsmem, cudaStream_t s, const double* L, int ldl, const T* W, double* B,
+                         int ldb, int n, int nc, int* ticket, double* mb, double* mb_next, int mbld, unsigned* err,
+                         unsigned long long limit_ns) {
+  if (fwd)
+    potrs_sweep_kernel<T, true, NR><<<nb, PT, dsmem, s>>>(L, ldl, W, B, ldb, n, nc, ticket, mb, mb_next, mbld, err, limit_ns);
+  else
+    potrs_sweep_kernel<T, false, NR><<<nb, PT, dsmem, s>>>(L, ldl, W, B, ldb, n, nc, ticket, mb, mb_next, mbld, err, limit_ns);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -560,12 +580,9 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
                                   (int)smem)) != cudaSuccess)
       return e;
     if (dsmem > 0) {
-      if ((e = cudaFuncSetAttribute(potrs_sweep_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dsmem)) != cudaSuccess)
-        return e;
-      if ((e = cudaFuncSetAttribute(potrs_sweep_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dsmem)) != cudaSuccess)
-        return e;
+      if ((e = sweep_smem_attr<T, 1>((int)dsmem)) != cudaSuccess) return e;
+      if ((e = sweep_smem_attr<T, 4>((int)dsmem)) != cudaSuccess) return e;
+      if ((e = sweep_smem_attr<T, MAX_RHS>((int)dsmem)) != cudaSuccess) return e;
     }
     attr_mask |= attr_bit;
   }
@@ -575,12 +592,19 @@ cudaError_t potrs_t(const double* L, int ldl, double* B, int ldb, int n, int nrh
   for (int c0 = 0; c0 < nrhs; c0 += MAX_RHS) {
     const int nc = nrhs - c0 < MAX_RHS ? nrhs - c0 : MAX_RHS;
     double* Bc = B + (size_t)c0 * ldb;
-    if ((e = cudaMemsetAsync(ticket, 0, sizeof(int), s)) != cudaSuccess) return e;
-    potrs_sweep_kernel<T, true><<<nb, PT, dsmem, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, mbf, mbb, mbld, err, limit_ns);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ticket, 0, sizeof(int), s)) != cudaSuccess) return e;
-    potrs_sweep_kernel<T, false><<<nb, PT, dsmem, s>>>(L, ldl, W, Bc, ldb, n, nc, ticket, mbb, mbf, mbld, err, limit_ns);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((e = cudaMemsetAsync(ticket, 0, sizeof(int), s)) != cudaSuccess) return e;
+      double* mb = pass == 0 ? mbf : mbb;
+      double* mb_next = pass == 0 ? mbb : mbf;
+      if (nc == 1)
+        e = launch_sweep<T, 1>(pass == 0, nb, dsmem, s, L, ldl, W, Bc, ldb, n, nc, ticket, mb, mb_next, mbld, err, limit_ns);
+      else if (nc <= 4)
+        e = launch_sweep<T, 4>(pass == 0, nb, dsmem, s, L, ldl, W, Bc, ldb, n, nc, ticket, mb, mb_next, mbld, err, limit_ns);
+      else
+        e = launch_sweep<T, MAX_RHS>(pass == 0, nb, dsmem, s, L, ldl, W, Bc, ldb, n, nc, ticket, mb, mb_next, mbld, err,
+                                     limit_ns);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
