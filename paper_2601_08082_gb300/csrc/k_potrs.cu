@@ -200,12 +200,12 @@ __device__ __forceinline__ double dot16_df(const fpair (&a)[16], int sa, const f
   return widen_scaled(s, sa + sv) + widen_scaled(c, sa + sv);
 }
 
-// x as a pair scaled by the largest exponent among the 16 lanes of its half-warp (the entries
-// k0 .. k0 + 15 of one column chunk); every lane of the warp must call it
+// x as a pair scaled by the largest exponent among the 32 lanes of its warp (the entries of two
+// 16-entry column chunks); every lane of the warp must call it
 __device__ __forceinline__ fpair split_chunk(double x, int& s) {
-  int ex = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+  // one warp-wide reduction: the scale is shared by the warp's two chunks (any common
+  // power of two keeps the pairs exact; the group only sets which entries count as negligible)
+  const int ex = (int)__reduce_max_sync(0xffffffffu, (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff));
   s = ex == 0 ? 0 : ex - 1023;
   return split_scaled(x, s);
 }
