@@ -211,11 +211,11 @@ __device__ __forceinline__ fpair split_chunk(double x, int& s) {
 }
 
 // ---- 2/3. sweeps ----
-// With T = double the far products (blocks solved two or more links earlier) stay in FP64,
-// off the chain; the link itself (the newest block's product and the product with W_r) runs
-// in double-float as above.  With T = float (the correction solves of the refinement) every
-// product is binary32.  NR (1, 4 or 16) bounds the right-hand sides of one launch, which sizes
-// the accumulators: a 1-RHS solve does not carry 16 of them through the sweep.
+// With T = double every 16-term partial product runs in double-float as above, and the sums
+// across chunks and blocks in FP64; the link between consecutive blocks is one product with
+// M_r (formed at the CTA's start).  With T = float (the correction solves of the refinement)
+// every product is binary32.  NR (1, 4 or 16) bounds the right-hand sides of one launch, which
+// sizes the accumulators: a 1-RHS solve does not carry 16 of them through the sweep.
 template <typename T, bool FWD, int NR>
 __global__ void __launch_bounds__(PT, 1)
 potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ W, double* __restrict__ B, int ldb,

@@ -229,6 +229,28 @@ def test_potrs_fp64_matches_oracle(hrp_mod, handle, n, nrhs):
     assert np.max(np.abs(X - X0)) <= 1e-12 * np.max(np.abs(X0))
 
 
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_potrs_columns_of_any_magnitude(hrp_mod, handle, nrhs):
+    """The solve forms its products in pairs of binary32 values scaled by powers of two per
+    group of entries: right-hand sides whose columns lie near the ends of the FP64 range
+    (2^-900 .. 2^900, far outside binary32's) are solved as accurately as unit ones, column
+    by column, against the oracle's FP64 solve."""
+    n = 1000
+    A = dominant_spd(n, 1.0, seed_for(0, 77), shift=1.0)
+    L0, _ = dense.cholesky(A)
+    B = rhs(n, nrhs, seed_for(0, 78))
+    exps = [(-900, 0, 900)[c % 3] for c in range(nrhs)]
+    B = B * np.array([2.0 ** e for e in exps])[None, :]
+    Lt = hrp_mod.colmajor(L0).cuda()
+    Bt = hrp_mod.colmajor(B).cuda()
+    handle.potrs(Lt, Bt)
+    X = hrp_mod.from_colmajor(Bt)
+    X0 = dense.potrs(L0, B)
+    for c in range(nrhs):
+        assert np.all(np.isfinite(X[:, c]))
+        assert np.max(np.abs(X[:, c] - X0[:, c])) <= 1e-12 * np.max(np.abs(X0[:, c])), (c, exps[c])
+
+
 def test_not_spd_reports_first_failing_column(hrp_mod, handle):
     n = 300
     A = dominant_spd(n, 2.0, seed_for(0, 9))
