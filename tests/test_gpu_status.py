@@ -1,6 +1,6 @@
 """Device-side status, range and replay behaviour of the GPU path (through the C ABI).
 
-* Bounded waits: a kernel waits on a flag that nothing sets with a short limit; the wait
+* Bounded waits: a kernel waits on a mailbox entry that nothing fills with a short limit; the wait
   expires, the status word records it and the call returns HRP_ERR_TIMEOUT with the
   context still usable.  Solves run with a 1 us limit either finish or report the
   timeout with NaN rows (never a plausible wrong answer).
@@ -8,7 +8,7 @@
   handles; an operand beyond 65504 is reported as HRP_ERR_RANGE, and hrp_posv refactors
   with the FP32 fallback tree.  The emulator applies the general rule to the same input.
 * Graph replay: factor + solve captured once and replayed must solve every system every
-  time (the solve's epochs come from a device counter advanced in the graph).
+  time (the solve's kernels empty their mailboxes themselves, in stream order).
 * Policy file and policy-chosen trees in the batched calls.
 """
 import os

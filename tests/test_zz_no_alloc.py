@@ -7,7 +7,7 @@ This test calls it through the C ABI twice in a row and checks each result again
 handle-based hrp_potrs and against the CPU oracle's solve with the same factor, with the
 tolerance of the other POTRS parity tests (1e-12 relative).  A second case uses an
 order close to the array's limit (n = 8150: 128 row blocks, the last
-inverse slot and the flags beside it) and 20 right-hand sides (two sweeps of 16 and 4).
+inverse slot and the mailboxes beside it) and 20 right-hand sides (two sweeps of 16 and 4).
 It lives in its own file, collected last.
 """
 import ctypes
