@@ -496,7 +496,7 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
   } else {
     for (int jj = 0; jj < ndep; ++jj) {
       const int j = FWD ? jj : nb - 1 - jj;
-      // this thread's 16 factor entries do not depend on the flag: load them first
+      // this thread's 16 factor entries do not depend on the mailbox: load them first
       T lv[16];
       load_l(j, lv);
       if (!await_block(j)) return;
