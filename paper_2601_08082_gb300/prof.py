@@ -60,6 +60,9 @@ def main() -> int:
                     help="print per-kernel-class device time of the last factorization (event timing mode)")
     ap.add_argument("--timeline", action="store_true",
                     help="print the critical stream's leaves and the launches between them (event timing mode)")
+    ap.add_argument("--no-lookahead", action="store_true", help="one stream: hrp_set_lookahead(h, 0)")
+    ap.add_argument("--f8-fp16", action="store_true",
+                    help="F8 levels on the kind::f16 GEMM with E4M3 values in FP16 storage (hrp_set_f8_gemm(h, 1))")
     args = ap.parse_args()
 
     import torch
@@ -68,6 +71,10 @@ def main() -> int:
     from . import hrp
 
     h = hrp.Handle(0)
+    if args.no_lookahead:
+        h.set_lookahead(False)
+    if args.f8_fp16:
+        h.set_f8_gemm(True)
     if args.device_gen:
         g = torch.Generator(device="cuda")
         g.manual_seed(seed_for(1, 0))
