@@ -270,8 +270,6 @@ potrs_sweep_kernel(const double* __restrict__ L, int ldl, const T* __restrict__ 
       else lv[q] = (kk < jrows && i < rows) ? (T)L[(size_t)(R0 + i) * ldl + J0 + kk] : (T)0;
     }
   };
-  // wait for block j, then stage it in yS; false when the wait expired (the block is then
-  // marked NaN and published, and the caller returns)
   // this block's solution (or NaN) into B and into the mailbox
   auto publish = [&](int ii, int c, double v) {
     B[(size_t)c * ldb + R0 + ii] = v;
