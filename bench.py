@@ -868,7 +868,8 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     launches = 0
-    with Clocks(local) as clk:
+    # the timed region lasts ~0.2 s: sample every 50 ms so that some samples fall inside it
+    with Clocks(local, period_ms=50) as clk:
         barrier()
         e0.record(stream)
         for s in range(args.warmup, nsteps):
