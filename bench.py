@@ -367,7 +367,8 @@ def run_batched(args, rank, world):
         return sum(gt) / len(gt)
 
     g_pool = graph_ms(False)
-    g_pers = graph_ms(True)                 # the persistent launch is the handle's default
+    g_pers = graph_ms(True)
+    h.set_batched_mode(False)               # the handle's default (the stream pool) for the POSV
     failed = [i for i, v in enumerate(d_info.cpu().tolist()) if v != 0]
     # (2) the full batched solve: mixed tree, fallback where it fails, FP64 refinement to 1e-12
     Xs = [torch.zeros_like(B) for B in B0]
