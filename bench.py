@@ -284,6 +284,28 @@ def cpu_oracle_sample(n_s: int = 3072, rho: float = 2.0, mats=None, budget_s: fl
             "seconds": secs}
 
 
+def cpu_dense_sample(mats, nrhs: int = 4, budget_s: float = 10.0, seed_base: int = 10000):
+    """Time the oracle's plain FP64 Cholesky and solve (oracle.dense) on `mats` one after
+    another until `budget_s` seconds have run: the CPU baseline of the batched workload."""
+    from oracle import dense
+    from synth import rhs, seed_for
+    done, secs, flops = 0, 0.0, 0.0
+    for i, A in enumerate(mats):
+        B = rhs(A.shape[0], nrhs, seed_for(3, seed_base + i))
+        t0 = time.perf_counter()
+        L, info = dense.cholesky(A)
+        assert info == 0
+        dense.potrs(L, B)
+        secs += time.perf_counter() - t0
+        done += 1
+        flops += A.shape[0] ** 3 / 3.0
+        if secs >= budget_s:
+            break
+    return {"value": flops / secs / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"plain FP64 Cholesky + {nrhs}-RHS solve (oracle.dense, float64 numpy) on the first "
+                      f"{done} of the batch's systems; {secs:.1f} s"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -373,16 +395,19 @@ def run_batched(args, rank, world):
     # (2) the full batched solve: mixed tree, fallback where it fails, FP64 refinement to 1e-12
     Xs = [torch.zeros_like(B) for B in B0]
     times = []
-    for rep in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        reps.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+    for rep in range(args.warmup):
         out = h.posv_batched(tree, A0, B0, Xs, max_iter=30, tol=1e-12)
-        e1.record()
-        torch.cuda.synchronize()
-        if rep >= args.warmup:
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for rep in range(args.steps):
+            torch.cuda.synchronize()
+            reps.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = h.posv_batched(tree, A0, B0, Xs, max_iter=30, tol=1e-12)
+            e1.record()
+            torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
     # every rank solves its LPT share (weak scaling: batch systems per rank on average): the
     # job's work over the slowest rank
@@ -416,7 +441,12 @@ def run_batched(args, rank, world):
             "systems_refactored_with_fallback": int(sum(out["used_fallback"])),
             "max_refinement_rounds": int(max(out["iters"])), "worst_solution_residual": worst,
             "graph_factor_solve_ms": {"persistent": g_pers, "stream_pool": g_pool},
-            "graph_systems_failing_mixed_tree": len(failed)}
+            "graph_systems_failing_mixed_tree": len(failed), "clocks": clk.summary(),
+            "roofline": None,
+            "roofline_note": "no single dominant kernel: each system's launch chain runs on one stream "
+                             "of a 32-stream pool, with refinement rounds and fallback refactorizations"}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_dense_sample(mats)
     reps.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

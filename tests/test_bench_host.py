@@ -148,3 +148,13 @@ def test_paired_ratio_ci_brackets_the_ratio():
     assert abs(r - a.mean() / b.mean()) < 1e-15
     assert lo <= r <= hi and hi - lo < 0.05
     assert bench.paired_ratio_ci(b, b)[1:] == (1.0, 1.0)     # identical pairs: no spread
+
+
+def test_cpu_dense_sample_times_the_oracle_on_a_bounded_prefix():
+    from synth import rbf_spd, seed_for
+    mats = [rbf_spd(n, seed_for(3, 1 + i)) for i, n in enumerate([64, 96, 80])]
+    out = bench.cpu_dense_sample(mats, budget_s=0.0)       # stops after the first system
+    assert out["kind"] == "oracle" and out["unit"] == "TFLOP/s" and out["cores"] >= 1
+    assert out["value"] > 0 and "first 1 of the batch's systems" in out["sample"]
+    out = bench.cpu_dense_sample(mats, budget_s=1e9)       # all of them
+    assert "first 3 of the batch's systems" in out["sample"]
