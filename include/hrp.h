@@ -27,6 +27,10 @@
  *   - There is no CPU fallback: every step runs in this library's CUDA kernels.
  *   - The first call that needs a larger workspace allocates it (cudaMalloc); make one
  *     call of each size before capturing calls into a CUDA graph.
+ *   - A handle's calls share its workspace (shadows, inverses, the solve's mailboxes): calls
+ *     on one handle must be ordered on the GPU (one stream, or streams joined by events).
+ *     Work that should run concurrently takes one handle per stream.  A handle is used by
+ *     one host thread at a time.
  */
 #ifndef HRP_H_
 #define HRP_H_
